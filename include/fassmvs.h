@@ -1,0 +1,250 @@
+/*
+ * fassmvs.h -- C ABI of the B300 (sm_103a) implementation of the FaSS-MVS hot
+ * path: plane-sweep census cost volume, surface-aware semi-global matching,
+ * winner-takes-all with sub-plane refinement, normal and confidence maps,
+ * coarse-to-fine over an image pyramid (Ruf, Weinmann, Hinz, arXiv 2112.00821).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All image, map and volume pointers are DEVICE pointers on the device the
+ *    context was created for; the caller owns them.  Camera and plane
+ *    parameters are HOST values (copied during the call).
+ *  - Layouts are row-major and unpadded unless a pitch or slot stride is given:
+ *      image  uint8  [H][W]            census uint64 [H][W]
+ *      volume uint16 [H][W][Ds]        slot s of pixel p holds plane lo_p + s,
+ *                                      s < D; Ds >= D is the slot stride
+ *      lo     int32  [H][W]            first plane of the window of each pixel
+ *                                      (NULL: lo_p = 0 everywhere)
+ *      dI     int8   [8][H][W]         per-path index jumps (surface-normal SGM)
+ *      depth  float  [H][W]            normal float [H][W][3]  conf float [H][W]
+ *  - Cameras: K is the 3x3 intrinsic matrix (row-major); neighbour k maps a
+ *    point X of the reference camera frame to its own frame as
+ *    X_k = R_k X + t_k (R_k row-major 3x3, t_k 3-vector), the relative pose of
+ *    Sec. 2.1 / Eq. homography.  side[k] = -1 for a view left of the
+ *    reference (k < ref), +1 for a view right of it.
+ *  - Planes: n^T X + delta = 0 in the reference frame; the finest list is
+ *    uniform in inverse distance, 1/delta_g = rho_far + g * drho, g = 0 the
+ *    farthest (Sec. 2.2.3).  Level l uses every 2^l-th plane.
+ *  - Path order of the aggregation (and of dI): r = (1,0) (-1,0) (0,1) (0,-1)
+ *    (1,1) (-1,-1) (1,-1) (-1,1); the predecessor of p on path r is p - r;
+ *    4-path aggregation uses the first four.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream).  The returned status covers argument validation and
+ *    launch errors; device-side failures surface at fassmvs_sync.  Nothing
+ *    throws or aborts across this boundary.  A context is not thread-safe;
+ *    use one context per host thread.
+ */
+#ifndef FASSMVS_H
+#define FASSMVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FASSMVS_API __attribute__((visibility("default")))
+#else
+#define FASSMVS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fassmvs_ctx fassmvs_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    FASSMVS_OK = 0,
+    FASSMVS_EINVAL = 1,    /* bad argument: sizes, pointers, limits */
+    FASSMVS_ENOMEM = 2,    /* scratch would exceed the context memory budget */
+    FASSMVS_EBUSY = 3,     /* no room for the request right now (serving) */
+    FASSMVS_ETIMEOUT = 4,  /* a bounded device wait gave up */
+    FASSMVS_ECUDA = 5,     /* a CUDA runtime call failed */
+    FASSMVS_EINTERNAL = 6  /* a kernel reported an inconsistency */
+} fassmvs_status;
+
+/* Sweep planes (Sec. 2.2): normal n (unit, reference frame) and the inverse
+ * distances of the finest list. */
+typedef struct {
+    double n[3];
+    double rho_far;  /* 1/delta of plane 0, the farthest */
+    double drho;     /* inverse-distance step of the finest list */
+    int32_t G0;      /* number of planes of the finest list */
+} fassmvs_planes;
+
+/* Estimation settings (Sec. 2.1-2.5 and Sec. 3.2-3.5). */
+typedef struct {
+    int32_t levels;        /* pyramid levels n, 1..8 (Sec. 2.1) */
+    int32_t D[8];          /* plane window per level below the top; the top
+                              level sweeps its whole list (<= 256 planes) */
+    int32_t paths;         /* 8 or 4 aggregation paths (Sec. 3.5) */
+    int32_t variant;       /* 0 plane-wise, 1 surface normal, 2 path gradient
+                              (Eq. sgm-smooth-fp / -sn / -pg) */
+    int32_t p1;            /* phi1 for one image per subset; multiplied by
+                              n_max = max(n_left, n_right) (Sec. 2.3.3) */
+    int32_t p2;            /* phi2 (x n_max) when adaptive_p2 == 0 */
+    int32_t adaptive_p2;   /* 1: phi2 = phi1 (1 + alpha exp(-dI / beta)) */
+    float alpha, beta;     /* Eq. p2-grad, 8 and 10 in the paper */
+    int32_t median5;       /* 5x5 median on the refined depth (Sec. 2.1) */
+    int32_t normal_radius; /* smoothing window radius; sigma = radius (Sec. 2.4) */
+    float normal_beta;     /* beta of Eq. normal-smooth, 10 in the paper */
+    float rho_deg;         /* critical angle of Eq. weight-normal, 60 */
+    int32_t dmax;          /* clamp of the sn / pg index jumps */
+} fassmvs_config;
+
+/* SGM parameters of one aggregation (Eq. xsgm ... Eq. p2-grad). */
+typedef struct {
+    int32_t paths;         /* 8 or 4 */
+    int32_t variant;       /* 0, 1, 2 as above */
+    int32_t p1;            /* phi1, already multiplied by n_max */
+    int32_t p2;            /* phi2, already multiplied, used when p2_lut == NULL */
+    int32_t dmax;          /* clamp of the index jumps */
+    const uint16_t* p2_lut;/* HOST table of 256 phi2 values indexed by |I(p) -
+                              I(p-r)|, or NULL for the fixed p2 */
+} fassmvs_sgm_params;
+
+/* Fills the paper's defaults: 1 level, D = 256, 8 paths, plane-wise,
+ * p1 = 24 (census 9x7, Sec. 3.4), adaptive phi2 with alpha = 8, beta = 10,
+ * median on, radius 2, beta 10, rho 60 deg, dmax 8. */
+FASSMVS_API fassmvs_status fassmvs_config_default(fassmvs_config* cfg);
+
+/* Creates a context on `device`.  Scratch (pyramids, census, cost and
+ * aggregated volumes, per-level maps) is allocated lazily and kept; its total
+ * never exceeds mem_budget bytes (0 = no limit), else FASSMVS_ENOMEM. */
+FASSMVS_API fassmvs_status fassmvs_create(const fassmvs_config* cfg, int device, size_t mem_budget,
+                              fassmvs_ctx** out);
+FASSMVS_API void fassmvs_destroy(fassmvs_ctx* ctx);
+
+/* Replaces the configuration (same validation as fassmvs_create). */
+FASSMVS_API fassmvs_status fassmvs_set_config(fassmvs_ctx* ctx, const fassmvs_config* cfg);
+
+/* Stores the calibration of the next estimates (host arrays, copied):
+ * K 3x3, R n_nb x 3 x 3, t n_nb x 3, side n_nb (Sec. 2.1). */
+FASSMVS_API fassmvs_status fassmvs_set_cameras(fassmvs_ctx* ctx, const double K[9], int n_nb,
+                                   const double* R, const double* t, const int8_t* side);
+
+/* Full hierarchical estimate of one reference frame (Sec. 2.1, Fig. overview):
+ * ref and nbrs[k] are W x H uint8 images with row pitch `pitch` bytes
+ * (nbrs is a HOST array of n_nb device pointers, n_nb equal to the count
+ * given to fassmvs_set_cameras); depth (W*H floats), normal (W*H*3) and conf
+ * (W*H) receive the level-0 maps.  Depth is the z distance in the reference
+ * frame; normals face the camera; confidence is in [0, 1]. */
+FASSMVS_API fassmvs_status fassmvs_estimate(fassmvs_ctx* ctx, const uint8_t* ref, int W, int H, int pitch,
+                                const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* planes,
+                                float* depth, float* normal, float* conf, void* stream);
+
+/* ---- stages of the hot path (used by the estimate and by parity tests) ---- */
+
+/* Sec. 2.1 pyramid level: 3x3 Gaussian (sigma 1, integer weights 70/116/70
+ * per axis) then decimation, out[y][x] = blur(in)(2x, 2y), size
+ * ceil(W/2) x ceil(H/2), clamp-to-edge, rounded half up. */
+FASSMVS_API fassmvs_status fassmvs_pyramid_down(fassmvs_ctx* ctx, const uint8_t* in, int W, int H,
+                                    uint8_t* out, void* stream);
+
+/* Census 9x7 (Sec. 2.2.1 / Sec. 3.4): bit (dy+3)*9 + (dx+4) = [I(q) < I(p)],
+ * clamp-to-edge, centre bit 0. */
+FASSMVS_API fassmvs_status fassmvs_census(fassmvs_ctx* ctx, const uint8_t* img, int W, int H, uint64_t* out,
+                              void* stream);
+
+/* Plane-sweep cost volume of one level (Alg. 1): for every pixel p and slot
+ * s < D (plane g = lo_p + s of a list of G planes with 1/delta_g = rho0 +
+ * g * drho), the census-Hamming cost of each neighbour warped by the
+ * plane-induced homography H = K (R - t n^T / delta) K^-1, summed over the
+ * left and the right views, each sum rescaled to max(n_left, n_right) images
+ * (round half up), S = min of the two.  A view whose centre sample leaves the
+ * image costs 62.  Samples are bilinear on a 1/256-pixel grid with 8-bit
+ * weights.  K, R, t, n are host arrays.  Slots D..Ds-1 are left untouched. */
+FASSMVS_API fassmvs_status fassmvs_cost_volume(fassmvs_ctx* ctx, const uint8_t* ref, const uint8_t* const* nbrs,
+                                   int n_nb, const int8_t* side, int W, int H, const double K[9],
+                                   const double* R, const double* t, const double n[3], double rho0,
+                                   double drho, int G, const int32_t* lo, int D, int Ds, uint16_t* S,
+                                   void* stream);
+
+/* Surface-aware SGM (Sec. 2.3, Eq. xsgm, sgm-smooth-fp/-sn/-pg, sgm-aggr) in
+ * the normalised form L_r(p,s) = S(p,s) + min(L'(s'), L'(s'-1) + P1,
+ * L'(s'+1) + P1, M + P2) - M, with s' = s + lo_p - lo_{p-r} + di, M = min L',
+ * slots outside the predecessor's window = +inf, P2 = max(P2, P1), L = S at
+ * the first pixel of a path.  di: 0 (plane-wise), dI[r][p] (surface normal)
+ * or g(p-2r) - g(p-r) with g = lo + argmin L_r (path gradient), clamped to
+ * +-dmax.  img (uint8 [H][W]) feeds the adaptive phi2 and may be NULL with a
+ * fixed p2.  Sbar receives sum_r L_r; FASSMVS_EINVAL if that sum could
+ * exceed 16 bits (paths * (max S + max P2) >= 65536 with max S = 62 * 6). */
+FASSMVS_API fassmvs_status fassmvs_sgm_aggregate(fassmvs_ctx* ctx, const uint16_t* S, const int32_t* lo,
+                                     const int8_t* dI, const uint8_t* img, int W, int H, int D,
+                                     int Ds, const fassmvs_sgm_params* prm, uint16_t* Sbar,
+                                     void* stream);
+
+/* Eq. sgm-wta + plane depth (Sec. 2.3.2) + refinement (Sec. 2.3.4): argmin
+ * (lowest slot on ties), parabola through the winner and its neighbours at
+ * their plane distances (none at a window edge), clamped between them;
+ * depth = -delta / (n^T K^-1 (x, y, 1)^T).  gwin (optional, int32 [H][W])
+ * receives the winning plane index lo + s. */
+FASSMVS_API fassmvs_status fassmvs_wta_refine(fassmvs_ctx* ctx, const uint16_t* Sbar, const int32_t* lo, int W,
+                                  int H, int D, int Ds, const double K[9], const double n[3],
+                                  double rho0, double drho, int G, float* depth, int32_t* gwin,
+                                  void* stream);
+
+/* 5x5 median (Sec. 2.1), clamp-to-edge. */
+FASSMVS_API fassmvs_status fassmvs_median5(fassmvs_ctx* ctx, const float* in, int W, int H, float* out,
+                               void* stream);
+
+/* Sec. 2.4 normals: n = h x v of back-projected central differences, turned
+ * to face the camera, then the appearance-weighted Gaussian of Eq.
+ * normal-smooth (window radius r, sigma = r, beta), normalised; (0,0,0) when
+ * undefined.  raw (optional) receives the unsmoothed normals.  When conf is
+ * not NULL it also receives Eq. weight-normal (Sec. 2.5) for the plane normal
+ * n_plane and critical angle rho_deg, clamped to [0, 1]. */
+FASSMVS_API fassmvs_status fassmvs_normals(fassmvs_ctx* ctx, const float* depth, const uint8_t* img, int W,
+                               int H, const double K[9], int radius, float beta, float* normal,
+                               float* raw, const double n_plane[3], float rho_deg, float* conf,
+                               void* stream);
+
+/* Eq. sampling_range / dynamic cost volume: window of D planes centred on the
+ * plane through the nearest-neighbour upscaled coarse depth dc (Wc x Hc):
+ * lo = clamp(floor(c + 1/2) - D/2, 0, G - D), c = (rho - rho0) / drho, taken
+ * in FP32 (see the oracle's statement of the operation order). */
+FASSMVS_API fassmvs_status fassmvs_window(fassmvs_ctx* ctx, const float* dc, int Wc, int Hc, int W, int H,
+                              const double K[9], const double n[3], double rho0, double drho,
+                              int G, int D, int32_t* lo, void* stream);
+
+/* Eq. sgm-smooth-sn index jumps from the upscaled coarse depth dc and normal
+ * nc (Wc x Hc): di = round_half_away((1/lambda - 1/d) / drho), clamped to
+ * +-dmax, 0 when the tangent plane does not face the rays (FP32). */
+FASSMVS_API fassmvs_status fassmvs_dsn(fassmvs_ctx* ctx, const float* dc, const float* nc, int Wc, int Hc,
+                           int W, int H, const double K[9], double drho, int dmax, int8_t* dI,
+                           void* stream);
+
+/* Stage timers.  While enabled, the library brackets each stage it launches
+ * with CUDA events on the call's stream and accumulates the elapsed time
+ * (milliseconds) and launch count per stage; reading waits for the recorded
+ * events.  Stages: */
+enum {
+    FASSMVS_STAGE_PYRAMID = 0, /* pyramid levels of all views */
+    FASSMVS_STAGE_CENSUS = 1,  /* reference census + per-level homography tables */
+    FASSMVS_STAGE_COST = 2,    /* plane-sweep cost volume kernel */
+    FASSMVS_STAGE_SGM = 3,     /* all aggregation paths */
+    FASSMVS_STAGE_WTA = 4,     /* winner-takes-all + refinement */
+    FASSMVS_STAGE_MEDIAN = 5,  /* 5x5 median */
+    FASSMVS_STAGE_NORMALS = 6, /* normals, smoothing, confidence */
+    FASSMVS_STAGE_WINDOW = 7,  /* plane windows + surface-normal jumps */
+    FASSMVS_NSTAGES = 8
+};
+FASSMVS_API fassmvs_status fassmvs_profile_enable(fassmvs_ctx* ctx, int on);
+/* ms[FASSMVS_NSTAGES], counts[FASSMVS_NSTAGES] (either may be NULL); reset != 0
+ * clears the totals after reading. */
+FASSMVS_API fassmvs_status fassmvs_profile_read(fassmvs_ctx* ctx, double* ms, uint64_t* counts,
+                                                int reset);
+
+/* Waits for the context's last stream and reports deferred device errors. */
+FASSMVS_API fassmvs_status fassmvs_sync(fassmvs_ctx* ctx);
+
+/* Human-readable description of the last failure of this context (never
+ * NULL; thread-local text for ctx == NULL). */
+FASSMVS_API const char* fassmvs_last_error(const fassmvs_ctx* ctx);
+
+/* Number of kernels the library launched since the context was created. */
+FASSMVS_API uint64_t fassmvs_launch_count(const fassmvs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASSMVS_H */

@@ -131,6 +131,20 @@ def cost_volume(ref, nbrs, side, K, R, t, n, rho0, drho, G, lo=None, D=None, Ds=
     return S
 
 
+def cost_at(ref, nbrs, side, K, R, t, n, rho0, drho, xs, ys, gs):
+    ref = _c(ref, np.uint8)
+    H, W = ref.shape
+    V = len(nbrs)
+    nb = [_c(x, np.uint8) for x in nbrs]
+    arr = (C.c_void_p * V)(*[x.ctypes.data for x in nb])
+    xs, ys, gs = (_c(a, np.int32) for a in (xs, ys, gs))
+    out = np.zeros(xs.size, np.uint16)
+    lib().or_cost_at(_p(ref), arr, V, _p(_c(side, np.int8)), W, H, _p(_c(K, np.float64)),
+                     _p(_c(R, np.float64)), _p(_c(t, np.float64)), _p(_c(n, np.float64)),
+                     C.c_double(rho0), C.c_double(drho), int(xs.size), _p(xs), _p(ys), _p(gs), _p(out))
+    return out
+
+
 def p2_table(p1, alpha=8.0, beta=10.0):
     lut = np.zeros(256, np.uint16)
     lib().or_p2_table(int(p1), C.c_double(alpha), C.c_double(beta), _p(lut))

@@ -323,6 +323,49 @@ OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int
     return 0;
 }
 
+/* The same cost for a list of individual voxels (pixel (x, y), plane g of
+   the level list), each computed on its own from the 9x7 window of warped
+   samples around the pixel -- used to check full-size volumes by sampling. */
+OR_EXPORT void or_cost_at(const uint8_t* ref, const uint8_t* const* nbrs, int V, const int8_t* side,
+                          int W, int H, const double K[9], const double* R, const double* t,
+                          const double n[3], double rho0, double drho, int npts, const int32_t* xs,
+                          const int32_t* ys, const int32_t* gs, uint16_t* out)
+{
+    int nL = 0, nR = 0;
+    for (int k = 0; k < V; ++k) { if (side[k] < 0) ++nL; else ++nR; }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < npts; ++i) {
+        int x = xs[i], y = ys[i];
+        uint64_t cref = 0;
+        int c0 = ref[(size_t)y * W + x];
+        for (int dy = -3; dy <= 3; ++dy)
+            for (int dx = -4; dx <= 4; ++dx) {
+                int xx = clampi(x + dx, 0, W - 1), yy = clampi(y + dy, 0, H - 1);
+                if (ref[(size_t)yy * W + xx] < c0) cref |= (uint64_t)1 << ((dy + 3) * 9 + dx + 4);
+            }
+        uint32_t sL = 0, sR = 0;
+        double Hm[9];
+        for (int k = 0; k < V; ++k) {
+            or_homography(K, R + 9 * k, t + 3 * k, n, plane_delta(rho0, drho, gs[i]), Hm);
+            int32_t valid;
+            int32_t cen = or_warp_sample(nbrs[k], W, H, Hm, x, y, &valid);
+            int h = 62;
+            if (valid) {
+                uint64_t bits = 0;
+                for (int dy = -3; dy <= 3; ++dy)
+                    for (int dx = -4; dx <= 4; ++dx) {
+                        int xx = clampi(x + dx, 0, W - 1), yy = clampi(y + dy, 0, H - 1);
+                        if (or_warp_sample(nbrs[k], W, H, Hm, xx, yy, NULL) < cen)
+                            bits |= (uint64_t)1 << ((dy + 3) * 9 + dx + 4);
+                    }
+                h = or_hamming(cref, bits);
+            }
+            if (side[k] < 0) sL += (uint32_t)h; else sR += (uint32_t)h;
+        }
+        out[i] = or_lr_combine(sL, nL, sR, nR);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Sec. 2.3.3, Eq. p2-grad: phi2 = phi1 (1 + alpha exp(-dI / beta)), with    */
 /* the penalties multiplied by the number of images per subset.  Reading:    */

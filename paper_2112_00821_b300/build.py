@@ -1,0 +1,40 @@
+"""Builds libfassmvs.so in-tree with nvcc for sm_103a (B300)."""
+from __future__ import annotations
+
+import glob
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu")))
+HDRS = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [
+    os.path.join(os.path.dirname(HERE), "include", "fassmvs.h")]
+LIB = os.path.join(HERE, "libfassmvs.so")
+NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
+         "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared", "--expt-relaxed-constexpr",
+         "-Xptxas", "-warn-spills"]
+
+
+def stale():
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(f) > t for f in SRC + HDRS)
+
+
+def build(force=False, verbose=False):
+    if not force and not stale():
+        return LIB
+    cmd = [NVCC, *FLAGS, "-o", LIB, *SRC, "-lcudart"]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
+    print(LIB)

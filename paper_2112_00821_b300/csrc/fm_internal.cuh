@@ -1,0 +1,95 @@
+// Internal declarations shared by the kernels and the C-ABI layer of the
+// B300 FaSS-MVS library.  Nothing here is part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fm {
+
+constexpr int kMaxViews = 16;     // neighbour views per reference frame
+constexpr int kMaxSlots = 256;    // planes per pixel window (32 lanes x 8 slots)
+constexpr int kCensusMax = 62;    // informative bits of a 9x7 census string
+
+// ---------------------------------------------------------------- cameras
+// Per view, the rank-1 form of the plane-induced homography
+//   H(rho) = A - rho * e c^T,  A = K R K^-1, e = K t, c = K^-T n,
+// (Eq. homography with rho = 1 / delta), precomputed on the host in FP64.
+struct ViewGeom {
+    double A[kMaxViews][9];
+    double e[kMaxViews][3];
+    double c[kMaxViews][3];
+};
+
+// One level of the sweep: G planes with 1/delta_g = rho0 + g * drho.
+struct LevelPlanes {
+    double rho0, drho;
+    int G, V;
+};
+
+// Device tables built once per level by prep_level_kernel:
+//   htab[(g * V + k) * 18 + i]     H_{g,k} entry i as (hi, lo) float pairs:
+//                                   i in 0..8 -> hi, 9..17 -> lo (row-major)
+//   delta[g]                        plane distance 1 / (rho0 + g drho)
+void launch_prep_level(const ViewGeom& vg, const LevelPlanes& lp, float* htab, float* delta,
+                       cudaStream_t st);
+
+// ---------------------------------------------------------------- cost volume
+struct ViewPtrs {
+    const uint8_t* img[kMaxViews];
+    int side[kMaxViews];          // -1 left, +1 right
+};
+
+struct CostArgs {
+    const uint64_t* cref;         // reference census [H][W]
+    ViewPtrs views;
+    int V, W, H, pitch;
+    int nL, nR, nmax;
+    uint64_t mL, mR;              // ceil(2^32 / nL), ceil(2^32 / nR)
+    const float* htab;
+    const int32_t* lo;            // may be null (window starts at 0)
+    int D, Ds, G;
+    uint16_t* S;
+};
+void launch_cost(const CostArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------- SGM
+struct SgmArgs {
+    const uint16_t* S;
+    const int32_t* lo;
+    const int8_t* dI;
+    const uint8_t* img;
+    int W, H, D, Ds, img_pitch;
+    int paths, variant, p1, p2, dmax;
+    int use_lut;
+    uint16_t lut[256];
+    uint16_t* Sbar;
+};
+void launch_sgm(const SgmArgs& a, cudaStream_t st);
+
+// ---------------------------------------------------------------- per-pixel stages
+void launch_pyramid_down(const uint8_t* in, int W, int H, int pitch_in, uint8_t* out,
+                         int pitch_out, cudaStream_t st);
+void launch_census(const uint8_t* img, int W, int H, int pitch, uint64_t* out, cudaStream_t st);
+
+struct Intr {
+    float fx, fy, cx, cy;
+};
+
+void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
+                       const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
+                       cudaStream_t st);
+void launch_delta_table(double rho0, double drho, int G, float* delta, cudaStream_t st);
+void launch_median5(const float* in, int W, int H, float* out, cudaStream_t st);
+void launch_normals(const float* depth, const uint8_t* img, int img_pitch, int W, int H, Intr K,
+                    int radius, float beta, float* raw, float* normal, const float npl[3],
+                    float rho_deg, float* conf, cudaStream_t st);
+void launch_window(const float* dc, int Wc, int Hc, int W, int H, Intr K, const float n[3],
+                   float rho0, float drho, int G, int D, int32_t* lo, cudaStream_t st);
+void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, Intr K,
+                float drho, int dmax, int8_t* dI, cudaStream_t st);
+
+// Counts kernel launches issued by this library (process-wide).
+uint64_t launches();
+void count_launch(int n = 1);
+
+}  // namespace fm

@@ -1,0 +1,349 @@
+// Per-pixel stages of the FaSS-MVS hot path for sm_103a: Gaussian pyramid
+// (Sec. 2.1), reference census (Sec. 2.2.1), winner-takes-all with sub-plane
+// refinement (Eq. sgm-wta, Sec. 2.3.4), 5x5 median (Sec. 2.1), normals with
+// appearance-weighted smoothing and confidence (Sec. 2.4, 2.5), per-pixel
+// plane windows (Eq. sampling_range) and surface-normal index jumps
+// (Eq. sgm-smooth-sn).  These are bandwidth- or latency-light next to the
+// cost volume and the aggregation.
+#include <math.h>
+
+#include "fm_internal.cuh"
+
+namespace fm {
+
+namespace {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// ---------------------------------------------------------------- pyramid
+__global__ void pyramid_kernel(const uint8_t* __restrict__ in, int W, int H, int pin,
+                               uint8_t* __restrict__ out, int pout)
+{
+    const int Wo = (W + 1) >> 1, Ho = (H + 1) >> 1;
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= Wo || y >= Ho) return;
+    const int w[3] = {70, 116, 70};       // 256 * exp(-i^2/2) / sum, rounded (sigma = 1)
+    int acc = 0;
+#pragma unroll
+    for (int j = -1; j <= 1; ++j) {
+        const uint8_t* row = in + (size_t)clampi(2 * y + j, 0, H - 1) * pin;
+        int hsum = w[0] * row[clampi(2 * x - 1, 0, W - 1)] + w[1] * row[clampi(2 * x, 0, W - 1)] +
+                   w[2] * row[clampi(2 * x + 1, 0, W - 1)];
+        acc += w[j + 1] * hsum;
+    }
+    out[(size_t)y * pout + x] = (uint8_t)((acc + 32768) >> 16);
+}
+
+// ---------------------------------------------------------------- census
+__global__ void census_kernel(const uint8_t* __restrict__ img, int W, int H, int pitch,
+                              uint64_t* __restrict__ out)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const int c = img[(size_t)y * pitch + x];
+    uint64_t bits = 0;
+#pragma unroll
+    for (int dy = -3; dy <= 3; ++dy) {
+        const uint8_t* row = img + (size_t)clampi(y + dy, 0, H - 1) * pitch;
+#pragma unroll
+        for (int dx = -4; dx <= 4; ++dx) {
+            const int k = (dy + 3) * 9 + (dx + 4);
+            if (__ldg(row + clampi(x + dx, 0, W - 1)) < c) bits |= 1ull << k;
+        }
+    }
+    out[(size_t)y * W + x] = bits;
+}
+
+// ---------------------------------------------------------------- WTA + refinement
+__global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __restrict__ lo, int W,
+                           int H, int D, int Ds, const float* __restrict__ delta, Intr K, float n0,
+                           float n1, float n2, float* __restrict__ depth, int32_t* __restrict__ gwin)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t p = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (p >= (size_t)W * H) return;
+    const int s0 = lane * 8;
+    uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (s0 < D) {
+        uint4 raw = __ldg(reinterpret_cast<const uint4*>(Sbar + p * Ds + s0));
+        v[0] = raw.x & 0xFFFF; v[1] = raw.x >> 16; v[2] = raw.y & 0xFFFF; v[3] = raw.y >> 16;
+        v[4] = raw.z & 0xFFFF; v[5] = raw.z >> 16; v[6] = raw.w & 0xFFFF; v[7] = raw.w >> 16;
+    }
+    uint32_t key = 0xFFFFFFFFu;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (s0 + i < D) key = min(key, (v[i] << 8) | (uint32_t)(s0 + i));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(0xFFFFFFFFu, key, o));
+    const int s = (int)(key & 255u);
+    // neighbour costs c[s-1], c[s+1] from the lanes that hold them
+    const int sm = max(s - 1, 0), sp = min(s + 1, D - 1);
+    uint32_t vm = 0, vp = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if ((sm & 7) == i) vm = v[i];
+        if ((sp & 7) == i) vp = v[i];
+    }
+    vm = __shfl_sync(0xFFFFFFFFu, vm, sm >> 3);
+    vp = __shfl_sync(0xFFFFFFFFu, vp, sp >> 3);
+    if (lane != 0) return;
+    const int x = (int)(p % W), y = (int)(p / W);
+    const int g = (lo ? lo[p] : 0) + s;
+    const float x0 = delta[g];
+    float xs = x0;
+    if (s > 0 && s < D - 1) {
+        const float xm = delta[g - 1], xp = delta[g + 1];
+        const float c0 = (float)(key >> 8), cm = (float)vm, cp = (float)vp;
+        const float A = (x0 - xm) * (c0 - cp);
+        const float B = (x0 - xp) * (c0 - cm);
+        const float den = A - B;
+        if (den > 0.0f) {
+            xs = x0 - 0.5f * ((x0 - xm) * A - (x0 - xp) * B) / den;
+            xs = fminf(fmaxf(xs, fminf(xm, xp)), fmaxf(xm, xp));
+        }
+    }
+    const float ray = n0 * ((x - K.cx) / K.fx) + n1 * ((y - K.cy) / K.fy) + n2;
+    depth[p] = -xs / ray;
+    if (gwin) gwin[p] = g;
+}
+
+// ---------------------------------------------------------------- median 5x5
+__global__ void median5_kernel(const float* __restrict__ in, int W, int H, float* __restrict__ out)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    float v[25];
+#pragma unroll
+    for (int j = 0; j < 5; ++j)
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            v[5 * j + i] = __ldg(in + (size_t)clampi(y + j - 2, 0, H - 1) * W + clampi(x + i - 2, 0, W - 1));
+    // the element of rank 12 (ties broken by position) is the median
+    float med = v[0];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) {
+        int rank = 0;
+#pragma unroll
+        for (int j = 0; j < 25; ++j)
+            rank += (v[j] < v[i]) || (v[j] == v[i] && j < i);
+        if (rank == 12) med = v[i];
+    }
+    out[(size_t)y * W + x] = med;
+}
+
+// ---------------------------------------------------------------- normals
+__device__ __forceinline__ float3 backproject(const float* __restrict__ d, int W, int x, int y, Intr K)
+{
+    float z = __ldg(d + (size_t)y * W + x);
+    return make_float3(z * ((x - K.cx) / K.fx), z * ((y - K.cy) / K.fy), z);
+}
+
+__global__ void normal_raw_kernel(const float* __restrict__ depth, int W, int H, Intr K,
+                                  float* __restrict__ raw)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    float3 A = backproject(depth, W, min(x + 1, W - 1), y, K);
+    float3 B = backproject(depth, W, max(x - 1, 0), y, K);
+    float3 C = backproject(depth, W, x, min(y + 1, H - 1), K);
+    float3 E = backproject(depth, W, x, max(y - 1, 0), K);
+    float3 P = backproject(depth, W, x, y, K);
+    float3 h = make_float3(A.x - B.x, A.y - B.y, A.z - B.z);
+    float3 v = make_float3(C.x - E.x, C.y - E.y, C.z - E.z);
+    float3 c = make_float3(h.y * v.z - h.z * v.y, h.z * v.x - h.x * v.z, h.x * v.y - h.y * v.x);
+    float len = sqrtf(c.x * c.x + c.y * c.y + c.z * c.z);
+    float* o = raw + 3 * ((size_t)y * W + x);
+    if (!(len > 0.0f)) { o[0] = o[1] = o[2] = 0.0f; return; }
+    float sgn = (c.x * P.x + c.y * P.y + c.z * P.z) > 0.0f ? -1.0f : 1.0f;
+    float inv = sgn / len;
+    o[0] = c.x * inv; o[1] = c.y * inv; o[2] = c.z * inv;
+}
+
+__global__ void normal_smooth_kernel(const float* __restrict__ raw, const uint8_t* __restrict__ img,
+                                     int pitch, int W, int H, int radius, float beta,
+                                     float* __restrict__ normal, float np0, float np1, float np2,
+                                     float cosr, float* __restrict__ conf)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const size_t p = (size_t)y * W + x;
+    const float sigma = (float)radius;
+    const float norm = rsqrtf(2.0f * 3.14159265358979f * sigma * sigma);
+    const float i2s2 = 1.0f / (2.0f * sigma * sigma);
+    const float ib = 1.0f / beta;
+    const float Ip = (float)img[(size_t)y * pitch + x];
+    float sx = raw[3 * p], sy = raw[3 * p + 1], sz = raw[3 * p + 2];
+    for (int j = -radius; j <= radius; ++j) {
+        int yy = y + j;
+        if (yy < 0 || yy >= H) continue;
+        for (int i = -radius; i <= radius; ++i) {
+            int xx = x + i;
+            if (xx < 0 || xx >= W) continue;
+            const size_t q = (size_t)yy * W + xx;
+            float dI = fabsf(Ip - (float)img[(size_t)yy * pitch + xx]);
+            float w = norm * expf(-(float)(i * i + j * j) * i2s2 - dI * ib);
+            sx += w * raw[3 * q];
+            sy += w * raw[3 * q + 1];
+            sz += w * raw[3 * q + 2];
+        }
+    }
+    float len = sqrtf(sx * sx + sy * sy + sz * sz);
+    float inv = len > 0.0f ? 1.0f / len : 0.0f;
+    sx *= inv; sy *= inv; sz *= inv;
+    normal[3 * p] = sx; normal[3 * p + 1] = sy; normal[3 * p + 2] = sz;
+    if (conf) {
+        float a = sx * np0 + sy * np1 + sz * np2;
+        float b = -np2;
+        float c = 0.0f;
+        if (a >= cosr && b >= cosr) c = fminf(fmaxf((a * b - cosr) / (1.0f - cosr), 0.0f), 1.0f);
+        conf[p] = c;
+    }
+}
+
+// ---------------------------------------------------------------- window (FP32 decision)
+__device__ __forceinline__ float ray_weight(float n0, float n1, float n2, int x, int y, Intr K)
+{
+    float a = __fdiv_rn(__fsub_rn((float)x, K.cx), K.fx);
+    float b = __fdiv_rn(__fsub_rn((float)y, K.cy), K.fy);
+    float s = __fadd_rn(__fmul_rn(n0, a), __fmul_rn(n1, b));
+    return -__fadd_rn(s, n2);
+}
+
+__global__ void window_kernel(const float* __restrict__ dc, int Wc, int Hc, int W, int H, Intr K,
+                              float n0, float n1, float n2, float rho0, float drho, int G, int D,
+                              int32_t* __restrict__ lo)
+{
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    float d = dc[(size_t)min(y >> 1, Hc - 1) * Wc + min(x >> 1, Wc - 1)];
+    float w = ray_weight(n0, n1, n2, x, y, K);
+    float rho = __fdiv_rn(1.0f, __fmul_rn(d, w));
+    float c = __fdiv_rn(__fsub_rn(rho, rho0), drho);
+    float fl = floorf(__fadd_rn(c, 0.5f));
+    int l;
+    if (!(fl > -1.0e9f)) l = 0;
+    else if (fl > 1.0e9f) l = G - D;
+    else l = (int)fl - D / 2;
+    lo[(size_t)y * W + x] = clampi(l, 0, G - D);
+}
+
+// ---------------------------------------------------------------- surface-normal jumps (FP32)
+__global__ void dsn_kernel(const float* __restrict__ dc, const float* __restrict__ nc, int Wc,
+                           int Hc, int W, int H, Intr K, float drho, int dmax,
+                           int8_t* __restrict__ dI)
+{
+    const int kdx[8] = {1, -1, 0, 0, 1, -1, 1, -1};
+    const int kdy[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const size_t pc = (size_t)min(y >> 1, Hc - 1) * Wc + min(x >> 1, Wc - 1);
+    const float d = dc[pc];
+    const float n0 = nc[3 * pc], n1 = nc[3 * pc + 1], n2 = nc[3 * pc + 2];
+    const float a = __fdiv_rn(__fsub_rn((float)x, K.cx), K.fx);
+    const float b = __fdiv_rn(__fsub_rn((float)y, K.cy), K.fy);
+    const float s0 = __fadd_rn(__fadd_rn(__fmul_rn(n0, a), __fmul_rn(n1, b)), n2);
+    const bool nz = (n0 != 0.0f || n1 != 0.0f || n2 != 0.0f);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const float gx = __fdiv_rn((float)kdx[r], K.fx);
+        const float gy = __fdiv_rn((float)kdy[r], K.fy);
+        const float s1 = __fadd_rn(__fmul_rn(n0, gx), __fmul_rn(n1, gy));
+        const float sp = __fsub_rn(s0, s1);
+        int out = 0;
+        if (nz && s0 < -1e-6f && sp < -1e-6f && d > 0.0f) {
+            const float den = __fmul_rn(__fmul_rn(d, s0), drho);
+            const float c = __fdiv_rn(-s1, den);
+            float rc = c >= 0.0f ? floorf(__fadd_rn(c, 0.5f)) : -floorf(__fadd_rn(-c, 0.5f));
+            rc = fminf(fmaxf(rc, (float)-dmax), (float)dmax);
+            out = (int)rc;
+        }
+        dI[(size_t)r * W * H + (size_t)y * W + x] = (int8_t)out;
+    }
+}
+
+__global__ void delta_kernel(double rho0, double drho, int G, float* __restrict__ delta)
+{
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < G) delta[g] = (float)(1.0 / (rho0 + (double)g * drho));
+}
+
+inline dim3 grid2(int W, int H, dim3 b) { return dim3((W + b.x - 1) / b.x, (H + b.y - 1) / b.y); }
+
+}  // namespace
+
+void launch_pyramid_down(const uint8_t* in, int W, int H, int pin, uint8_t* out, int pout,
+                         cudaStream_t st)
+{
+    dim3 b(32, 8);
+    pyramid_kernel<<<grid2((W + 1) / 2, (H + 1) / 2, b), b, 0, st>>>(in, W, H, pin, out, pout);
+    count_launch();
+}
+
+void launch_census(const uint8_t* img, int W, int H, int pitch, uint64_t* out, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    census_kernel<<<grid2(W, H, b), b, 0, st>>>(img, W, H, pitch, out);
+    count_launch();
+}
+
+void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
+                       const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
+                       cudaStream_t st)
+{
+    size_t np = (size_t)W * H;
+    int per = 8;
+    wta_kernel<<<(unsigned)((np + per - 1) / per), per * 32, 0, st>>>(Sbar, lo, W, H, D, Ds, delta, K, n[0],
+                                                                  n[1], n[2], depth, gwin);
+    count_launch();
+}
+
+void launch_delta_table(double rho0, double drho, int G, float* delta, cudaStream_t st)
+{
+    delta_kernel<<<(G + 127) / 128, 128, 0, st>>>(rho0, drho, G, delta);
+    count_launch();
+}
+
+void launch_median5(const float* in, int W, int H, float* out, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    median5_kernel<<<grid2(W, H, b), b, 0, st>>>(in, W, H, out);
+    count_launch();
+}
+
+void launch_normals(const float* depth, const uint8_t* img, int img_pitch, int W, int H, Intr K,
+                    int radius, float beta, float* raw, float* normal, const float npl[3],
+                    float rho_deg, float* conf, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    normal_raw_kernel<<<grid2(W, H, b), b, 0, st>>>(depth, W, H, K, raw);
+    float cosr = cosf(rho_deg * 3.14159265358979f / 180.0f);
+    normal_smooth_kernel<<<grid2(W, H, b), b, 0, st>>>(raw, img, img_pitch, W, H, radius, beta,
+                                                       normal, npl[0], npl[1], npl[2], cosr, conf);
+    count_launch(2);
+}
+
+void launch_window(const float* dc, int Wc, int Hc, int W, int H, Intr K, const float n[3],
+                   float rho0, float drho, int G, int D, int32_t* lo, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    window_kernel<<<grid2(W, H, b), b, 0, st>>>(dc, Wc, Hc, W, H, K, n[0], n[1], n[2], rho0, drho, G,
+                                                D, lo);
+    count_launch();
+}
+
+void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, Intr K,
+                float drho, int dmax, int8_t* dI, cudaStream_t st)
+{
+    dim3 b(32, 8);
+    dsn_kernel<<<grid2(W, H, b), b, 0, st>>>(dc, nc, Wc, Hc, W, H, K, drho, dmax, dI);
+    count_launch();
+}
+
+}  // namespace fm

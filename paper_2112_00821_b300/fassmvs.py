@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libfassmvs.so (see include/fassmvs.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current stream.  There
+is no CPU fallback: if the library is missing or no CUDA device is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfassmvs.so")
+_lib = None
+
+OK, EINVAL, ENOMEM, EBUSY, ETIMEOUT, ECUDA, EINTERNAL = range(7)
+_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ETIMEOUT", 5: "ECUDA", 6: "EINTERNAL"}
+
+
+class FassmvsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Planes(C.Structure):
+    _fields_ = [("n", C.c_double * 3), ("rho_far", C.c_double), ("drho", C.c_double),
+                ("G0", C.c_int32)]
+
+
+class Config(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("D", C.c_int32 * 8), ("paths", C.c_int32),
+                ("variant", C.c_int32), ("p1", C.c_int32), ("p2", C.c_int32),
+                ("adaptive_p2", C.c_int32), ("alpha", C.c_float), ("beta", C.c_float),
+                ("median5", C.c_int32), ("normal_radius", C.c_int32), ("normal_beta", C.c_float),
+                ("rho_deg", C.c_float), ("dmax", C.c_int32)]
+
+
+class SgmParams(C.Structure):
+    _fields_ = [("paths", C.c_int32), ("variant", C.c_int32), ("p1", C.c_int32),
+                ("p2", C.c_int32), ("dmax", C.c_int32), ("p2_lut", C.c_void_p)]
+
+
+_VP = C.c_void_p
+_SIGS = {
+    "fassmvs_config_default": [_VP],
+    "fassmvs_create": [_VP, C.c_int, C.c_size_t, _VP],
+    "fassmvs_destroy": [_VP],
+    "fassmvs_set_config": [_VP, _VP],
+    "fassmvs_set_cameras": [_VP, _VP, C.c_int, _VP, _VP, _VP],
+    "fassmvs_estimate": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP],
+    "fassmvs_pyramid_down": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
+    "fassmvs_census": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
+    "fassmvs_cost_volume": [_VP, _VP, _VP, C.c_int, _VP, C.c_int, C.c_int, _VP, _VP, _VP, _VP,
+                            C.c_double, C.c_double, C.c_int, _VP, C.c_int, C.c_int, _VP, _VP],
+    "fassmvs_sgm_aggregate": [_VP, _VP, _VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP,
+                              _VP, _VP],
+    "fassmvs_wta_refine": [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double,
+                           C.c_double, C.c_int, _VP, _VP, _VP],
+    "fassmvs_median5": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
+    "fassmvs_normals": [_VP, _VP, _VP, C.c_int, C.c_int, _VP, C.c_int, C.c_float, _VP, _VP, _VP,
+                        C.c_float, _VP, _VP],
+    "fassmvs_window": [_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double,
+                       C.c_double, C.c_int, C.c_int, _VP, _VP],
+    "fassmvs_dsn": [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, C.c_double, C.c_int,
+                    _VP, _VP],
+    "fassmvs_profile_enable": [_VP, C.c_int],
+    "fassmvs_profile_read": [_VP, _VP, _VP, C.c_int],
+    "fassmvs_sync": [_VP],
+    "fassmvs_last_error": [_VP],
+    "fassmvs_launch_count": [_VP],
+}
+EXPORTS = tuple(_SIGS)
+
+
+def lib():
+    """Load the in-tree library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libfassmvs.so is not built; run paper_2112_00821_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.fassmvs_destroy.restype = None
+        L.fassmvs_last_error.restype = C.c_char_p
+        L.fassmvs_launch_count.restype = C.c_uint64
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dbl(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    if n is not None and a.size != n:
+        raise ValueError("expected %d values" % n)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+def default_config(**kw):
+    c = Config()
+    lib().fassmvs_config_default(C.byref(c))
+    for k, v in kw.items():
+        if k == "D":
+            v = list(v) + [256] * (8 - len(v))
+            c.D = (C.c_int32 * 8)(*v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+class Context:
+    """A fassmvs_ctx on one CUDA device (torch's current device by default)."""
+
+    def __init__(self, cfg=None, device=None, mem_budget=0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("fassmvs needs a CUDA device; there is no CPU fallback")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._h = C.c_void_p()
+        cfg = cfg if cfg is not None else default_config()
+        self._check(lib().fassmvs_create(C.byref(cfg), self.device, mem_budget, C.byref(self._h)),
+                    ctx=False)
+
+    def close(self):
+        if self._h:
+            lib().fassmvs_destroy(self._h)
+            self._h = C.c_void_p()
+
+    __del__ = close
+
+    def _check(self, st, ctx=True):
+        if st != OK:
+            msg = lib().fassmvs_last_error(self._h if ctx else None)
+            raise FassmvsError(st, (msg or b"").decode())
+
+    # ------------------------------------------------------------ full path
+    def set_config(self, cfg):
+        self._check(lib().fassmvs_set_config(self._h, C.byref(cfg)))
+
+    def set_cameras(self, K, R, t, side):
+        R = np.asarray(R, dtype=np.float64)
+        V = R.shape[0]
+        k_, kp = _dbl(K, 9)
+        r_, rp = _dbl(R, 9 * V)
+        t_, tp = _dbl(t, 3 * V)
+        s_ = np.ascontiguousarray(side, dtype=np.int8)
+        self._check(lib().fassmvs_set_cameras(self._h, kp, V, rp, tp, s_.ctypes.data_as(C.c_void_p)))
+
+    def estimate(self, ref, nbrs, planes, depth=None, normal=None, conf=None):
+        import torch
+        H, W = ref.shape
+        pitch = ref.stride(0)
+        for x in nbrs:
+            if x.shape != ref.shape or x.stride(0) != pitch or x.dtype != torch.uint8:
+                raise ValueError("neighbours must match the reference layout")
+        dev = ref.device
+        depth = depth if depth is not None else torch.empty((H, W), dtype=torch.float32, device=dev)
+        normal = normal if normal is not None else torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        conf = conf if conf is not None else torch.empty((H, W), dtype=torch.float32, device=dev)
+        arr = (C.c_void_p * len(nbrs))(*[x.data_ptr() for x in nbrs])
+        self._check(lib().fassmvs_estimate(self._h, _ptr(ref), W, H, pitch, arr, len(nbrs),
+                                           C.byref(planes), _ptr(depth), _ptr(normal), _ptr(conf),
+                                           _stream()))
+        return depth, normal, conf
+
+    def sync(self):
+        self._check(lib().fassmvs_sync(self._h))
+
+    STAGES = ("pyramid", "census", "cost", "sgm", "wta", "median", "normals", "window")
+
+    def profile(self, on=True):
+        self._check(lib().fassmvs_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset=True):
+        """{stage: (total ms, stage launches)} accumulated since the last reset."""
+        ms = (C.c_double * 8)()
+        cnt = (C.c_uint64 * 8)()
+        self._check(lib().fassmvs_profile_read(self._h, ms, cnt, 1 if reset else 0))
+        return {n: (ms[i], int(cnt[i])) for i, n in enumerate(self.STAGES)}
+
+    @staticmethod
+    def launch_count():
+        return int(lib().fassmvs_launch_count(None))
+
+    # ------------------------------------------------------------ stages
+    def pyramid_down(self, img, out=None):
+        import torch
+        H, W = img.shape
+        out = out if out is not None else torch.empty(((H + 1) // 2, (W + 1) // 2), dtype=torch.uint8,
+                                                      device=img.device)
+        self._check(lib().fassmvs_pyramid_down(self._h, _ptr(img), W, H, _ptr(out), _stream()))
+        return out
+
+    def census(self, img, out=None):
+        import torch
+        H, W = img.shape
+        out = out if out is not None else torch.empty((H, W), dtype=torch.int64, device=img.device)
+        self._check(lib().fassmvs_census(self._h, _ptr(img), W, H, _ptr(out), _stream()))
+        return out
+
+    def cost_volume(self, ref, nbrs, side, K, R, t, n, rho0, drho, G, lo=None, D=None, Ds=None,
+                    out=None):
+        import torch
+        H, W = ref.shape
+        D = G if D is None else D
+        Ds = ((D + 7) // 8) * 8 if Ds is None else Ds
+        V = len(nbrs)
+        out = out if out is not None else torch.zeros((H, W, Ds), dtype=torch.int16, device=ref.device)
+        arr = (C.c_void_p * V)(*[x.data_ptr() for x in nbrs])
+        s_ = np.ascontiguousarray(side, dtype=np.int8)
+        k_, kp = _dbl(K, 9)
+        r_, rp = _dbl(R, 9 * V)
+        t_, tp = _dbl(t, 3 * V)
+        n_, npp = _dbl(n, 3)
+        self._check(lib().fassmvs_cost_volume(self._h, _ptr(ref), arr, V, s_.ctypes.data_as(C.c_void_p),
+                                              W, H, kp, rp, tp, npp, rho0, drho, int(G), _ptr(lo),
+                                              int(D), int(Ds), _ptr(out), _stream()))
+        return out
+
+    def sgm_aggregate(self, S, D, p1, p2=0, lut=None, lo=None, dI=None, img=None, paths=8,
+                      variant=0, dmax=8, out=None):
+        import torch
+        H, W, Ds = S.shape
+        out = out if out is not None else torch.zeros_like(S)
+        lut_a = None
+        if lut is not None:
+            lut_a = np.ascontiguousarray(lut, dtype=np.uint16)
+        prm = SgmParams(paths, variant, int(p1), int(p2), int(dmax),
+                        None if lut_a is None else lut_a.ctypes.data)
+        self._check(lib().fassmvs_sgm_aggregate(self._h, _ptr(S), _ptr(lo), _ptr(dI), _ptr(img), W, H,
+                                                int(D), Ds, C.byref(prm), _ptr(out), _stream()))
+        return out
+
+    def wta_refine(self, Sbar, D, K, n, rho0, drho, G, lo=None):
+        import torch
+        H, W, Ds = Sbar.shape
+        depth = torch.empty((H, W), dtype=torch.float32, device=Sbar.device)
+        gwin = torch.empty((H, W), dtype=torch.int32, device=Sbar.device)
+        k_, kp = _dbl(K, 9)
+        n_, npp = _dbl(n, 3)
+        self._check(lib().fassmvs_wta_refine(self._h, _ptr(Sbar), _ptr(lo), W, H, int(D), Ds, kp, npp,
+                                             rho0, drho, int(G), _ptr(depth), _ptr(gwin), _stream()))
+        return depth, gwin
+
+    def median5(self, d):
+        import torch
+        H, W = d.shape
+        out = torch.empty_like(d)
+        self._check(lib().fassmvs_median5(self._h, _ptr(d), W, H, _ptr(out), _stream()))
+        return out
+
+    def normals(self, depth, img, K, radius=2, beta=10.0, n_plane=(0.0, 0.0, -1.0), rho_deg=60.0,
+                with_conf=True):
+        import torch
+        H, W = depth.shape
+        normal = torch.empty((H, W, 3), dtype=torch.float32, device=depth.device)
+        raw = torch.empty((H, W, 3), dtype=torch.float32, device=depth.device)
+        conf = torch.empty((H, W), dtype=torch.float32, device=depth.device) if with_conf else None
+        k_, kp = _dbl(K, 9)
+        n_, npp = _dbl(n_plane, 3)
+        self._check(lib().fassmvs_normals(self._h, _ptr(depth), _ptr(img), W, H, kp, int(radius),
+                                          float(beta), _ptr(normal), _ptr(raw), npp, float(rho_deg),
+                                          _ptr(conf), _stream()))
+        return normal, raw, conf
+
+    def window(self, dc, W, H, K, n, rho0, drho, G, D):
+        import torch
+        Hc, Wc = dc.shape
+        lo = torch.empty((H, W), dtype=torch.int32, device=dc.device)
+        k_, kp = _dbl(K, 9)
+        n_, npp = _dbl(n, 3)
+        self._check(lib().fassmvs_window(self._h, _ptr(dc), Wc, Hc, W, H, kp, npp, rho0, drho, int(G),
+                                         int(D), _ptr(lo), _stream()))
+        return lo
+
+    def dsn(self, dc, nc, W, H, K, drho, dmax=8):
+        import torch
+        Hc, Wc = dc.shape
+        out = torch.empty((8, H, W), dtype=torch.int8, device=dc.device)
+        k_, kp = _dbl(K, 9)
+        self._check(lib().fassmvs_dsn(self._h, _ptr(dc), _ptr(nc), Wc, Hc, W, H, kp, drho, int(dmax),
+                                      _ptr(out), _stream()))
+        return out
+
+
+def planes_of(scene):
+    """fassmvs_planes of a synth.Scene."""
+    p = Planes()
+    p.n = (C.c_double * 3)(*[float(v) for v in scene.plane_n])
+    p.rho_far = float(scene.rho_far)
+    p.drho = float(scene.drho)
+    p.G0 = int(scene.G0)
+    return p
+
