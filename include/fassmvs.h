@@ -183,6 +183,27 @@ FASSMVS_API fassmvs_status fassmvs_wta_refine(fassmvs_ctx* ctx, const uint16_t* 
                                   double rho0, double drho, int G, float* depth, int32_t* gwin,
                                   void* stream);
 
+/* The same winner-takes-all and refinement as fassmvs_wta_refine, for callers
+ * that cannot allocate device memory: loops that must not call cudaMalloc
+ * once running (it can synchronize the device and its latency is unbounded),
+ * and processes whose device memory is already reserved by another allocator,
+ * so that cudaMalloc would fail although the caller's buffers are valid.  It
+ * takes no context and allocates nothing.  The plane-distance table it needs
+ * lives in one static device array of FASSMVS_NOALLOC_MAX_PLANES floats
+ * (16 KB, held by every device that loads the library until the process
+ * exits); G beyond that limit returns FASSMVS_EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's table: calls that overlap on
+ * the GPU (on different streams) race on it.  Runs on the current device.
+ * The paper has no counterpart of this entry point. */
+#define FASSMVS_NOALLOC_MAX_PLANES 4096
+FASSMVS_API fassmvs_status fassmvs_wta_refine_noalloc(const uint16_t* Sbar, const int32_t* lo, int W,
+                                                      int H, int D, int Ds, const double K[9],
+                                                      const double n[3], double rho0, double drho,
+                                                      int G, float* depth, int32_t* gwin,
+                                                      void* stream);
+
 /* 5x5 median (Sec. 2.1), clamp-to-edge. */
 FASSMVS_API fassmvs_status fassmvs_median5(fassmvs_ctx* ctx, const float* in, int W, int H, float* out,
                                void* stream);

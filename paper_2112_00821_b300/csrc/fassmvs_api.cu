@@ -61,6 +61,12 @@ fassmvs_status fail(fassmvs_ctx* c, fassmvs_status s, const char* fmt, ...)
     return s;
 }
 
+}  // namespace
+
+void fm::set_error(const char* msg) { t_err = msg; }
+
+namespace {
+
 fassmvs_status cuda_check(fassmvs_ctx* c, cudaError_t e, const char* what)
 {
     if (e == cudaSuccess) return FASSMVS_OK;

@@ -88,6 +88,9 @@ void launch_window(const float* dc, int Wc, int Hc, int W, int H, Intr K, const 
 void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, Intr K,
                 float drho, int dmax, int8_t* dI, cudaStream_t st);
 
+// Records the thread-local error text returned by fassmvs_last_error(NULL).
+void set_error(const char* msg);
+
 // Counts kernel launches issued by this library (process-wide).
 uint64_t launches();
 void count_launch(int n = 1);

@@ -7,6 +7,9 @@
 // cost volume and the aggregation.
 #include <math.h>
 
+#include <mutex>
+
+#include "../../include/fassmvs.h"
 #include "fm_internal.cuh"
 
 namespace fm {
@@ -347,3 +350,63 @@ void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, 
 }
 
 }  // namespace fm
+
+// ---------------------------------------------------------------- no-alloc WTA
+// Plane-distance table of fassmvs_wta_refine_noalloc: one static device array
+// shared by every call (see the header for the contract).
+namespace {
+static __device__ __align__(256) float g_noalloc_delta[FASSMVS_NOALLOC_MAX_PLANES];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+
+// device address of the table on the current device, looked up once per device
+cudaError_t noalloc_table(int dev, float** out)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_delta);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+fassmvs_status noalloc_fail(fassmvs_status s, const char* msg)
+{
+    fm::set_error(msg);
+    return s;
+}
+}  // namespace
+
+extern "C" fassmvs_status fassmvs_wta_refine_noalloc(const uint16_t* Sbar, const int32_t* lo, int W, int H,
+                                                     int D, int Ds, const double K[9], const double n[3],
+                                                     double rho0, double drho, int G, float* depth,
+                                                     int32_t* gwin, void* stream)
+{
+    if (!Sbar || !K || !n || !depth || W < 1 || H < 1)
+        return noalloc_fail(FASSMVS_EINVAL, "bad WTA arguments");
+    if (D < 1 || D > fm::kMaxSlots || Ds < D || (Ds & 7) || G < D)
+        return noalloc_fail(FASSMVS_EINVAL, "bad D / Ds / G");
+    if (G > FASSMVS_NOALLOC_MAX_PLANES)
+        return noalloc_fail(FASSMVS_EINVAL, "G exceeds the static plane table of the no-alloc entry point (4096)");
+    if (reinterpret_cast<uintptr_t>(Sbar) & 15)
+        return noalloc_fail(FASSMVS_EINVAL, "volume must be 16-byte aligned");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return noalloc_fail(FASSMVS_ECUDA, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FASSMVS_EINVAL, "device index beyond 63");
+    float* table = nullptr;
+    e = noalloc_table(dev, &table);
+    if (e != cudaSuccess) return noalloc_fail(FASSMVS_ECUDA, cudaGetErrorString(e));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    fm::launch_delta_table(rho0, drho, G, table, st);
+    float nf[3] = {(float)n[0], (float)n[1], (float)n[2]};
+    fm::Intr ki{(float)K[0], (float)K[4], (float)K[2], (float)K[5]};
+    fm::launch_wta_refine(Sbar, lo, W, H, D, Ds, table, ki, nf, depth, gwin, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return noalloc_fail(FASSMVS_ECUDA, cudaGetErrorString(e));
+    return FASSMVS_OK;
+}

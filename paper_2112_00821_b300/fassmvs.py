@@ -60,6 +60,8 @@ _SIGS = {
                               _VP, _VP],
     "fassmvs_wta_refine": [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double,
                            C.c_double, C.c_int, _VP, _VP, _VP],
+    "fassmvs_wta_refine_noalloc": [_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double,
+                                   C.c_double, C.c_int, _VP, _VP, _VP],
     "fassmvs_median5": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
     "fassmvs_normals": [_VP, _VP, _VP, C.c_int, C.c_int, _VP, C.c_int, C.c_float, _VP, _VP, _VP,
                         C.c_float, _VP, _VP],
@@ -295,6 +297,23 @@ class Context:
         self._check(lib().fassmvs_dsn(self._h, _ptr(dc), _ptr(nc), Wc, Hc, W, H, kp, drho, int(dmax),
                                       _ptr(out), _stream()))
         return out
+
+
+def wta_refine_noalloc(Sbar, D, K, n, rho0, drho, G, lo=None, depth=None, gwin=None):
+    """fassmvs_wta_refine_noalloc on the current device: no context and no
+    device allocation inside the library (pass depth / gwin to avoid torch
+    allocating them here)."""
+    import torch
+    H, W, Ds = Sbar.shape
+    depth = depth if depth is not None else torch.empty((H, W), dtype=torch.float32, device=Sbar.device)
+    gwin = gwin if gwin is not None else torch.empty((H, W), dtype=torch.int32, device=Sbar.device)
+    k_, kp = _dbl(K, 9)
+    n_, npp = _dbl(n, 3)
+    st = lib().fassmvs_wta_refine_noalloc(_ptr(Sbar), _ptr(lo), W, H, int(D), Ds, kp, npp, rho0, drho,
+                                          int(G), _ptr(depth), _ptr(gwin), _stream())
+    if st != OK:
+        raise FassmvsError(st, (lib().fassmvs_last_error(None) or b"").decode())
+    return depth, gwin
 
 
 def planes_of(scene):

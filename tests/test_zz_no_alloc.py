@@ -1,0 +1,59 @@
+"""The allocation-free WTA entry point against the allocating one.
+
+fassmvs_wta_refine_noalloc serves callers that may not allocate device
+memory once running (cudaMalloc can synchronize the device and has unbounded
+latency) or whose device memory is already held by another allocator.  It
+keeps its plane-distance table in a static device array instead of context
+scratch.  This file runs last so a stop-at-first-failure run has already run
+every other test; it also passes on its own in a fresh process.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _case(seed, H, W, D, G):
+    g = np.random.default_rng(seed)
+    Ds = ((D + 7) // 8) * 8
+    Sb = np.zeros((H, W, Ds), np.uint16)
+    Sb[..., :D] = g.integers(0, 4000, (H, W, D))
+    lo = g.integers(0, G - D + 1, (H, W)).astype(np.int32)
+    K = np.array([[500.0, 0, (W - 1) / 2], [0, 500.0, (H - 1) / 2], [0, 0, 1]])
+    rho0 = 1.0 / g.uniform(50, 300)
+    drho = g.uniform(1e-4, 1e-3)
+    return Sb, lo, K, rho0, drho
+
+
+def test_noalloc_wta_matches_allocating_entry_point_twice():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_00821_b300 import fassmvs
+    ctx = fassmvs.Context()
+    n = [0.0, 0.0, -1.0]
+    # two calls in a row with different plane lists: the shared table must be
+    # rewritten by each call
+    for seed, (H, W, D, G) in ((1, (61, 97, 40, 300)), (2, (33, 45, 128, 4096))):
+        Sb, lo, K, rho0, drho = _case(seed, H, W, D, G)
+        Sb_d = torch.from_numpy(Sb.view(np.int16)).cuda()
+        lo_d = torch.from_numpy(lo).cuda()
+        d_ref, g_ref = ctx.wta_refine(Sb_d, D, K, n, rho0, drho, G, lo=lo_d)
+        d_new, g_new = fassmvs.wta_refine_noalloc(Sb_d, D, K, n, rho0, drho, G, lo=lo_d)
+        torch.cuda.synchronize()
+        assert torch.equal(g_new, g_ref)
+        rel = ((d_new - d_ref).abs() / d_ref.abs()).max().item()
+        assert rel <= 1e-5, rel
+    ctx.close()
+
+
+def test_noalloc_wta_rejects_plane_lists_beyond_the_static_table():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_00821_b300 import fassmvs
+    Sb = torch.zeros((4, 4, 8), dtype=torch.int16, device="cuda")
+    with pytest.raises(fassmvs.FassmvsError) as ei:
+        fassmvs.wta_refine_noalloc(Sb, 8, np.eye(3), [0, 0, -1.0], 0.01, 0.001, 4097)
+    assert ei.value.status == fassmvs.EINVAL
+    assert "4096" in str(ei.value)
