@@ -172,11 +172,12 @@ OR_EXPORT void or_homography(const double K[9], const double R[9], const double 
 /* the reference view is the same as sampling I_k at H q for every q of the */
 /* reference support window.  Reading of the sampling                       */
 /* (the paper does not fix it): positions are taken on a 1/256-pixel grid,  */
-/* P = floor(256 u) (as GPU texture units quantise bilinear weights), and    */
-/* the bilinear blend is exact integer arithmetic with 8-bit weights, giving */
-/* a value in [0, 255 * 65536].  Positions are clamped to the image (clamp-  */
-/* to-edge).  A point behind the neighbour camera (homogeneous w <= 0) is    */
-/* treated as lying at (-inf, -inf).                                         */
+/* P = floor(256 u) (as GPU texture units quantise bilinear weights), the    */
+/* bilinear blend is exact integer arithmetic with 8-bit weights, and the    */
+/* blended value is kept at 1/16 grey level, rounded half up:               */
+/* V = (blend + 2048) >> 12, in [0, 4080].  Positions are clamped to the    */
+/* image (clamp-to-edge).  A point behind the neighbour camera (homogeneous */
+/* w <= 0) is treated as lying at (-inf, -inf).                             */
 /* ------------------------------------------------------------------------ */
 #define OR_PMAX (1 << 24)
 
@@ -213,7 +214,7 @@ static int32_t bilinear_fix(const uint8_t* img, int W, int H, int64_t Pu, int64_
     const uint8_t* r1 = r0 + W;
     int32_t top = r0[0] * (256 - A) + r0[1] * A;
     int32_t bot = r1[0] * (256 - A) + r1[1] * A;
-    return top * (256 - B) + bot * B;
+    return (top * (256 - B) + bot * B + 2048) >> 12;
 }
 
 /* value of the warped neighbour at reference pixel (x, y); *valid tells

@@ -136,17 +136,23 @@ def test_homography_identity_and_stereo_normal_case(orc):
 def test_warp_identity_integer_and_half_shifts(orc):
     g = np.random.default_rng(5)
     img = g.integers(0, 256, (20, 30), dtype=np.uint8)
+    # warped values are kept at 1/16 grey level
     w, val = orc.warp_image(img, np.eye(3))
-    assert val.all() and np.array_equal(w, img.astype(np.int32) * 65536)
+    assert val.all() and np.array_equal(w, img.astype(np.int32) * 16)
     T = np.array([[1, 0, 2.0], [0, 1, -1.0], [0, 0, 1]])
     w, val = orc.warp_image(img, T)
-    exp = img[:-1, 2:].astype(np.int32) * 65536           # value at (x+2, y-1)
+    exp = img[:-1, 2:].astype(np.int32) * 16              # value at (x+2, y-1)
     assert np.array_equal(w[1:, :-2], exp)
     assert val[1:, :-2].all() and not val[0].any() and not val[:, -2:].any()
     Th = np.array([[1, 0, 0.5], [0, 1, 0.0], [0, 0, 1]])
     w, _ = orc.warp_image(img, Th)
-    exp = (img[:, :-1].astype(np.int32) + img[:, 1:]) * 128 * 256
+    exp = (img[:, :-1].astype(np.int32) + img[:, 1:]) * 8
     assert np.array_equal(w[:, :-1], exp)
+    # a quarter-pixel shift rounds (3 a + b) / 4 * 16 = 12 a + 4 b exactly
+    Tq = np.array([[1, 0, 0.25], [0, 1, 0.0], [0, 0, 1]])
+    w, _ = orc.warp_image(img, Tq)
+    a32 = img.astype(np.int32)
+    assert np.array_equal(w[:, :-1], 12 * a32[:, :-1] + 4 * a32[:, 1:])
 
 
 def test_warp_bilinear_exact_on_ramp(orc):
@@ -163,7 +169,8 @@ def test_warp_bilinear_exact_on_ramp(orc):
             u = A[0] @ [x, y, 1]
             v = A[1] @ [x, y, 1]
             Pu, Pv = math.floor(256 * u), math.floor(256 * v)
-            assert w[y, x] == 256 * (5 * Pu + 3 * Pv)
+            # blend = 256 (5 Pu + 3 Pv); kept at 1/16 grey level, half up
+            assert w[y, x] == (256 * (5 * Pu + 3 * Pv) + 2048) >> 12
 
 
 # ---------------------------------------------------------------- left/right
