@@ -1,29 +1,51 @@
 // Plane-sweep census cost volume (Alg. 1 of FaSS-MVS) for sm_103a.
 //
-// One CTA owns a 32 x 8 tile of reference pixels and walks the planes its
-// windows need, eight planes per batch (one warp per plane).  For each view
-// the eight warped 40 x 14 sample tiles (tile + census halo) are produced
-// into shared memory, then every warp builds the 9x7 census strings of its
-// plane for the 8 pixels of its lane's column, XORs them with the reference
-// census and accumulates the left / right subset sums in registers.
-//
-// Sampling reading (shared with the oracle, stated in the header): the
-// homography is evaluated in double-float arithmetic (two FP32 words) so the
-// 1/256-pixel fixed-point position floor(256 u) agrees with an FP64
-// evaluation except within ~1e-10 px of a grid line; the bilinear blend is
-// exact integer arithmetic with 8-bit weights.
+// A CTA of 8 warps owns a 56 x 52 tile of reference pixels and walks every
+// plane its windows need, one (plane, view) pair per iteration:
+//   1. sampling: the 64 x 58 warped sample tile (tile + 9x7 census halo) is
+//      produced cooperatively -- each warp owns ~7 sample rows, each lane two
+//      sample columns (coalesced neighbour-image reads), the homography is
+//      stepped down the column in double-float arithmetic; samples are stored
+//      as FP16 pairs (V(x), V(x+1)) so the census can load two at a time;
+//   2. one __syncthreads (the sample tile is double-buffered);
+//   3. census: warp w takes a 32-column x 13-row chunk of the tile; for every
+//      window row, five packed FP16 saturating subtractions give ten
+//      comparison bits [V(q) < V(p)] which five packed FMAs add, with
+//      power-of-two weights, into four FP16x2 accumulators (10 bits per half,
+//      biased by 1024 so the half's bit pattern holds the integer); the XOR
+//      with the reference census (pre-arranged in the same layout) and four
+//      popcounts give the Hamming distance; left / right sums accumulate in
+//      registers over the views and the plane's costs are stored after the
+//      last view.
+// Sampling reading (shared with the oracle): 1/256-pixel fixed-point
+// positions floor(256 u), exact integer bilinear blend with 8-bit weights,
+// value kept at 1/16 grey level.  Values lie in [0, 4080]; shifted by -2040
+// they are exact FP16 integers, and the FP16 difference of two of them keeps
+// its sign and its >= 1 test, so the census comparisons are exact.
+#include <cuda_fp16.h>
+
 #include "fm_internal.cuh"
 
 namespace fm {
 
 namespace {
 
-constexpr int TX = 32, TY = 8;          // pixel tile
-constexpr int SX = TX + 8, SY = TY + 6; // sample tile with the 9x7 halo
-constexpr int PB = 8;                   // planes per batch (= warps)
-constexpr int THREADS = 256;
-constexpr int RUN = SX / 2;             // samples per sampling task (one half row)
+constexpr int PW = 56, PH = 52;          // pixel tile
+constexpr int SW = 64, SH = PH + 6;      // sample tile (PW + 8 <= SW)
+constexpr int NWARP = 8, THREADS = 256;
+constexpr int CH = 13;                   // pixel rows per census chunk (PH / 4)
 constexpr int PMAX = 1 << 24;
+constexpr float MAGIC = 12582912.0f;     // 1.5 * 2^23: adding it leaves an integer in the mantissa
+constexpr int MAGIC_BITS = 0x4B400000;
+constexpr uint32_t LAYOUT_MASK = 0x03FF03FFu;
+
+struct SmemCost {
+    uint32_t pair[2][SH][SW];            // FP16x2 (V(x) - 2040, V(x+1) - 2040)
+    uint32_t okm[2][PH][2];              // centre-in-image bit per pixel column
+    uint4 refl[PH][PW];                  // reference census in the accumulator layout
+    int32_t lo[PH][PW];
+    int glo, ghi;
+};
 
 struct df { float hi, lo; };
 
@@ -35,13 +57,25 @@ __device__ __forceinline__ df two_sum(float a, float b)
     return {s, e};
 }
 
+// a + b; the low word is not renormalised (it stays far below the high word
+// over the few dozen steps of a column)
 __device__ __forceinline__ df df_add(df a, df b)
 {
     df s = two_sum(a.hi, b.hi);
-    float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
-    float h = __fadd_rn(s.hi, lo);
-    return {h, __fsub_rn(lo, __fsub_rn(h, s.hi))};
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
 }
+
+// Values whose high word lies on the 2^-10 grid with magnitude below 2^14
+// add exactly in FP32, so stepping down a column costs two additions: the
+// homography is scaled (prep_level_kernel) so that |N|, |D| stay below 2^14
+// over and well around the image, and the step's high words are on the grid.
+constexpr float GRID_MAGIC = 12288.0f;   // 1.5 * 2^13: rounds |x| < 2^12 to the 2^-10 grid
+__device__ __forceinline__ df to_grid(df a)
+{
+    float h = __fsub_rn(__fadd_rn(a.hi, GRID_MAGIC), GRID_MAGIC);
+    return {h, __fadd_rn(a.lo, __fsub_rn(a.hi, h))};
+}
+__device__ __forceinline__ df grid_add(df a, df b) { return {__fadd_rn(a.hi, b.hi), __fadd_rn(a.lo, b.lo)}; }
 
 // a * b for an integer-valued b (|b| < 2^24)
 __device__ __forceinline__ df df_mul_int(df a, float b)
@@ -60,185 +94,236 @@ __device__ __forceinline__ float rcp_approx(float x)
     return r;
 }
 
-// floor(256 * N / Dn) clamped to [-2^24, 2^24], for Dn > 0.  q = N/D to a few
-// ulps, then the residual N - q D in double-float gives the correction.
-__device__ __forceinline__ int fix_pos(df N, df Dn)
+__device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h + i), __ldg(h + 9 + i)}; }
+
+// floor(256 N / D) for D > 0 (r ~ 1/(D.hi + D.lo)), for |N / D| < 16000:
+// q = N/D to a few ulps, the double-float residual N - q D gives the
+// correction, and the floors come from adding 1.5 * 2^23 with round-down.
+// The words of N and D are split on the 2^-10 grid, so the low words are not
+// small: q and r are formed from the summed words.
+__device__ __forceinline__ int fix_pos(df N, df Dn, float r)
 {
-    float r = rcp_approx(Dn.hi);
-    float q = __fmul_rn(N.hi, r);
+    float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
     float e1 = __fmaf_rn(-q, Dn.hi, N.hi);
     float e2 = __fmaf_rn(-q, Dn.lo, N.lo);
     float corr = __fmul_rn(__fadd_rn(e1, e2), r);
-    float a = __fmul_rn(q, 256.0f);
-    a = fminf(fmaxf(a, -17000000.0f), 17000000.0f);
-    float af = floorf(a);
-    float rem = __fadd_rn(__fsub_rn(a, af), __fmul_rn(corr, 256.0f));
-    int P = (int)af + (int)floorf(rem);
-    return min(max(P, -PMAX), PMAX);
+    float a = fminf(fmaxf(__fmul_rn(q, 256.0f), -4194000.0f), 4194000.0f);
+    float t1 = __fadd_rd(a, MAGIC);
+    float fa = __fsub_rn(t1, MAGIC);
+    float rem = __fmaf_rn(corr, 256.0f, __fsub_rn(a, fa));
+    float t2 = __fadd_rd(rem, MAGIC);
+    return __float_as_int(t1) + __float_as_int(t2) - 2 * MAGIC_BITS;
 }
 
-__device__ __forceinline__ df load_df(const float* h, int i) { return {h[i], h[9 + i]}; }
-
-// warped sample value of image img (W x H, pitch) at the fixed-point position
-__device__ __forceinline__ int bilinear_fix(const uint8_t* __restrict__ img, int W, int H, int pitch,
-                                            int Pu, int Pv)
+// one warped sample: FP16-ready value V - 2040 and whether the position lies
+// on the image grid
+template <bool WANT_OK>
+__device__ __forceinline__ float sample(const uint8_t* __restrict__ img, int W, int H, int pitch, df Nu,
+                                        df Nv, df Dn, bool& ok)
 {
-    int cu = min(max(Pu, 0), 256 * (W - 1));
-    int cv = min(max(Pv, 0), 256 * (H - 1));
-    int iu = min(cu >> 8, W - 2);
-    int iv = min(cv >> 8, H - 2);
-    int A = cu - 256 * iu, B = cv - 256 * iv;
+    int Pu = -PMAX, Pv = -PMAX;
+    const bool front = Dn.hi > 0.0f || (Dn.hi == 0.0f && Dn.lo > 0.0f);
+    if (front) {
+        float r = rcp_approx(__fadd_rn(Dn.hi, Dn.lo));
+        Pu = fix_pos(Nu, Dn, r);
+        Pv = fix_pos(Nv, Dn, r);
+    }
+    const int wmax = 256 * (W - 1), hmax = 256 * (H - 1);
+    if (WANT_OK) ok = front && Pu >= 0 && Pu <= wmax && Pv >= 0 && Pv <= hmax;
+    const int cu = min(max(Pu, 0), wmax), cv = min(max(Pv, 0), hmax);
+    const int iu = min(cu >> 8, W - 2), iv = min(cv >> 8, H - 2);
+    const int A = cu - 256 * iu, B = cv - 256 * iv;
     const uint8_t* r0 = img + (size_t)iv * pitch + iu;
-    int i00 = __ldg(r0), i01 = __ldg(r0 + 1);
-    int i10 = __ldg(r0 + pitch), i11 = __ldg(r0 + pitch + 1);
-    int top = i00 * (256 - A) + i01 * A;
-    int bot = i10 * (256 - A) + i11 * A;
-    return top * (256 - B) + bot * B;
+    const int i00 = __ldg(r0), i01 = __ldg(r0 + 1);
+    const int i10 = __ldg(r0 + pitch), i11 = __ldg(r0 + pitch + 1);
+    const int top = (i00 << 8) + A * (i01 - i00);
+    const int bot = (i10 << 8) + A * (i11 - i10);
+    const int v16 = ((top << 8) + B * (bot - top) + 2048) >> 12;     // [0, 4080]
+    return __int_as_float(MAGIC_BITS + v16) - (MAGIC + 2040.0f);
 }
 
-__global__ void __launch_bounds__(THREADS, 2)
-cost_kernel(const CostArgs a)
+// canonical 9x7 census word -> four accumulator words: window row dy, pair p
+// (columns 2p, 2p+1) is packed-FMA number m = 5 dy + p, which lands in word
+// m / 10 at bit m % 10 of the low (even column) / high (odd column) half
+__device__ __forceinline__ uint4 to_layout(uint64_t c)
 {
-    __shared__ int32_t sV[PB][SY][SX];
-    __shared__ uint8_t sOk[PB][TY][TX];
-    __shared__ int s_glo, s_ghi;
+    uint32_t w[4];
+#pragma unroll
+    for (int R = 0; R < 4; ++R) {
+        uint32_t v = 0x64006400u;
+#pragma unroll
+        for (int b = 0; b < 10; ++b) {
+            const int m = 10 * R + b;
+            if (m >= 35) break;
+            const int dy = m / 5, p = m % 5;
+            v |= (uint32_t)((c >> (dy * 9 + 2 * p)) & 1u) << b;
+            if (2 * p + 1 <= 8) v |= (uint32_t)((c >> (dy * 9 + 2 * p + 1)) & 1u) << (16 + b);
+        }
+        w[R] = v;
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
 
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+__device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
+__device__ __forceinline__ uint32_t as_u32(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+
+__global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx0 = blockIdx.x * PW, ty0 = blockIdx.y * PH;
     const int W = a.W, H = a.H;
 
-    // plane range needed by this tile: union of [lo_p, lo_p + D)
-    if (tid == 0) { s_glo = a.G; s_ghi = 0; }
+    if (tid == 0) { sm.glo = a.G; sm.ghi = 0; }
     __syncthreads();
-    {
-        int px = tx0 + (tid & 31), py = ty0 + (tid >> 5);
-        if (px < W && py < H) {
-            int l = a.lo ? a.lo[(size_t)py * W + px] : 0;
-            atomicMin(&s_glo, l);
-            atomicMax(&s_ghi, l + a.D);
+    for (int i = tid; i < PH * PW; i += THREADS) {
+        const int r = i / PW, c = i % PW;
+        const int px = tx0 + c, py = ty0 + r;
+        const bool in = px < W && py < H;
+        const int l = in ? (a.lo ? a.lo[(size_t)py * W + px] : 0) : (1 << 30);
+        sm.lo[r][c] = l;
+        if (in) {
+            atomicMin(&sm.glo, l);
+            atomicMax(&sm.ghi, l + a.D);
         }
+        sm.refl[r][c] = to_layout(in ? a.cref[(size_t)py * W + px] : 0ull);
     }
     __syncthreads();
-    const int glo = max(s_glo, 0), ghi = min(s_ghi, a.G);   // guards against an out-of-range window map
+    // planes of this tile (guarded against an out-of-range window map), split
+    // into gridDim.z consecutive chunks
+    const int tlo = max(sm.glo, 0), thi = min(sm.ghi, a.G);
+    const int chunk = (thi - tlo + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int glo = tlo + (int)blockIdx.z * chunk, ghi = min(thi, glo + chunk);
 
-    // this lane's column of 8 pixels: reference census and windows
-    const int px = tx0 + lane;
-    uint32_t rlo[TY], rhi[TY];
-    int plo[TY];
+    // census role: columns cp*32 + lane, rows rc*13 .. rc*13 + 12
+    const int pc = (warp & 1) * 32 + lane;
+    const int pr0 = (warp >> 1) * CH;
+    const bool cact = pc < PW;
+    // sampling role: sample rows [rs, re), sample columns lane and 32 + lane
+    const int rs = (SH * warp) / NWARP, re = (SH * (warp + 1)) / NWARP;
+    const int X0 = min(max(tx0 - 4 + lane, 0), W - 1);
+    const int X1 = min(max(tx0 + 28 + lane, 0), W - 1);
+
+    int buf = 0;
+    for (int g = glo; g < ghi; ++g) {
+        uint32_t slr[CH];
 #pragma unroll
-    for (int r = 0; r < TY; ++r) {
-        int py = ty0 + r;
-        bool in = px < W && py < H;
-        uint64_t c = in ? a.cref[(size_t)py * W + px] : 0ull;
-        rlo[r] = (uint32_t)c;
-        rhi[r] = (uint32_t)(c >> 32);
-        plo[r] = in ? (a.lo ? a.lo[(size_t)py * W + px] : 0) : (1 << 30);
-    }
-
-    for (int g0 = glo; g0 < ghi; g0 += PB) {
-        uint32_t acc[TY];   // left sum in the low half, right sum in the high half
-#pragma unroll
-        for (int r = 0; r < TY; ++r) acc[r] = 0;
-
+        for (int r = 0; r < CH; ++r) slr[r] = 0;
         for (int k = 0; k < a.V; ++k) {
-            // ---- sampling: 8 planes x 14 rows x 2 half rows = 224 tasks
-            if (tid < PB * SY * 2) {
-                const int b = tid / (SY * 2);
-                const int row = (tid % (SY * 2)) >> 1;
-                const int half = tid & 1;
-                const int g = g0 + b;
-                if (g < ghi) {
-                    const float* h = a.htab + ((size_t)g * a.V + k) * 18;
-                    const int y = min(max(ty0 - 3 + row, 0), H - 1);
-                    const int xs = tx0 - 4 + half * RUN;
-                    int xc = min(max(xs, 0), W - 1);
-                    const float fx = (float)xc, fy = (float)y;
-                    df Nu = df_add(df_add(df_mul_int(load_df(h, 0), fx), df_mul_int(load_df(h, 1), fy)), load_df(h, 2));
-                    df Nv = df_add(df_add(df_mul_int(load_df(h, 3), fx), df_mul_int(load_df(h, 4), fy)), load_df(h, 5));
-                    df Dn = df_add(df_add(df_mul_int(load_df(h, 6), fx), df_mul_int(load_df(h, 7), fy)), load_df(h, 8));
-                    const df h0 = load_df(h, 0), h3 = load_df(h, 3), h6 = load_df(h, 6);
-                    const uint8_t* img = a.views.img[k];
-#pragma unroll 4
-                    for (int j = 0; j < RUN; ++j) {
-                        int x = xs + j;
-                        if (j > 0 && x >= 1 && x <= W - 1) {
-                            Nu = df_add(Nu, h0);
-                            Nv = df_add(Nv, h3);
-                            Dn = df_add(Dn, h6);
-                        }
-                        bool front = Dn.hi > 0.0f || (Dn.hi == 0.0f && Dn.lo > 0.0f);
-                        int Pu = -PMAX, Pv = -PMAX;
-                        if (front) {
-                            Pu = fix_pos(Nu, Dn);
-                            Pv = fix_pos(Nv, Dn);
-                        }
-                        const int sx = half * RUN + j;
-                        sV[b][row][sx] = bilinear_fix(img, W, H, a.pitch, Pu, Pv);
-                        if (row >= 3 && row < 3 + TY && sx >= 4 && sx < 4 + TX) {
-                            bool ok = front && Pu >= 0 && Pu <= 256 * (W - 1) && Pv >= 0 &&
-                                      Pv <= 256 * (H - 1);
-                            sOk[b][row - 3][sx - 4] = ok;
+            // ---------------------------------------------------------- sampling
+            {
+                const float* h = a.htab + ((size_t)g * a.V + k) * 18;
+                const uint8_t* img = a.views.img[k];
+                const df h0 = load_df(h, 0), h1 = load_df(h, 1), h2 = load_df(h, 2);
+                const df h3 = load_df(h, 3), h4 = load_df(h, 4), h5 = load_df(h, 5);
+                const df h6 = load_df(h, 6), h7 = load_df(h, 7), h8 = load_df(h, 8);
+                const float fy = (float)min(max(ty0 - 3 + rs, 0), H - 1);
+                const float fx0 = (float)X0, fx1 = (float)X1;
+                const df by_u = df_add(df_mul_int(h1, fy), h2);
+                const df by_v = df_add(df_mul_int(h4, fy), h5);
+                const df by_d = df_add(df_mul_int(h7, fy), h8);
+                df u0 = to_grid(df_add(df_mul_int(h0, fx0), by_u)), v0 = to_grid(df_add(df_mul_int(h3, fx0), by_v));
+                df d0 = to_grid(df_add(df_mul_int(h6, fx0), by_d));
+                df u1 = to_grid(df_add(df_mul_int(h0, fx1), by_u)), v1 = to_grid(df_add(df_mul_int(h3, fx1), by_v));
+                df d1 = to_grid(df_add(df_mul_int(h6, fx1), by_d));
+                const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
+                uint32_t(*prow)[SW] = sm.pair[buf];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = rs + jj;
+                    if (j >= re) break;
+                    const int Y = ty0 - 3 + j;
+                    if (jj > 0 && Y >= 1 && Y <= H - 1) {
+                        u0 = grid_add(u0, s1); v0 = grid_add(v0, s4); d0 = grid_add(d0, s7);
+                        u1 = grid_add(u1, s1); v1 = grid_add(v1, s4); d1 = grid_add(d1, s7);
+                    }
+                    bool ok0 = false, ok1 = false;
+                    const bool centre_row = j >= 3 && j < 3 + PH;
+                    float q0, q1;
+                    if (centre_row) {
+                        q0 = sample<true>(img, W, H, a.pitch, u0, v0, d0, ok0);
+                        q1 = sample<true>(img, W, H, a.pitch, u1, v1, d1, ok1);
+                    } else {
+                        q0 = sample<false>(img, W, H, a.pitch, u0, v0, d0, ok0);
+                        q1 = sample<false>(img, W, H, a.pitch, u1, v1, d1, ok1);
+                    }
+                    float n0 = __shfl_sync(0xFFFFFFFFu, q0, (lane + 1) & 31);
+                    const float t1 = __shfl_sync(0xFFFFFFFFu, q1, 0);
+                    float n1 = __shfl_sync(0xFFFFFFFFu, q1, (lane + 1) & 31);
+                    if (lane == 31) { n0 = t1; n1 = 0.0f; }
+                    prow[j][lane] = as_u32(__floats2half2_rn(q0, n0));
+                    prow[j][32 + lane] = as_u32(__floats2half2_rn(q1, n1));
+                    if (centre_row) {
+                        const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, ok0);
+                        const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, ok1);
+                        if (lane == 0) {
+                            sm.okm[buf][j - 3][0] = (m0 >> 4) | (m1 << 28);
+                            sm.okm[buf][j - 3][1] = m1 >> 4;
                         }
                     }
                 }
             }
             __syncthreads();
-
-            // ---- census + Hamming: warp = plane, lane = column, 8 pixels
-            const int g = g0 + warp;
-            if (g < ghi) {
-                uint32_t cen[TY], blo[TY], bhi[TY];
+            // ---------------------------------------------------------- census
+            if (cact) {
+                const uint32_t* base = &sm.pair[buf][pr0][pc];
+                __half2 cen[CH];
+                __half2 acc[CH][4];
+                const __half2 bias = __floats2half2_rn(1024.0f, 1024.0f);
 #pragma unroll
-                for (int r = 0; r < TY; ++r) {
-                    cen[r] = (uint32_t)sV[warp][r + 3][lane + 4];
-                    blo[r] = 0;
-                    bhi[r] = 0;
+                for (int r = 0; r < CH; ++r) {
+                    cen[r] = __low2half2(as_h2(base[(r + 3) * SW + 4]));
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = bias;
                 }
 #pragma unroll
-                for (int j = 0; j < SY; ++j) {
-                    uint32_t v[9];
+                for (int jr = 0; jr < CH + 6; ++jr) {
+                    __half2 wv[5];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) v[i] = (uint32_t)sV[warp][j][lane + i];
+                    for (int p = 0; p < 5; ++p) wv[p] = as_h2(base[jr * SW + 2 * p]);
 #pragma unroll
-                    for (int r = 0; r < TY; ++r) {
-                        const int dy = j - r;
+                    for (int r = 0; r < CH; ++r) {
+                        const int dy = jr - r;
                         if (dy < 0 || dy > 6) continue;
 #pragma unroll
-                        for (int i = 0; i < 9; ++i) {
-                            const int kb = dy * 9 + i;
-                            uint32_t bit = v[i] < cen[r] ? 1u : 0u;
-                            if (kb < 32) blo[r] |= bit << kb;
-                            else bhi[r] |= bit << (kb - 32);
+                        for (int p = 0; p < 5; ++p) {
+                            const int m = dy * 5 + p;
+                            const float wt = (float)(1 << (m % 10));
+                            const __half2 w2 = __floats2half2_rn(wt, p == 4 ? 0.0f : wt);
+                            const __half2 bits = __hsub2_sat(cen[r], wv[p]);
+                            acc[r][m / 10] = __hfma2(bits, w2, acc[r][m / 10]);
                         }
                     }
                 }
                 const int sh = a.views.side[k] < 0 ? 0 : 16;
 #pragma unroll
-                for (int r = 0; r < TY; ++r) {
-                    uint32_t hcost = __popc(blo[r] ^ rlo[r]) + __popc(bhi[r] ^ rhi[r]);
-                    if (!sOk[warp][r][lane]) hcost = kCensusMax;
-                    acc[r] += hcost << sh;
+                for (int r = 0; r < CH; ++r) {
+                    const uint4 rf = sm.refl[pr0 + r][pc];
+                    uint32_t hcost = __popc((as_u32(acc[r][0]) ^ rf.x) & LAYOUT_MASK) +
+                                     __popc((as_u32(acc[r][1]) ^ rf.y) & LAYOUT_MASK) +
+                                     __popc((as_u32(acc[r][2]) ^ rf.z) & LAYOUT_MASK) +
+                                     __popc((as_u32(acc[r][3]) ^ rf.w) & LAYOUT_MASK);
+                    const bool ok = (sm.okm[buf][pr0 + r][pc >> 5] >> (pc & 31)) & 1u;
+                    if (!ok) hcost = kCensusMax;
+                    slr[r] += hcost << sh;
                 }
             }
-            __syncthreads();
+            buf ^= 1;
         }
-
-        // ---- left/right combination and store
-        const int g = g0 + warp;
-        if (g < ghi && px < W) {
+        // -------------------------------------------------------------- store
+        if (cact && tx0 + pc < W) {
 #pragma unroll
-            for (int r = 0; r < TY; ++r) {
-                const int py = ty0 + r;
-                const int s = g - plo[r];
+            for (int r = 0; r < CH; ++r) {
+                const int py = ty0 + pr0 + r;
+                const int s = g - sm.lo[pr0 + r][pc];
                 if (py < H && s >= 0 && s < a.D) {
-                    uint32_t sl = acc[r] & 0xFFFFu, sr = acc[r] >> 16;
+                    const uint32_t sl = slr[r] & 0xFFFFu, sr = slr[r] >> 16;
                     uint32_t vl = 0xFFFFFFFFu, vr = 0xFFFFFFFFu;
-                    // round-half-up rescaling to nmax images: (s*nmax + n/2) / n
                     // (x * ceil(2^32 / n)) >> 32 == x / n exactly for x < 2^16, n <= 16
                     if (a.nL > 0) vl = (uint32_t)(((uint64_t)(sl * a.nmax + (a.nL >> 1)) * a.mL) >> 32);
                     if (a.nR > 0) vr = (uint32_t)(((uint64_t)(sr * a.nmax + (a.nR >> 1)) * a.mR) >> 32);
-                    a.S[((size_t)py * W + px) * a.Ds + s] = (uint16_t)min(vl, vr);
+                    a.S[((size_t)py * W + tx0 + pc) * a.Ds + s] = (uint16_t)min(vl, vr);
                 }
             }
         }
@@ -249,26 +334,44 @@ cost_kernel(const CostArgs a)
 
 void launch_cost(const CostArgs& a, cudaStream_t st)
 {
-    dim3 grid((a.W + TX - 1) / TX, (a.H + TY - 1) / TY);
-    cost_kernel<<<grid, THREADS, 0, st>>>(a);
+    static bool attr = false;
+    const int smem = (int)sizeof(SmemCost);
+    if (!attr) {
+        cudaFuncSetAttribute(cost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        attr = true;
+    }
+    dim3 grid((a.W + PW - 1) / PW, (a.H + PH - 1) / PH, 1);
+    // enough CTAs for about three waves of two CTAs per SM on 148 SMs
+    const int tiles = (int)(grid.x * grid.y);
+    grid.z = (unsigned)max(1, min((3 * 2 * 148 + tiles - 1) / tiles, (a.D + 7) / 8));
+    cost_kernel<<<grid, THREADS, smem, st>>>(a);
     count_launch();
 }
 
 // ---------------------------------------------------------------- level tables
 namespace {
-__global__ void prep_level_kernel(const ViewGeom vg, const LevelPlanes lp, float* htab,
-                                  float* delta)
+__global__ void prep_level_kernel(const ViewGeom vg, const LevelPlanes lp, float* htab, float* delta)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= lp.G * lp.V) return;
     int g = i / lp.V, k = i % lp.V;
     double rho = lp.rho0 + (double)g * lp.drho;
     float* o = htab + (size_t)i * 18;
+    double Hm[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Hm[3 * r + c] = vg.A[k][3 * r + c] - rho * vg.e[k][r] * vg.c[k][c];
+    // the homography is defined up to scale: make the homogeneous coordinate
+    // 1 at the image centre (keeps |N|, |D| small for the exact-grid steps);
+    // a centre behind the camera keeps its sign, so the w > 0 test is unchanged
+    const double wc = Hm[6] * lp.xc + Hm[7] * lp.yc + Hm[8];
+    const double sc = (wc != 0.0 && isfinite(wc)) ? 1.0 / fabs(wc) : 1.0;
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            double h = vg.A[k][3 * r + c] - rho * vg.e[k][r] * vg.c[k][c];
+            double h = Hm[3 * r + c] * sc;
             float hi = (float)h;
             o[3 * r + c] = hi;
             o[9 + 3 * r + c] = (float)(h - (double)hi);

@@ -218,6 +218,7 @@ fassmvs_status cost_volume_impl(fassmvs_ctx* c, const uint8_t* ref, const uint8_
 {
     if (!ref || !nbrs || !side || !K || !R || !t || !n || !Sv) return fail(c, FASSMVS_EINVAL, "NULL argument");
     if (W < 2 || H < 2) return fail(c, FASSMVS_EINVAL, "image must be at least 2x2");
+    if (W > 8192 || H > 8192) return fail(c, FASSMVS_EINVAL, "images up to 8192 pixels per side");
     if (pitch < W) return fail(c, FASSMVS_EINVAL, "pitch < W");
     if (V < 1 || V > fm::kMaxViews) return fail(c, FASSMVS_EINVAL, "1..%d neighbour views", fm::kMaxViews);
     if (D < 1 || D > fm::kMaxSlots || G < D || Ds < D) return fail(c, FASSMVS_EINVAL, "need 1 <= D <= 256, D <= G, D <= Ds");
@@ -228,7 +229,7 @@ fassmvs_status cost_volume_impl(fassmvs_ctx* c, const uint8_t* ref, const uint8_
         if (!nbrs[k]) return fail(c, FASSMVS_EINVAL, "neighbour %d is NULL", k);
     fm::ViewGeom vg;
     FM_TRY(view_geom(c, K, V, R, t, n, &vg));
-    fm::LevelPlanes lp{rho0, drho, G, V};
+    fm::LevelPlanes lp{rho0, drho, G, V, 0.5 * (W - 1), 0.5 * (H - 1)};
     void *htab, *delta, *cref;
     FM_TRY(ensure(c, "htab", sizeof(float) * 18 * (size_t)G * V, &htab));
     FM_TRY(ensure(c, "delta", sizeof(float) * (size_t)G, &delta));

@@ -24,6 +24,7 @@ struct ViewGeom {
 struct LevelPlanes {
     double rho0, drho;
     int G, V;
+    double xc, yc;    // image centre, where the homographies are normalised
 };
 
 // Device tables built once per level by prep_level_kernel:
