@@ -33,118 +33,215 @@ __device__ __forceinline__ uint4 pack8(const uint32_t (&o)[8])
                       o[6] | (o[7] << 16));
 }
 
+// The data costs and running aggregate of the pixel PF steps down the line
+// are copied into a per-warp shared ring with cp.async (each lane its own 16
+// bytes, so a per-thread wait suffices); the small per-pixel values (window
+// start, image value, surface-normal jump) are prefetched in registers.
+constexpr int PF = 8;
+
+struct StepScal {
+    int lo, ipix, dsn;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void load_scal(const SgmArgs& a, int r, int x, int y, StepScal& o)
+{
+    const size_t pix = (size_t)y * a.W + x;
+    o.lo = a.lo ? __ldg(a.lo + pix) : 0;
+    o.ipix = a.use_lut ? (int)__ldg(a.img + (size_t)y * a.img_pitch + x) : 0;
+    o.dsn = (a.variant == 1 && a.dI) ? (int)a.dI[(size_t)r * a.W * a.H + pix] : 0;
+}
+
+// Two hypotheses per 32-bit register: every path cost stays below 2^13 (the
+// host checks paths * (max S + max P2) < 2^16), so packed values never carry
+// or borrow across the halves; INF16 marks slots outside the window.
+constexpr uint32_t INF16 = 0x3FFFu;
+constexpr uint32_t INF2 = INF16 | (INF16 << 16);
+
+__device__ __forceinline__ uint32_t dup2(uint32_t v) { return v | (v << 16); }
+
 __global__ void __launch_bounds__(WARPS * 32)
 sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
 {
-    __shared__ uint32_t sT[WARPS][kMaxSlots + 2];
+    __shared__ uint16_t sT[WARPS][kMaxSlots + 4];
+    __shared__ uint4 ring[WARPS][PF][2][32];   // [step][S, S_bar][lane]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int line = blockIdx.x * WARPS + warp;
     if (line >= nlines) return;                // warp-uniform
     const int W = a.W, H = a.H, D = a.D;
-    int x, y;
-    if (dy == 0) { x = dx > 0 ? 0 : W - 1; y = line; }
-    else if (dx == 0) { y = dy > 0 ? 0 : H - 1; x = line; }
-    else if (line < H) { x = dx > 0 ? 0 : W - 1; y = line; }
-    else { int i = line - H; y = dy > 0 ? 0 : H - 1; x = dx > 0 ? i + 1 : W - 2 - i; }
+    int x0, y0;
+    if (dy == 0) { x0 = dx > 0 ? 0 : W - 1; y0 = line; }
+    else if (dx == 0) { y0 = dy > 0 ? 0 : H - 1; x0 = line; }
+    else if (line < H) { x0 = dx > 0 ? 0 : W - 1; y0 = line; }
+    else { int i = line - H; y0 = dy > 0 ? 0 : H - 1; x0 = dx > 0 ? i + 1 : W - 2 - i; }
+    int n = 1 << 30;                           // steps until the path leaves the image
+    if (dx > 0) n = min(n, W - x0);
+    if (dx < 0) n = min(n, x0 + 1);
+    if (dy > 0) n = min(n, H - y0);
+    if (dy < 0) n = min(n, y0 + 1);
 
     const int s0 = lane * 8;
     const bool act = s0 < D;
-    uint32_t Lp[8], L[8], Sv[8];
+    // valid-slot masks per packed pair
+    uint32_t vmask[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        vmask[j] = ((s0 + 2 * j < D) ? 0xFFFFu : 0u) | ((s0 + 2 * j + 1 < D) ? 0xFFFF0000u : 0u);
+    uint32_t Lp[4];
+    uint32_t left = INF2, right = INF2;        // neighbour pairs of the previous step
     uint32_t M = 0;
-    int g1 = 0, g2 = 0;       // winning plane of p - r and p - 2r (path gradient)
-    int lo_prev = 0;
-    int ipix_prev = 0;
-    const size_t plane_stride = (size_t)W * H;
+    int g1 = 0, g2 = 0;                        // winning plane of p - r and p - 2r (path gradient)
+    int lo_prev = 0, ipix_prev = 0;
+    const uint32_t P1 = (uint32_t)a.p1, P1P1 = dup2(P1);
+    uint16_t* buf = sT[warp];
 
-    uint4 sraw = make_uint4(0, 0, 0, 0);
-    if (act) sraw = __ldg(reinterpret_cast<const uint4*>(a.S + ((size_t)y * W + x) * a.Ds + s0));
-
-    for (int step = 0; x >= 0 && x < W && y >= 0 && y < H; ++step, x += dx, y += dy) {
-        const size_t pix = (size_t)y * W + x;
-        unpack8(sraw, Sv);
-        // prefetch the next pixel's costs
-        const int nx = x + dx, ny = y + dy;
-        if (act && nx >= 0 && nx < W && ny >= 0 && ny < H)
-            sraw = __ldg(reinterpret_cast<const uint4*>(a.S + ((size_t)ny * W + nx) * a.Ds + s0));
-        uint4 acc_raw = make_uint4(0, 0, 0, 0);
-        if (!first && act) acc_raw = *reinterpret_cast<const uint4*>(a.Sbar + pix * a.Ds + s0);
-
-        const int lo_p = a.lo ? __ldg(a.lo + pix) : 0;
-        if (step == 0) {
+    uint4(*rg)[2][32] = ring[warp];
+    StepScal q[PF];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) L[i] = (s0 + i < D) ? Sv[i] : INF;
-        } else {
-            int di = 0;
-            if (a.variant == 1 && a.dI) di = a.dI[(size_t)r * plane_stride + pix];
-            else if (a.variant == 2 && step >= 2) di = g2 - g1;
-            di = min(max(di, -a.dmax), a.dmax);
-            const int sigma = lo_p - lo_prev + di;
-            int P2 = a.p2;
-            if (a.use_lut) {
-                int d = (int)__ldg(a.img + (size_t)y * a.img_pitch + x) - ipix_prev;
-                P2 = a.lut[d < 0 ? -d : d];
+    for (int u = 0; u < PF; ++u) {
+        if (u < n) {
+            const int xx = x0 + u * dx, yy = y0 + u * dy;
+            const size_t pp = ((size_t)yy * W + xx) * a.Ds + s0;
+            if (act) {
+                cp_async16(&rg[u][0][lane], a.S + pp);
+                if (!first) cp_async16(&rg[u][1][lane], a.Sbar + pp);
             }
-            P2 = max(P2, a.p1);
-            const uint32_t P1 = (uint32_t)a.p1;
-            const uint32_t cap = M + (uint32_t)P2;
-            uint32_t left = __shfl_up_sync(FULL, Lp[7], 1);
-            uint32_t right = __shfl_down_sync(FULL, Lp[0], 1);
-            if (lane == 0) left = INF;
-            if (lane == 31) right = INF;
-            uint32_t T[8];
+            load_scal(a, r, xx, yy, q[u]);
+        }
+        cp_async_commit();
+    }
+
+    for (int base = 0; base < n; base += PF) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                uint32_t pv = i == 0 ? left : Lp[i - 1];
-                uint32_t nv = i == 7 ? right : Lp[i + 1];
-                T[i] = min(min(Lp[i], cap), min(pv, nv) + P1);
-            }
-            if (sigma != 0) {
-                uint32_t* buf = sT[warp];
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    if (s0 + i < D) buf[1 + s0 + i] = T[i];
-                if (lane == 0) buf[0] = min(Lp[0] + P1, cap);
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    if (s0 + i == D - 1) buf[D + 1] = min(Lp[i] + P1, cap);
-                __syncwarp();
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    int q = s0 + i + sigma;
-                    T[i] = (q >= -1 && q <= D) ? buf[q + 1] : cap;
+        for (int u = 0; u < PF; ++u) {
+            const int step = base + u;
+            if (step >= n) break;              // warp-uniform
+            const int x = x0 + step * dx, y = y0 + step * dy;
+            const size_t pix = (size_t)y * W + x;
+            const StepScal cur = q[u];
+            cp_async_wait<PF - 1>();           // this step's group has landed
+            const uint4 sraw = rg[u][0][lane];
+            const uint4 acc = rg[u][1][lane];
+            __syncwarp();
+            if (step + PF < n) {
+                const int xx = x + PF * dx, yy = y + PF * dy;
+                const size_t pp = ((size_t)yy * W + xx) * a.Ds + s0;
+                if (act) {
+                    cp_async16(&rg[u][0][lane], a.S + pp);
+                    if (!first) cp_async16(&rg[u][1][lane], a.Sbar + pp);
                 }
-                __syncwarp();
+                load_scal(a, r, xx, yy, q[u]);
             }
+            cp_async_commit();
+            const uint32_t Sv[4] = {sraw.x, sraw.y, sraw.z, sraw.w};
+            const int lo_p = cur.lo;
+            uint32_t L[4];
+            if (step == 0) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) L[i] = (s0 + i < D) ? Sv[i] + T[i] - M : INF;
-        }
-        // new minimum (and its slot, lowest on ties)
-        uint32_t key = 0xFFFFFFFFu;
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (s0 + i < D) key = min(key, (L[i] << 8) | (uint32_t)(s0 + i));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(FULL, key, o));
-        M = key >> 8;
-        g2 = g1;
-        g1 = lo_p + (int)(key & 255u);
-        // accumulate
-        if (act) {
-            uint32_t o[8];
-            if (first) {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) o[i] = (s0 + i < D) ? (L[i] & 0xFFFFu) : 0u;
+                for (int j = 0; j < 4; ++j) L[j] = (Sv[j] & vmask[j]) | (INF2 & ~vmask[j]);
             } else {
-                unpack8(acc_raw, o);
+                int di = 0;
+                if (a.variant == 1) di = cur.dsn;
+                else if (a.variant == 2 && step >= 2) di = g2 - g1;
+                di = min(max(di, -a.dmax), a.dmax);
+                const int sigma = lo_p - lo_prev + di;
+                int P2 = a.p2;
+                if (a.use_lut) {
+                    int d = cur.ipix - ipix_prev;
+                    P2 = a.lut[d < 0 ? -d : d];
+                }
+                P2 = max(P2, a.p1);
+                const uint32_t cap = M + (uint32_t)P2, cap2 = dup2(cap);
+                // T(s') = min(L'(s'), L'(s'-1) + P1, L'(s'+1) + P1, M + P2), packed,
+                // with the 16x2 dynamic-programming min / add-min instructions
+                uint32_t T[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) o[i] = (s0 + i < D) ? ((o[i] + L[i]) & 0xFFFFu) : o[i];
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t pv = __byte_perm(j == 0 ? left : Lp[j - 1], Lp[j], 0x5432);
+                    const uint32_t nv = __byte_perm(Lp[j], j == 3 ? right : Lp[j + 1], 0x5432);
+                    T[j] = __vimin3_u16x2(Lp[j], cap2, __viaddmin_u16x2(pv, P1P1, nv + P1P1));
+                }
+                if (sigma != 0) {
+                    // shift by sigma slots through shared memory: index k + 2 holds
+                    // T(k) for k in [-2, D+1]; beyond the predecessor's window the
+                    // transition costs M + P2 (k = -2, D + 1 and clamped indices)
+                    uint32_t* b32 = reinterpret_cast<uint32_t*>(buf);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (s0 + 2 * j + 1 < D) b32[1 + (s0 >> 1) + j] = T[j];
+                        else if (s0 + 2 * j < D) buf[2 + s0 + 2 * j] = (uint16_t)(T[j] & 0xFFFFu);
+                    }
+                    const uint32_t lp0 = __shfl_sync(FULL, Lp[0], 0) & 0xFFFFu;
+                    const int lastl = (D - 1) >> 3, lasti = (D - 1) & 7;
+                    uint32_t lsel = Lp[0];
+#pragma unroll
+                    for (int j = 1; j < 4; ++j)
+                        if ((lasti >> 1) == j) lsel = Lp[j];
+                    const uint32_t lpw = __shfl_sync(FULL, lsel, lastl);
+                    const uint32_t lpD = (lasti & 1) ? (lpw >> 16) : (lpw & 0xFFFFu);
+                    if (lane == 0) {
+                        buf[0] = (uint16_t)cap;
+                        buf[1] = (uint16_t)min(lp0 + P1, cap);
+                        buf[D + 2] = (uint16_t)min(lpD + P1, cap);
+                        buf[D + 3] = (uint16_t)cap;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int q0 = min(max(s0 + 2 * j + sigma, -2), D + 1) + 2;
+                        const int q1 = min(max(s0 + 2 * j + 1 + sigma, -2), D + 1) + 2;
+                        T[j] = (uint32_t)buf[q0] | ((uint32_t)buf[q1] << 16);
+                    }
+                    __syncwarp();
+                }
+                const uint32_t M2 = dup2(M);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) L[j] = ((Sv[j] + T[j] - M2) & vmask[j]) | (INF2 & ~vmask[j]);
             }
-            *reinterpret_cast<uint4*>(a.Sbar + pix * a.Ds + s0) = pack8(o);
-        }
+            // neighbours for the next step, then the new minimum over the window
+            // (with its lowest slot for the path gradient) by a warp reduction
+            left = __shfl_up_sync(FULL, L[3], 1);
+            right = __shfl_down_sync(FULL, L[0], 1);
+            if (lane == 0) left = INF2;
+            if (lane == 31) right = INF2;
+            if (a.variant == 2) {
+                uint32_t key = 0xFFFFFFFFu;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) Lp[i] = L[i];
-        lo_prev = lo_p;
-        if (a.use_lut) ipix_prev = __ldg(a.img + (size_t)y * a.img_pitch + x);
+                for (int j = 0; j < 4; ++j) {
+                    key = min(key, ((L[j] & 0xFFFFu) << 8) | (uint32_t)(s0 + 2 * j));
+                    key = min(key, ((L[j] >> 16) << 8) | (uint32_t)(s0 + 2 * j + 1));
+                }
+                key = __reduce_min_sync(FULL, key);
+                M = key >> 8;
+                g2 = g1;
+                g1 = lo_p + (int)(key & 255u);
+            } else {
+                const uint32_t mm = __vimin3_u16x2(__vimin3_u16x2(L[0], L[1], L[2]), L[3], L[3]);
+                M = __reduce_min_sync(FULL, min(mm & 0xFFFFu, mm >> 16));
+            }
+            if (act) {
+                uint4 o;
+                if (first) {
+                    o = make_uint4(L[0] & vmask[0], L[1] & vmask[1], L[2] & vmask[2], L[3] & vmask[3]);
+                } else {
+                    o = make_uint4(acc.x + (L[0] & vmask[0]), acc.y + (L[1] & vmask[1]),
+                                   acc.z + (L[2] & vmask[2]), acc.w + (L[3] & vmask[3]));
+                }
+                *reinterpret_cast<uint4*>(a.Sbar + pix * a.Ds + s0) = o;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Lp[j] = L[j];
+            lo_prev = lo_p;
+            ipix_prev = cur.ipix;
+        }
     }
 }
 
