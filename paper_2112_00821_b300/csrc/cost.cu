@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
                 df d1 = to_grid(df_add(df_mul_int(h6, fx1), by_d));
                 const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
                 uint32_t(*prow)[SW] = sm.pair[buf];
-#pragma unroll
+#pragma unroll 2
                 for (int jj = 0; jj < 8; ++jj) {
                     const int j = rs + jj;
                     if (j >= re) break;
