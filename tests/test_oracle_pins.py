@@ -568,3 +568,43 @@ def test_fronto_plane_exact_shift_views_give_exact_plane_index(orc):
         Sb = orc.sgm_aggregate(S, p1, p2=p2)
         _, gw = orc.wta_refine(Sb, K, [0, 0, -1.0], rho0, drho)
         assert np.all(gw[inner] == gstar), (p1, p2)
+
+
+def test_normal_smoothing_commutes_with_mirroring(orc):
+    """Mirroring depth and image about the principal point mirrors the smoothed
+    normals (n_x changes sign): the window and its weights are symmetric (an
+    off-by-one window or a one-sided difference breaks this)."""
+    g = np.random.default_rng(21)
+    W, H = 31, 23
+    K = np.array([[50.0, 0, (W - 1) / 2], [0, 50.0, (H - 1) / 2], [0, 0, 1]])
+    xs, ys = np.meshgrid(np.arange(W), np.arange(H))
+    d = (15.0 + np.sin(xs / 5.0) + 0.5 * np.cos(ys / 4.0) + 0.3 * xs / W).astype(np.float32)
+    img = g.integers(0, 256, (H, W), dtype=np.uint8)
+    sm, _ = orc.normals(d, img, K, radius=2, beta=10.0)
+    smf, _ = orc.normals(d[:, ::-1].copy(), img[:, ::-1].copy(), K, radius=2, beta=10.0)
+    mir = smf[:, ::-1].copy()
+    mir[..., 0] *= -1
+    assert np.allclose(sm, mir, atol=1e-6)
+
+
+def test_normal_smoothing_stops_at_image_edges(orc):
+    """The appearance term exp(-dI / beta) with dI = 255, beta = 10 weighs a
+    neighbour across a strong image edge by e^-25.5, so a pixel next to the
+    edge keeps its own surface's normal; with a uniform image the neighbour
+    across mixes in."""
+    K = np.array([[60.0, 0, 15.5], [0, 60.0, 12.5], [0, 0, 1]])
+    xs, ys = np.meshgrid(np.arange(32), np.arange(26))
+    n1 = np.array([0.4, 0.0, -1.0]); n1 /= np.linalg.norm(n1)
+    n2 = np.array([-0.4, 0.0, -1.0]); n2 /= np.linalg.norm(n2)
+    d1 = _plane_depth(n1, 10.0, K, 32, 26)
+    d2 = _plane_depth(n2, 10.0, K, 32, 26)
+    d = np.where(xs <= 15, d1, d2).astype(np.float32)   # surface changes between 15 | 16
+    img = np.where(xs <= 16, 0, 255).astype(np.uint8)   # image edge between 16 | 17
+    sm, raw = orc.normals(d, img, K, radius=2, beta=10.0)
+    # column 18: its window (16..20) holds column 16, whose raw normal straddles
+    # the surface change, but 16 lies across the image edge
+    assert np.allclose(raw[5:-5, 17:21], n2, atol=5e-5)
+    # (the raw normals themselves carry ~0.01 degree of FP32-depth noise)
+    assert np.degrees(np.max(np.arccos(np.clip(sm[5:-5, 18] @ n2, -1, 1)))) < 0.05
+    sm_u, _ = orc.normals(d, np.full_like(img, 128), K, radius=2, beta=10.0)
+    assert np.degrees(np.arccos(np.clip(sm_u[10, 18] @ n2, -1, 1))) > 0.5
