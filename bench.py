@@ -45,6 +45,9 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--form", default="frame", choices=["frame", "batch"],
+                   help="frame: the 1080p per-frame workload (default line); batch: the mixed "
+                        "16-frame batch, batched form against one estimate per frame")
     return p.parse_args()
 
 
@@ -338,13 +341,13 @@ def run_ours(a):
     sgm_bytes = 4.0 * sum(w * h * d for w, h, d in lv) * a.steps
     hbm = (peaks or {}).get("hbm_gbs", 6400.0)
     sgm_ach = sgm_bytes / (sgm_ms * 1e-3) / 1e9 if sgm_ms > 0 else 0.0
-    rl_cost = {"kernel": "cost_kernel", "bound": "alu", "achieved": round(cost_ach, 3),
+    rl_cost = {"kernel": "cost_batch_kernel", "bound": "alu", "achieved": round(cost_ach, 3),
                "peak": round(alu_peak, 3), "unit": "Tops/s", "frac": round(cost_ach / alu_peak, 4),
-               "traffic": _traffic("cost_kernel", sum(w * h * d for w, h, d in lv[:1]))}
-    rl_sgm = {"kernel": "sgm_dir_kernel", "bound": "hbm", "achieved": round(sgm_ach, 1),
+               "traffic": _traffic("cost_batch_kernel", sum(w * h * d for w, h, d in lv[:1]))}
+    rl_sgm = {"kernel": "sgm_batch_dir_kernel", "bound": "hbm", "achieved": round(sgm_ach, 1),
               "peak": hbm, "unit": "GB/s", "frac": round(sgm_ach / hbm, 4),
               "peak_source": "measured" if peaks else "fallback",
-              "traffic": _traffic("sgm_dir_kernel", sum(w * h * d for w, h, d in lv[:1]))}
+              "traffic": _traffic("sgm_batch_dir_kernel", sum(w * h * d for w, h, d in lv[:1]))}
     dominant = rl_cost if cost_ms >= sgm_ms else rl_sgm
     step_ms = {k: round(v[0] / a.steps, 3) for k, v in stages.items()}
     line = {
@@ -373,10 +376,125 @@ def run_ours(a):
     return 0
 
 
+# ---------------------------------------------------------------- batched form
+BATCH_CFG = dict(levels=4, D=[256, 256, 256, 256], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1)
+
+
+def run_batch_form(a):
+    """Mixed 16-frame batch (sizes 640x480 .. 2720x1530, 64-256 planes, 3-6
+    views): frames/s of one fassmvs_estimate per frame against
+    fassmvs_estimate_batch (eager, under a CUDA graph, and autotuned), on the
+    same frames and outputs, which must be identical."""
+    import numpy as np
+    import torch
+    from paper_2112_00821_b300 import fassmvs, synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    scenes = synth.batch_frames(a.seed + rank, 16)
+    t_render = time.perf_counter() - t0
+    cfg = fassmvs.default_config(**BATCH_CFG)
+    items = []
+    dev_imgs = {}
+    for sc in scenes:
+        key = id(sc.ref)
+        if key not in dev_imgs:
+            dev_imgs[key] = torch.from_numpy(sc.ref).cuda()
+        for x in sc.nbrs:
+            if id(x) not in dev_imgs:
+                dev_imgs[id(x)] = torch.from_numpy(x).cuda()
+        items.append(dict(ref=dev_imgs[id(sc.ref)], nbrs=[dev_imgs[id(x)] for x in sc.nbrs], K=sc.K, R=sc.R,
+                          t=sc.t, side=sc.side, planes=fassmvs.planes_of(sc)))
+    vox = sum(w * h * d for sc in scenes for w, h, d in level_voxels(sc.W, sc.H, 4, sc.G0, BATCH_CFG["D"]))
+
+    def outputs():
+        return [(torch.empty((sc.H, sc.W), dtype=torch.float32, device="cuda"),
+                 torch.empty((sc.H, sc.W, 3), dtype=torch.float32, device="cuda"),
+                 torch.empty((sc.H, sc.W), dtype=torch.float32, device="cuda")) for sc in scenes]
+
+    def with_out(outs):
+        return [dict(it, depth=o[0], normal=o[1], conf=o[2]) for it, o in zip(items, outs)]
+
+    stream = torch.cuda.Stream()
+
+    def timed(fn, steps, warm):
+        with torch.cuda.stream(stream):
+            for _ in range(warm):
+                fn()
+            stream.synchronize()
+            n0 = fassmvs.Context.launch_count()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps, (fassmvs.Context.launch_count() - n0) // steps
+
+    warm = max(a.warmup, 3)
+    res = {}
+    # one estimate per frame (the plain form), one context
+    plain_out = outputs()
+    cp = fassmvs.Context(cfg)
+
+    def plain():
+        for it, o in zip(items, plain_out):
+            cp.set_cameras(it["K"], it["R"], it["t"], it["side"])
+            cp.estimate(it["ref"], it["nbrs"], it["planes"], *o)
+
+    clocks = Clocks(local)
+    clocks.start()
+    res["plain_per_frame"] = timed(plain, a.steps, warm)
+    cp.close()
+    # batched, eager
+    cb = fassmvs.Context(cfg)
+    b_out = outputs()
+    b_items = with_out(b_out)
+    res["batched_eager"] = timed(lambda: cb.estimate_batch(b_items), a.steps, warm)
+    # batched under a CUDA graph (captured each call, executable updated in place)
+    cb.set_graph(True)
+    res["batched_graph"] = timed(lambda: cb.estimate_batch(b_items), a.steps, warm)
+    cb.set_graph(False)
+    # autotuned decomposition of the persistent cost kernel, then graph again
+    with torch.cuda.stream(stream):
+        tune = cb.autotune(b_items)
+    stream.synchronize()
+    cb.set_graph(True)
+    res["batched_graph_tuned"] = timed(lambda: cb.estimate_batch(b_items), a.steps, warm)
+    ck = clocks.stop()
+    torch.cuda.synchronize()
+    same = all(torch.equal(x, y) for o1, o2 in zip(plain_out, b_out) for x, y in zip(o1, o2))
+    cb.close()
+    if rank != 0:
+        return 0
+    best = min(("batched_eager", "batched_graph", "batched_graph_tuned"), key=lambda k: res[k][0])
+    forms = {k: {"ms_per_batch": round(v[0], 3), "frames_per_s": round(16e3 / v[0], 2),
+                 "Mpix_planes_per_s": round(vox / (v[0] * 1e-3) / 1e6, 1), "gpu_launches_per_batch": int(v[1])}
+             for k, v in res.items()}
+    line = {
+        "form": "batch", "metric": "frames/s of the mixed 16-frame batch", "unit": "frames/s",
+        "value": forms[best]["frames_per_s"], "best": best, "n_gpus": world, "steps": a.steps, "warmup": warm,
+        "higher_is_better": True, "dtype": "u16", "data": "synthetic",
+        "config": {"workload": "batch16_mixed", "frames": [[sc.W, sc.H, sc.G0, len(sc.nbrs)] for sc in scenes],
+                   "voxels_per_batch": vox, "levels": 4, "variant": "path-gradient", "paths": 8,
+                   "l2": "working set exceeds L2; no flush", "render_s": round(t_render, 1)},
+        "forms": forms,
+        "speedup_vs_plain": round(res["plain_per_frame"][0] / res[best][0], 3),
+        "autotuned": {"chunk_planes": tune[0], "ctas_per_sm": tune[1], "sgm_parts": tune[2]},
+        "identical_to_plain": bool(same),
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.form == "batch":
+        return run_batch_form(a)
     return run_ours(a)
 
 

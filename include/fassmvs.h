@@ -132,6 +132,68 @@ FASSMVS_API fassmvs_status fassmvs_estimate(fassmvs_ctx* ctx, const uint8_t* ref
                                 const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* planes,
                                 float* depth, float* normal, float* conf, void* stream);
 
+/* ---- batched form ------------------------------------------------------- */
+
+/* One reference frame of a batch (all pointers as for fassmvs_estimate; the
+ * camera and plane parameters are HOST arrays read during the call). */
+typedef struct {
+    const uint8_t* ref;           /* device, W x H, row pitch `pitch` */
+    const uint8_t* const* nbrs;   /* HOST array of n_nb device pointers, same layout */
+    int32_t W, H, pitch, n_nb;
+    const double* K;              /* 3x3 */
+    const double* R;              /* n_nb x 3 x 3, reference -> neighbour */
+    const double* t;              /* n_nb x 3 */
+    const int8_t* side;           /* n_nb: -1 left, +1 right */
+    fassmvs_planes planes;
+    float* depth;                 /* device W*H */
+    float* normal;                /* device W*H*3 */
+    float* conf;                  /* device W*H */
+} fassmvs_frame;
+
+/* Estimates n (1..64) frames of mixed size, view count and plane count with
+ * the context's configuration (Sec. 2.1 applied to every frame).  Per level
+ * the frames share launches: the cost volumes of all frames come from one
+ * persistent kernel pulling (frame, tile, plane chunk) work items from an
+ * atomic counter, and the aggregation runs several directions of all frames
+ * per launch, each into its own partial sum (see fassmvs_tuning), which the
+ * winner-take-all step adds.  Results equal those of n separate
+ * fassmvs_estimate calls, bit for bit, for every tuning.  Scratch for every
+ * frame of the batch is held at once: per frame and level about
+ * W*H*Ds*2*(1 + parts) bytes for the cost volume and the partial sums (Ds =
+ * window planes rounded up to 8), within the context budget (FASSMVS_ENOMEM
+ * beyond it).  The per-call argument blocks go through two pinned staging
+ * halves; a call waits until the call two before it has finished on the
+ * device.  Calls on one context must be ordered (one stream, or synchronised
+ * between streams): frames of concurrent calls would share scratch.
+ * With graphs enabled (fassmvs_set_graph) and a non-default stream, a batch
+ * whose shapes were seen before is captured and launched as one CUDA graph,
+ * the executable graph of that shape being updated in place each call; the
+ * first call of a shape runs eagerly and allocates. */
+FASSMVS_API fassmvs_status fassmvs_estimate_batch(fassmvs_ctx* ctx, const fassmvs_frame* frames, int n,
+                                                  void* stream);
+FASSMVS_API fassmvs_status fassmvs_set_graph(fassmvs_ctx* ctx, int on);
+
+/* Work decomposition of the batched form; no setting changes any result.
+ *   chunk_planes  planes per work item of the persistent cost kernel, 1..256,
+ *                 or 0: enough items for about three waves (chunks >= 8)
+ *   ctas_per_sm   resident cost CTAs per SM, 1 or 2
+ *   sgm_parts     partial sums of the aggregation, 1, 2, 4 or 8 (at most the
+ *                 path count), or 0: one per path.  With P parts, P
+ *                 directions run concurrently in each of paths/P launches. */
+typedef struct {
+    int32_t chunk_planes, ctas_per_sm, sgm_parts;
+} fassmvs_tuning;
+
+/* fassmvs_autotune times a set of candidate tunings on the given batch
+ * (running it once per candidate, outputs written each time) and keeps the
+ * fastest for later batches of the same shapes; the choice is returned in
+ * *chosen (may be NULL) and appended as one JSON line to the file named by the
+ * FASSMVS_TUNE_FILE environment variable, when set.  fassmvs_set_tuning sets
+ * the context default and forgets earlier choices. */
+FASSMVS_API fassmvs_status fassmvs_set_tuning(fassmvs_ctx* ctx, const fassmvs_tuning* tuning);
+FASSMVS_API fassmvs_status fassmvs_autotune(fassmvs_ctx* ctx, const fassmvs_frame* frames, int n,
+                                            void* stream, fassmvs_tuning* chosen);
+
 /* ---- stages of the hot path (used by the estimate and by parity tests) ---- */
 
 /* Sec. 2.1 pyramid level: 3x3 Gaussian (sigma 1, integer weights 70/116/70

@@ -167,12 +167,12 @@ __device__ __forceinline__ uint4 to_layout(uint64_t c)
 __device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
 __device__ __forceinline__ uint32_t as_u32(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
-__global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
+// One tile (bx, by) of one frame, plane chunk bz of nz.  Called by the
+// single-frame grid kernel and by the persistent multi-frame kernel.
+__device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int bz, int nz, SmemCost& sm)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tx0 = blockIdx.x * PW, ty0 = blockIdx.y * PH;
+    const int tx0 = bx * PW, ty0 = by * PH;
     const int W = a.W, H = a.H;
 
     if (tid == 0) { sm.glo = a.G; sm.ghi = 0; }
@@ -191,10 +191,10 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
     }
     __syncthreads();
     // planes of this tile (guarded against an out-of-range window map), split
-    // into gridDim.z consecutive chunks
+    // into nz consecutive chunks
     const int tlo = max(sm.glo, 0), thi = min(sm.ghi, a.G);
-    const int chunk = (thi - tlo + (int)gridDim.z - 1) / (int)gridDim.z;
-    const int glo = tlo + (int)blockIdx.z * chunk, ghi = min(thi, glo + chunk);
+    const int chunk = (thi - tlo + nz - 1) / nz;
+    const int glo = tlo + bz * chunk, ghi = min(thi, glo + chunk);
 
     // census role: columns cp*32 + lane, rows rc*13 .. rc*13 + 12
     const int pc = (warp & 1) * 32 + lane;
@@ -330,21 +330,77 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
     }
 }
 
+__global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
+    cost_tile(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm);
+}
+
+// Persistent form for a batch of frames: every CTA pulls work items
+// (frame, tile x, tile y, chunk | chunks << 16) from one atomic counter; the
+// frame's arguments are staged in shared memory for the item.
+__global__ void __launch_bounds__(THREADS, 2)
+cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ items, int n_items, int* counter)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
+    __shared__ CostArgs sa;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int4 w = items[it];
+        {
+            const int* src = reinterpret_cast<const int*>(args + w.x);
+            int* dst = reinterpret_cast<int*>(&sa);
+            for (int i = threadIdx.x; i < (int)(sizeof(CostArgs) / sizeof(int)); i += THREADS) dst[i] = src[i];
+        }
+        __syncthreads();
+        cost_tile(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int cost_tiles_x(int W) { return (W + PW - 1) / PW; }
+int cost_tiles_y(int H) { return (H + PH - 1) / PH; }
+
+namespace {
+// the shared-memory opt-in is a per-device function attribute
+void cost_smem_optin()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    const int smem = (int)sizeof(SmemCost);
+    cudaFuncSetAttribute(cost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(cost_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    done[dev] = true;
+}
 }  // namespace
 
 void launch_cost(const CostArgs& a, cudaStream_t st)
 {
-    static bool attr = false;
-    const int smem = (int)sizeof(SmemCost);
-    if (!attr) {
-        cudaFuncSetAttribute(cost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr = true;
-    }
+    cost_smem_optin();
     dim3 grid((a.W + PW - 1) / PW, (a.H + PH - 1) / PH, 1);
     // enough CTAs for about three waves of two CTAs per SM on 148 SMs
     const int tiles = (int)(grid.x * grid.y);
     grid.z = (unsigned)max(1, min((3 * 2 * 148 + tiles - 1) / tiles, (a.D + 7) / 8));
-    cost_kernel<<<grid, THREADS, smem, st>>>(a);
+    cost_kernel<<<grid, THREADS, sizeof(SmemCost), st>>>(a);
+    count_launch();
+}
+
+void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas,
+                       cudaStream_t st)
+{
+    cost_smem_optin();
+    cudaMemsetAsync(counter, 0, sizeof(int), st);
+    cost_batch_kernel<<<ctas, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, counter);
     count_launch();
 }
 

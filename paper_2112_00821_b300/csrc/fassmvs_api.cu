@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <string>
 #include <vector>
@@ -40,6 +41,17 @@ struct fassmvs_ctx {
     std::vector<Rec> pending;
     double ms[FASSMVS_NSTAGES] = {};
     uint64_t cnt[FASSMVS_NSTAGES] = {};
+    // batched form: work decomposition, graphs, pinned staging of the per-call
+    // argument blocks (two halves, each released by an event)
+    fassmvs_tuning tune{0, 2, 0};              // automatic chunks and parts
+    std::map<uint64_t, fassmvs_tuning> tuned;
+    bool graph = false;
+    std::map<uint64_t, cudaGraphExec_t> execs;
+    std::map<uint64_t, int> seen;
+    unsigned char* host_arena[2] = {nullptr, nullptr};
+    size_t host_cap = 0;
+    cudaEvent_t arena_ev[2] = {nullptr, nullptr};
+    int arena_half = 0;
 };
 
 namespace {
@@ -364,6 +376,12 @@ void fassmvs_destroy(fassmvs_ctx* c)
         if (kv.second.p) cudaFree(kv.second.p);
     for (auto& r : c->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->pool) cudaEventDestroy(e);
+    for (auto& kv : c->execs)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
+    for (int i = 0; i < 2; ++i) {
+        if (c->host_arena[i]) cudaFreeHost(c->host_arena[i]);
+        if (c->arena_ev[i]) cudaEventDestroy(c->arena_ev[i]);
+    }
     delete c;
 }
 
@@ -512,119 +530,534 @@ fassmvs_status fassmvs_dsn(fassmvs_ctx* c, const float* dc, const float* nc, int
     return launch_status(c, "dsn launch");
 }
 
+}  // extern "C"
+
+namespace {
+
+// per-frame state of one batch call
+struct FrameRun {
+    const fassmvs_frame* fr;
+    int V = 0, nL = 0, nR = 0, nmax = 0, P1 = 0;
+    uint16_t lut[256];
+    int Ws[8], Hs[8], Ps[8];
+    const uint8_t* img[8][fm::kMaxViews + 1];
+    float* dprev = nullptr;
+    float* nprev = nullptr;
+    // this level
+    int w = 0, h = 0, D = 0, Ds = 0, Gl = 0;
+    double Kl[9];
+    double drl = 0;
+    void *pS = nullptr, *pSb = nullptr, *pdraw = nullptr, *pdmed = nullptr, *pnraw = nullptr, *pnrm = nullptr;
+    void *plo = nullptr, *pdI = nullptr, *htab = nullptr, *delta = nullptr, *cref = nullptr;
+};
+
+fassmvs_status check_frame(fassmvs_ctx* c, const fassmvs_frame& f, int L, int idx)
+{
+    if (!f.ref || !f.nbrs || !f.K || !f.R || !f.t || !f.side || !f.depth || !f.normal || !f.conf)
+        return fail(c, FASSMVS_EINVAL, "frame %d: NULL argument", idx);
+    if (f.W < 2 || f.H < 2 || f.W > 8192 || f.H > 8192 || f.pitch < f.W)
+        return fail(c, FASSMVS_EINVAL, "frame %d: bad size or pitch", idx);
+    if (f.n_nb < 1 || f.n_nb > fm::kMaxViews) return fail(c, FASSMVS_EINVAL, "frame %d: 1..16 views", idx);
+    for (int k = 0; k < f.n_nb; ++k)
+        if (!f.nbrs[k]) return fail(c, FASSMVS_EINVAL, "frame %d: neighbour %d is NULL", idx, k);
+    double Ki[9];
+    if (!k_inverse(f.K, Ki)) return fail(c, FASSMVS_EINVAL, "frame %d: K must be upper triangular", idx);
+    for (int i = 0; i < 9 * f.n_nb; ++i)
+        if (!std::isfinite(f.R[i])) return fail(c, FASSMVS_EINVAL, "frame %d: R is not finite", idx);
+    for (int i = 0; i < 3 * f.n_nb; ++i)
+        if (!std::isfinite(f.t[i])) return fail(c, FASSMVS_EINVAL, "frame %d: t is not finite", idx);
+    if (((f.W - 1) >> (L - 1)) + 1 < 2 || ((f.H - 1) >> (L - 1)) + 1 < 2)
+        return fail(c, FASSMVS_EINVAL, "frame %d: image too small for %d levels", idx, L);
+    if (f.planes.G0 < 1) return fail(c, FASSMVS_EINVAL, "frame %d: G0 must be >= 1", idx);
+    if ((f.planes.G0 - 1) / (1 << (L - 1)) + 1 > fm::kMaxSlots)
+        return fail(c, FASSMVS_EINVAL, "frame %d: top level has more than 256 planes (Sec. 3.2 cap)", idx);
+    if (!(std::isfinite(f.planes.rho_far) && std::isfinite(f.planes.drho)) ||
+        !(f.planes.rho_far > 0.0 || (f.planes.rho_far >= 0.0 && f.planes.drho > 0.0)))
+        return fail(c, FASSMVS_EINVAL, "frame %d: plane list must have positive inverse distances", idx);
+    return FASSMVS_OK;
+}
+
+// bump allocator over the two mirrored staging blocks (pinned host, device)
+struct Stage {
+    unsigned char* host;
+    unsigned char* dev;
+    size_t off, cap;
+    int half;
+    void* take(size_t bytes, size_t& at)
+    {
+        at = (off + 255) & ~(size_t)255;
+        off = at + bytes;
+        return off <= cap ? host + at : nullptr;
+    }
+};
+
+std::string fname(int f, const char* what)
+{
+    char b[48];
+    snprintf(b, sizeof b, "f%d:%s", f, what);
+    return b;
+}
+
+// partial sums of the aggregation: one per direction when automatic
+int sgm_parts(const fassmvs_tuning& t, int paths)
+{
+    const int p = t.sgm_parts ? t.sgm_parts : paths;
+    return p > paths ? paths : p;
+}
+
+// Picks the staging half for one call and waits until the call that last used
+// it has finished on the device; grows both halves (pinned host and device
+// mirror) when the batch needs more.  Never runs while a stream is captured.
+fassmvs_status stage_prepare(fassmvs_ctx* c, const fassmvs_frame* frames, int n, int chunk_planes, Stage* out)
+{
+    const int L = c->cfg.levels;
+    const int cmin = chunk_planes > 0 ? chunk_planes : 8;   // automatic chunks hold >= 8 planes
+    size_t need = 4096;
+    for (int l = 0; l < L; ++l) {
+        size_t items = 0;
+        for (int f = 0; f < n; ++f) {
+            const int w = ((frames[f].W - 1) >> l) + 1, h = ((frames[f].H - 1) >> l) + 1;
+            items += (size_t)fm::cost_tiles_x(w) * fm::cost_tiles_y(h) *
+                     ((fm::kMaxSlots + cmin - 1) / cmin + 1);
+        }
+        need += 2 * 256 + n * sizeof(fm::CostArgs) + items * sizeof(int4);
+    }
+    if (need > c->host_cap) {
+        for (int i = 0; i < 2; ++i) {
+            if (c->arena_ev[i]) FM_TRY(cuda_check(c, cudaEventSynchronize(c->arena_ev[i]), "staging wait"));
+            if (c->host_arena[i]) cudaFreeHost(c->host_arena[i]);
+            c->host_arena[i] = nullptr;
+            FM_TRY(cuda_check(c, cudaHostAlloc((void**)&c->host_arena[i], need, cudaHostAllocDefault), "cudaHostAlloc"));
+            if (!c->arena_ev[i])
+                FM_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->arena_ev[i], cudaEventDisableTiming), "event"));
+        }
+        c->host_cap = need;
+    }
+    const int half = c->arena_half;
+    c->arena_half ^= 1;
+    FM_TRY(cuda_check(c, cudaEventSynchronize(c->arena_ev[half]), "staging wait"));
+    void* dstage;
+    FM_TRY(ensure(c, half ? "stageB" : "stageA", c->host_cap, &dstage));
+    *out = Stage{c->host_arena[half], (unsigned char*)dstage, 0, c->host_cap, half};
+    return FASSMVS_OK;
+}
+
+fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cudaStream_t st,
+                         const fassmvs_tuning& tn, const Stage& stage)
+{
+    const fassmvs_config& cfg = c->cfg;
+    const int L = cfg.levels;
+    const int chunk_planes = tn.chunk_planes, ctas_per_sm = tn.ctas_per_sm;
+    const int parts = sgm_parts(tn, cfg.paths);
+    const bool capturing = [&] {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        return cs != cudaStreamCaptureStatusNone;
+    }();
+    const bool prof = c->prof;
+    if (capturing) c->prof = false;
+    struct Restore { fassmvs_ctx* c; bool p; ~Restore() { c->prof = p; } } restore{c, prof};
+
+    std::vector<FrameRun> fr(n);
+    for (int f = 0; f < n; ++f) {
+        FrameRun& F = fr[f];
+        F.fr = &frames[f];
+        F.V = frames[f].n_nb;
+        for (int k = 0; k < F.V; ++k) { if (frames[f].side[k] < 0) ++F.nL; else ++F.nR; }
+        F.nmax = std::max(F.nL, F.nR);
+        F.P1 = cfg.p1 * F.nmax;
+        p2_table(F.P1, cfg.alpha, cfg.beta, F.lut);
+        F.Ws[0] = frames[f].W; F.Hs[0] = frames[f].H; F.Ps[0] = frames[f].pitch;
+        F.img[0][0] = frames[f].ref;
+        for (int k = 0; k < F.V; ++k) F.img[0][k + 1] = frames[f].nbrs[k];
+        for (int l = 1; l < L; ++l) {
+            F.Ws[l] = (F.Ws[l - 1] + 1) / 2;
+            F.Hs[l] = (F.Hs[l - 1] + 1) / 2;
+            F.Ps[l] = F.Ws[l];
+        }
+    }
+    void* counter;
+    FM_TRY(ensure(c, "counter", 256, &counter));
+    Stage sg = stage;
+    std::vector<fm::SgmArgs> sargs;
+    static thread_local fm::SgmBatch sb;       // 20 KB: kept off the stack
+
+    // ---- pyramids of every frame
+    {
+        StageTimer tm(c, FASSMVS_STAGE_PYRAMID, st);
+        for (int f = 0; f < n; ++f) {
+            FrameRun& F = fr[f];
+            for (int l = 1; l < L; ++l) {
+                void* p;
+                FM_TRY(ensure(c, fname(f, ("pyr" + std::to_string(l)).c_str()).c_str(),
+                              (size_t)(F.V + 1) * F.Ws[l] * F.Hs[l], &p));
+                for (int k = 0; k <= F.V; ++k) {
+                    uint8_t* o = (uint8_t*)p + (size_t)k * F.Ws[l] * F.Hs[l];
+                    fm::launch_pyramid_down(F.img[l - 1][k], F.Ws[l - 1], F.Hs[l - 1], F.Ps[l - 1], o, F.Ps[l], st);
+                    F.img[l][k] = o;
+                }
+            }
+        }
+    }
+    int ctas = 0;
+    {
+        int nsm = 148;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+        ctas = nsm * ctas_per_sm;
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const size_t block0 = (sg.off + 255) & ~(size_t)255;
+        size_t at_cargs, at_items;
+        fm::CostArgs* cargs = (fm::CostArgs*)sg.take(sizeof(fm::CostArgs) * n, at_cargs);
+        if (!cargs) return fail(c, FASSMVS_EINTERNAL, "staging overflow");
+        sargs.resize(n);
+        std::vector<int4> items;
+        std::vector<int> order(n);
+        for (int f = 0; f < n; ++f) {
+            FrameRun& F = fr[f];
+            const fassmvs_frame& X = *F.fr;
+            F.w = F.Ws[l]; F.h = F.Hs[l];
+            const size_t np = (size_t)F.w * F.h;
+            const double sc = (double)(1 << l);
+            const double Kl[9] = {X.K[0] / sc, X.K[1] / sc, X.K[2] / sc, 0.0, X.K[4] / sc, X.K[5] / sc, 0.0, 0.0, 1.0};
+            memcpy(F.Kl, Kl, sizeof Kl);
+            F.Gl = (X.planes.G0 - 1) / (1 << l) + 1;
+            F.drl = X.planes.drho * sc;
+            F.D = (l == L - 1) ? F.Gl : std::min(cfg.D[l], F.Gl);
+            F.Ds = (F.D + 7) & ~7;
+            FM_TRY(ensure(c, fname(f, "S").c_str(), sizeof(uint16_t) * np * F.Ds, &F.pS));
+            FM_TRY(ensure(c, fname(f, "Sbar").c_str(), sizeof(uint16_t) * np * F.Ds * parts, &F.pSb));
+            FM_TRY(ensure(c, fname(f, "draw").c_str(), sizeof(float) * np, &F.pdraw));
+            FM_TRY(ensure(c, fname(f, "nraw").c_str(), sizeof(float) * 3 * np, &F.pnraw));
+            FM_TRY(ensure(c, fname(f, "cref").c_str(), sizeof(uint64_t) * np, &F.cref));
+            FM_TRY(ensure(c, fname(f, "htab").c_str(), sizeof(float) * 18 * (size_t)F.Gl * F.V, &F.htab));
+            FM_TRY(ensure(c, fname(f, "delta").c_str(), sizeof(float) * (size_t)F.Gl, &F.delta));
+            if (l > 0) {
+                FM_TRY(ensure(c, fname(f, (l & 1) ? "dmedA" : "dmedB").c_str(), sizeof(float) * np, &F.pdmed));
+                FM_TRY(ensure(c, fname(f, (l & 1) ? "nrmA" : "nrmB").c_str(), sizeof(float) * 3 * np, &F.pnrm));
+            } else {
+                F.pdmed = X.depth;
+                F.pnrm = X.normal;
+            }
+            F.plo = nullptr;
+            F.pdI = nullptr;
+            if (l < L - 1) FM_TRY(ensure(c, fname(f, "lo").c_str(), sizeof(int32_t) * np, &F.plo));
+            if (cfg.variant == 1) FM_TRY(ensure(c, fname(f, "dI").c_str(), 8 * np, &F.pdI));
+            const float nf[3] = {(float)X.planes.n[0], (float)X.planes.n[1], (float)X.planes.n[2]};
+            if (l < L - 1) {
+                StageTimer tm(c, FASSMVS_STAGE_WINDOW, st);
+                fm::launch_window(F.dprev, F.Ws[l + 1], F.Hs[l + 1], F.w, F.h, intr(F.Kl), nf, (float)X.planes.rho_far,
+                                  (float)F.drl, F.Gl, F.D, (int32_t*)F.plo, st);
+                if (cfg.variant == 1)
+                    fm::launch_dsn(F.dprev, F.nprev, F.Ws[l + 1], F.Hs[l + 1], F.w, F.h, intr(F.Kl), (float)F.drl,
+                                   cfg.dmax, (int8_t*)F.pdI, st);
+            } else if (cfg.variant == 1) {
+                FM_TRY(cuda_check(c, cudaMemsetAsync(F.pdI, 0, 8 * np, st), "memset dI"));
+            }
+            fm::ViewGeom vg;
+            FM_TRY(view_geom(c, F.Kl, F.V, X.R, X.t, X.planes.n, &vg));
+            fm::LevelPlanes lp{X.planes.rho_far, F.drl, F.Gl, F.V, 0.5 * (F.w - 1), 0.5 * (F.h - 1)};
+            {
+                StageTimer tm(c, FASSMVS_STAGE_CENSUS, st);
+                fm::launch_prep_level(vg, lp, (float*)F.htab, (float*)F.delta, st);
+                fm::launch_census(F.img[l][0], F.w, F.h, F.Ps[l], (uint64_t*)F.cref, st);
+            }
+            // cost arguments
+            fm::CostArgs& a = cargs[f];
+            memset(&a, 0, sizeof a);
+            a.cref = (const uint64_t*)F.cref;
+            for (int k = 0; k < F.V; ++k) {
+                a.views.img[k] = F.img[l][k + 1];
+                a.views.side[k] = X.side[k] < 0 ? -1 : 1;
+            }
+            a.V = F.V; a.W = F.w; a.H = F.h; a.pitch = F.Ps[l];
+            a.nL = F.nL; a.nR = F.nR; a.nmax = F.nmax;
+            a.mL = F.nL ? ((1ull << 32) + F.nL - 1) / F.nL : 0;
+            a.mR = F.nR ? ((1ull << 32) + F.nR - 1) / F.nR : 0;
+            a.htab = (const float*)F.htab;
+            a.lo = (const int32_t*)F.plo;
+            a.D = F.D; a.Ds = F.Ds; a.G = F.Gl;
+            a.S = (uint16_t*)F.pS;
+            // aggregation arguments
+            fm::SgmArgs& g = sargs[f];
+            memset(&g, 0, sizeof g);
+            int p2max = cfg.adaptive_p2 ? 0 : cfg.p2 * F.nmax;
+            if (cfg.adaptive_p2) {
+                g.use_lut = 1;
+                for (int i = 0; i < 256; ++i) { g.lut[i] = F.lut[i]; p2max = std::max(p2max, (int)F.lut[i]); }
+            }
+            p2max = std::max(p2max, F.P1);
+            if ((long long)cfg.paths * (fm::kCensusMax * F.nmax + p2max) >= 65536)
+                return fail(c, FASSMVS_EINVAL, "frame %d: aggregated costs could exceed 16 bits", f);
+            g.S = (const uint16_t*)F.pS; g.lo = (const int32_t*)F.plo; g.dI = (const int8_t*)F.pdI;
+            g.img = F.img[l][0]; g.img_pitch = F.Ps[l];
+            g.W = F.w; g.H = F.h; g.D = F.D; g.Ds = F.Ds;
+            g.paths = cfg.paths; g.variant = cfg.variant; g.p1 = F.P1; g.p2 = cfg.p2 * F.nmax; g.dmax = cfg.dmax;
+            g.Sbar = (uint16_t*)F.pSb;
+            g.part_stride = np * F.Ds;
+            order[f] = f;
+        }
+        // cost work items: larger views x window first, frame by frame
+        std::sort(order.begin(), order.end(), [&](int x, int y) {
+            return (long long)fr[x].V * fr[x].D * fr[x].w * fr[x].h > (long long)fr[y].V * fr[y].D * fr[y].w * fr[y].h;
+        });
+        // plane chunks per tile: fixed size, or (automatic) enough items for
+        // about three waves of the persistent CTAs, chunks of at least 8 planes
+        long long tiles = 0;
+        for (int f = 0; f < n; ++f) tiles += (long long)fm::cost_tiles_x(fr[f].w) * fm::cost_tiles_y(fr[f].h);
+        const int auto_nz = (int)std::max(1LL, (3LL * ctas + tiles - 1) / tiles);
+        for (int f : order) {
+            const FrameRun& F = fr[f];
+            const int nz = chunk_planes > 0 ? std::max(1, (F.D + chunk_planes - 1) / chunk_planes)
+                                            : std::max(1, std::min(auto_nz, (F.D + 7) / 8));
+            const int tx = fm::cost_tiles_x(F.w), ty = fm::cost_tiles_y(F.h);
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ty; ++y)
+                    for (int x = 0; x < tx; ++x) items.push_back(make_int4(f, x, y, z | (nz << 16)));
+        }
+        int4* hitems = (int4*)sg.take(sizeof(int4) * items.size(), at_items);
+        if (!hitems) return fail(c, FASSMVS_EINTERNAL, "staging overflow");
+        memcpy(hitems, items.data(), sizeof(int4) * items.size());
+        FM_TRY(cuda_check(c, cudaMemcpyAsync(sg.dev + block0, sg.host + block0, sg.off - block0, cudaMemcpyHostToDevice, st),
+                          "staging copy"));
+        {
+            StageTimer tm(c, FASSMVS_STAGE_COST, st);
+            fm::launch_cost_batch((const fm::CostArgs*)(sg.dev + at_cargs), (const int4*)(sg.dev + at_items),
+                                  (int)items.size(), (int*)counter, ctas, st);
+        }
+        {
+            StageTimer tm(c, FASSMVS_STAGE_SGM, st);
+            // `parts` partial sums: launch g runs, for every part k, direction
+            // k * (paths / parts) + g into part k (writing it when g == 0), so
+            // `parts` directions run concurrently; frames in groups of up to
+            // kSgmBatch, each group's arguments by value
+            const int per = cfg.paths / parts;
+            for (int f0 = 0; f0 < n; f0 += fm::kSgmBatch) {
+                const int m = std::min(n - f0, fm::kSgmBatch);
+                sb.nframes = m;
+                for (int f = 0; f < m; ++f) sb.a[f] = sargs[f0 + f];
+                for (int g = 0; g < per; ++g) {
+                    // slots with the longest paths first (they start in the first wave)
+                    int order_k[8];
+                    for (int k = 0; k < parts; ++k) order_k[k] = k;
+                    auto plen = [&](int k) {
+                        int dx, dy;
+                        fm::sgm_dir_of(k * per + g, &dx, &dy);
+                        return dy == 0 ? 2 : (dx == 0 ? 1 : 0);
+                    };
+                    std::stable_sort(order_k, order_k + parts, [&](int x, int y) { return plen(x) > plen(y); });
+                    sb.nslots = parts;
+                    int acc = 0;
+                    for (int j = 0; j < parts; ++j) {
+                        const int k = order_k[j], r = k * per + g;
+                        sb.r[j] = r;
+                        fm::sgm_dir_of(r, &sb.dx[j], &sb.dy[j]);
+                        sb.part[j] = k;
+                        sb.first[j] = g == 0;
+                        for (int f = 0; f < m; ++f) {
+                            sb.seg[j][f] = acc;
+                            acc += fm::sgm_lines(fr[f0 + f].w, fr[f0 + f].h, r);
+                        }
+                        sb.seg[j][m] = acc;
+                    }
+                    fm::launch_sgm_batch(sb, st);
+                }
+            }
+        }
+        for (int f = 0; f < n; ++f) {
+            FrameRun& F = fr[f];
+            const fassmvs_frame& X = *F.fr;
+            const float nf[3] = {(float)X.planes.n[0], (float)X.planes.n[1], (float)X.planes.n[2]};
+            {
+                StageTimer tm(c, FASSMVS_STAGE_WTA, st);
+                fm::launch_wta_refine((const uint16_t*)F.pSb, (const int32_t*)F.plo, F.w, F.h, F.D, F.Ds,
+                                      (const float*)F.delta, intr(F.Kl), nf,
+                                      cfg.median5 ? (float*)F.pdraw : (float*)F.pdmed, nullptr, st, parts,
+                                      (size_t)F.w * F.h * F.Ds);
+            }
+            if (cfg.median5) {
+                StageTimer tm(c, FASSMVS_STAGE_MEDIAN, st);
+                fm::launch_median5((const float*)F.pdraw, F.w, F.h, (float*)F.pdmed, st);
+            }
+            {
+                StageTimer tm(c, FASSMVS_STAGE_NORMALS, st);
+                fm::launch_normals((const float*)F.pdmed, F.img[l][0], F.Ps[l], F.w, F.h, intr(F.Kl), cfg.normal_radius,
+                                   cfg.normal_beta, (float*)F.pnraw, (float*)F.pnrm, nf, cfg.rho_deg,
+                                   l == 0 ? X.conf : nullptr, st);
+            }
+            F.dprev = (float*)F.pdmed;
+            F.nprev = (float*)F.pnrm;
+        }
+        FM_TRY(launch_status(c, "level launch"));
+    }
+    FM_TRY(cuda_check(c, cudaEventRecordWithFlags(c->arena_ev[sg.half], st, capturing ? cudaEventRecordExternal : 0),
+                      "staging event"));
+    return FASSMVS_OK;
+}
+
+uint64_t batch_signature(const fassmvs_ctx* c, const fassmvs_frame* fr, int n, const fassmvs_tuning* tn)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+    mix((uint64_t)n);
+    if (tn) { mix((uint64_t)tn->chunk_planes); mix((uint64_t)tn->ctas_per_sm); mix((uint64_t)tn->sgm_parts); }
+    const unsigned char* cb = reinterpret_cast<const unsigned char*>(&c->cfg);
+    for (size_t i = 0; i < sizeof(c->cfg); ++i) mix(cb[i]);
+    for (int f = 0; f < n; ++f) {
+        mix((uint64_t)fr[f].W); mix((uint64_t)fr[f].H); mix((uint64_t)fr[f].pitch);
+        mix((uint64_t)fr[f].n_nb); mix((uint64_t)fr[f].planes.G0);
+    }
+    return h;
+}
+
+fassmvs_status check_tuning(fassmvs_ctx* c, const fassmvs_tuning& t)
+{
+    if (t.chunk_planes < 0 || t.chunk_planes > 256 || t.ctas_per_sm < 1 || t.ctas_per_sm > 2)
+        return fail(c, FASSMVS_EINVAL, "chunk_planes 0 (automatic) or 1..256, ctas_per_sm 1..2");
+    if (t.sgm_parts != 0 && t.sgm_parts != 1 && t.sgm_parts != 2 && t.sgm_parts != 4 && t.sgm_parts != 8)
+        return fail(c, FASSMVS_EINVAL, "sgm_parts 0 (automatic), 1, 2, 4 or 8");
+    return FASSMVS_OK;
+}
+
+fassmvs_status estimate_batch_impl(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cudaStream_t st)
+{
+    if (n < 1 || n > 64) return fail(c, FASSMVS_EINVAL, "1..64 frames per batch");
+    if (!frames) return fail(c, FASSMVS_EINVAL, "frames is NULL");
+    for (int f = 0; f < n; ++f) FM_TRY(check_frame(c, frames[f], c->cfg.levels, f));
+    FM_TRY(set_device(c));
+    c->last = st;
+    fassmvs_tuning tn = c->tune;
+    auto it = c->tuned.find(batch_signature(c, frames, n, nullptr));
+    if (it != c->tuned.end()) tn = it->second;
+    const uint64_t sig = batch_signature(c, frames, n, &tn);
+    Stage sg;
+    FM_TRY(stage_prepare(c, frames, n, tn.chunk_planes, &sg));
+    if (!c->graph || st == nullptr || !c->seen.count(sig)) {
+        // eager (and the first run of a shape: allocates all scratch)
+        FM_TRY(run_batch(c, frames, n, st, tn, sg));
+        c->seen[sig] = 1;
+        return FASSMVS_OK;
+    }
+    FM_TRY(cuda_check(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "begin capture"));
+    fassmvs_status rs = run_batch(c, frames, n, st, tn, sg);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(st, &g);
+    if (rs != FASSMVS_OK) { if (g) cudaGraphDestroy(g); return rs; }
+    FM_TRY(cuda_check(c, ce, "end capture"));
+    cudaGraphExec_t& ex = c->execs[sig];
+    if (ex) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(ex, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ex);
+            ex = nullptr;
+        }
+    }
+    if (!ex) {
+        cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+        if (ie != cudaSuccess) { cudaGraphDestroy(g); ex = nullptr; return cuda_check(c, ie, "graph instantiate"); }
+    }
+    cudaGraphDestroy(g);
+    return cuda_check(c, cudaGraphLaunch(ex, st), "graph launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+fassmvs_status fassmvs_estimate_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, void* stream)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    return estimate_batch_impl(c, frames, n, S(stream));
+}
+
+fassmvs_status fassmvs_set_graph(fassmvs_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    c->graph = on != 0;
+    return FASSMVS_OK;
+}
+
+fassmvs_status fassmvs_set_tuning(fassmvs_ctx* c, const fassmvs_tuning* t)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (!t) return fail(c, FASSMVS_EINVAL, "tuning is NULL");
+    FM_TRY(check_tuning(c, *t));
+    c->tune = *t;
+    c->tuned.clear();
+    return FASSMVS_OK;
+}
+
+fassmvs_status fassmvs_autotune(fassmvs_ctx* c, const fassmvs_frame* frames, int n, void* stream,
+                                fassmvs_tuning* chosen)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (n < 1 || n > 64 || !frames) return fail(c, FASSMVS_EINVAL, "1..64 frames");
+    for (int f = 0; f < n; ++f) FM_TRY(check_frame(c, frames[f], c->cfg.levels, f));
+    FM_TRY(set_device(c));
+    cudaStream_t st = S(stream);
+    // candidates: plane chunks of the persistent cost kernel x resident CTAs
+    // x partial sums of the aggregation (directions run concurrently)
+    std::vector<fassmvs_tuning> cand;
+    for (int parts : {2, 4, 8}) {
+        if (parts > c->cfg.paths) continue;
+        for (int chunk : {0, 64}) cand.push_back({chunk, 2, parts});
+    }
+    cand.push_back({0, 1, 0});
+    cudaEvent_t e0, e1;
+    FM_TRY(cuda_check(c, cudaEventCreate(&e0), "event"));
+    FM_TRY(cuda_check(c, cudaEventCreate(&e1), "event"));
+    const bool prof = c->prof;
+    c->prof = false;
+    float best = 1e30f;
+    fassmvs_tuning bt = c->tune;
+    Stage sg;
+    fassmvs_status rs = FASSMVS_OK;
+    for (size_t i = 0; i <= cand.size() && rs == FASSMVS_OK; ++i) {
+        // the first pass (the current setting) allocates scratch and warms up
+        const fassmvs_tuning t = i == 0 ? c->tune : cand[i - 1];
+        if ((rs = stage_prepare(c, frames, n, t.chunk_planes, &sg)) != FASSMVS_OK) break;
+        cudaEventRecord(e0, st);
+        rs = run_batch(c, frames, n, st, t, sg);
+        cudaEventRecord(e1, st);
+        if (rs != FASSMVS_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rs = cuda_check(c, cudaGetLastError(), "autotune"); break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (i > 0 && ms < best) { best = ms; bt = t; }
+    }
+    c->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rs != FASSMVS_OK) return rs;
+    const uint64_t shape = batch_signature(c, frames, n, nullptr);
+    c->tuned[shape] = bt;
+    if (chosen) *chosen = bt;
+    if (const char* path = getenv("FASSMVS_TUNE_FILE")) {
+        if (FILE* fp = fopen(path, "a")) {
+            fprintf(fp, "{\"frames\": %d, \"shape\": \"%016llx\", \"chunk_planes\": %d, \"ctas_per_sm\": %d, "
+                        "\"sgm_parts\": %d, \"ms\": %.3f}\n",
+                    n, (unsigned long long)shape, bt.chunk_planes, bt.ctas_per_sm, bt.sgm_parts, best);
+            fclose(fp);
+        }
+    }
+    return FASSMVS_OK;
+}
+
 fassmvs_status fassmvs_estimate(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch,
                                 const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* pl, float* depth,
                                 float* normal, float* conf, void* stream)
 {
     if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
     if (!c->cams) return fail(c, FASSMVS_EINVAL, "fassmvs_set_cameras was not called");
-    if (!ref || !nbrs || !pl || !depth || !normal || !conf) return fail(c, FASSMVS_EINVAL, "NULL argument");
+    if (!pl) return fail(c, FASSMVS_EINVAL, "NULL argument");
     if (n_nb != c->V) return fail(c, FASSMVS_EINVAL, "n_nb %d differs from the %d cameras set", n_nb, c->V);
-    if (W < 2 || H < 2 || pitch < W) return fail(c, FASSMVS_EINVAL, "bad image size or pitch");
-    const fassmvs_config& cfg = c->cfg;
-    const int L = cfg.levels;
-    if (((W - 1) >> (L - 1)) + 1 < 2 || ((H - 1) >> (L - 1)) + 1 < 2)
-        return fail(c, FASSMVS_EINVAL, "image too small for %d levels", L);
-    if (pl->G0 < 1) return fail(c, FASSMVS_EINVAL, "G0 must be >= 1");
-    const int Gtop = (pl->G0 - 1) / (1 << (L - 1)) + 1;
-    if (Gtop > fm::kMaxSlots) return fail(c, FASSMVS_EINVAL, "top level has %d planes (> 256, Sec. 3.2 cap)", Gtop);
-    FM_TRY(set_device(c));
-    cudaStream_t st = S(stream);
-    c->last = st;
-    const int V = c->V;
-    int nL = 0, nR = 0;
-    for (int k = 0; k < V; ++k) { if (c->side[k] < 0) ++nL; else ++nR; }
-    const int nmax = nL > nR ? nL : nR;
-    const int P1 = cfg.p1 * nmax;
-    uint16_t lut[256];
-    p2_table(P1, cfg.alpha, cfg.beta, lut);
-    fassmvs_sgm_params prm{cfg.paths, cfg.variant, P1, cfg.p2 * nmax, cfg.dmax, cfg.adaptive_p2 ? lut : nullptr};
-
-    // image pyramids (level 0 is the caller's)
-    int Ws[8], Hs[8], Ps[8];
-    const uint8_t* img[8][fm::kMaxViews + 1];
-    Ws[0] = W; Hs[0] = H; Ps[0] = pitch;
-    img[0][0] = ref;
-    for (int k = 0; k < V; ++k) img[0][k + 1] = nbrs[k];
-    StageTimer* tpyr = new StageTimer(c, FASSMVS_STAGE_PYRAMID, st);
-    for (int l = 1; l < L; ++l) {
-        Ws[l] = (Ws[l - 1] + 1) / 2;
-        Hs[l] = (Hs[l - 1] + 1) / 2;
-        Ps[l] = Ws[l];
-        void* p;
-        char name[32];
-        snprintf(name, sizeof name, "pyr%d", l);
-        fassmvs_status es = ensure(c, name, (size_t)(V + 1) * Ws[l] * Hs[l], &p);
-        if (es != FASSMVS_OK) { delete tpyr; return es; }
-        for (int k = 0; k <= V; ++k) {
-            uint8_t* o = (uint8_t*)p + (size_t)k * Ws[l] * Hs[l];
-            fm::launch_pyramid_down(img[l - 1][k], Ws[l - 1], Hs[l - 1], Ps[l - 1], o, Ps[l], st);
-            img[l][k] = o;
-        }
-    }
-    delete tpyr;
-    float* dprev = nullptr;
-    float* nprev = nullptr;
-    for (int l = L - 1; l >= 0; --l) {
-        const int w = Ws[l], h = Hs[l];
-        const size_t np = (size_t)w * h;
-        const double sc = (double)(1 << l);
-        const double Kl[9] = {c->K[0] / sc, c->K[1] / sc, c->K[2] / sc, 0.0, c->K[4] / sc, c->K[5] / sc, 0.0, 0.0, 1.0};
-        const int Gl = (pl->G0 - 1) / (1 << l) + 1;
-        const double drl = pl->drho * sc;
-        const int D = (l == L - 1) ? Gl : (cfg.D[l] < Gl ? cfg.D[l] : Gl);
-        const int Ds = (D + 7) & ~7;
-        void *pS, *pSb, *pdraw, *pdmed, *pnraw, *pnrm, *plo = nullptr, *pdI = nullptr;
-        FM_TRY(ensure(c, "S", sizeof(uint16_t) * np * Ds, &pS));
-        FM_TRY(ensure(c, "Sbar", sizeof(uint16_t) * np * Ds, &pSb));
-        FM_TRY(ensure(c, "draw", sizeof(float) * np, &pdraw));
-        FM_TRY(ensure(c, "nraw", sizeof(float) * 3 * np, &pnraw));
-        if (l > 0) {
-            FM_TRY(ensure(c, (l & 1) ? "dmedA" : "dmedB", sizeof(float) * np, &pdmed));
-            FM_TRY(ensure(c, (l & 1) ? "nrmA" : "nrmB", sizeof(float) * 3 * np, &pnrm));
-        } else {
-            pdmed = depth;
-            pnrm = normal;
-        }
-        if (l < L - 1) {
-            FM_TRY(ensure(c, "lo", sizeof(int32_t) * np, &plo));
-            if (cfg.variant == 1) FM_TRY(ensure(c, "dI", 8 * np, &pdI));
-            StageTimer tm(c, FASSMVS_STAGE_WINDOW, st);
-            float nf[3] = {(float)pl->n[0], (float)pl->n[1], (float)pl->n[2]};
-            fm::launch_window(dprev, Ws[l + 1], Hs[l + 1], w, h, intr(Kl), nf, (float)pl->rho_far, (float)drl, Gl, D,
-                              (int32_t*)plo, st);
-            if (cfg.variant == 1) {
-                fm::launch_dsn(dprev, nprev, Ws[l + 1], Hs[l + 1], w, h, intr(Kl), (float)drl, cfg.dmax, (int8_t*)pdI, st);
-            }
-        } else if (cfg.variant == 1) {
-            FM_TRY(ensure(c, "dI", 8 * np, &pdI));
-            FM_TRY(cuda_check(c, cudaMemsetAsync(pdI, 0, 8 * np, st), "memset dI"));
-        }
-        FM_TRY(cost_volume_impl(c, img[l][0], &img[l][1], V, c->side.data(), w, h, Ps[l], Kl, c->R.data(),
-                                c->t.data(), pl->n, pl->rho_far, drl, Gl, (const int32_t*)plo, D, Ds,
-                                (uint16_t*)pS, st));
-        FM_TRY(sgm_impl(c, (const uint16_t*)pS, (const int32_t*)plo, (const int8_t*)pdI, img[l][0], Ps[l], w, h, D, Ds,
-                        &prm, fm::kCensusMax * nmax, (uint16_t*)pSb, st));
-        void* delta;
-        FM_TRY(ensure(c, "delta", sizeof(float) * (size_t)Gl, &delta));
-        float nf[3] = {(float)pl->n[0], (float)pl->n[1], (float)pl->n[2]};
-        {
-            StageTimer tm(c, FASSMVS_STAGE_WTA, st);
-            fm::launch_wta_refine((const uint16_t*)pSb, (const int32_t*)plo, w, h, D, Ds, (const float*)delta, intr(Kl),
-                                  nf, cfg.median5 ? (float*)pdraw : (float*)pdmed, nullptr, st);
-        }
-        if (cfg.median5) {
-            StageTimer tm(c, FASSMVS_STAGE_MEDIAN, st);
-            fm::launch_median5((const float*)pdraw, w, h, (float*)pdmed, st);
-        }
-        StageTimer tmn(c, FASSMVS_STAGE_NORMALS, st);
-        fm::launch_normals((const float*)pdmed, img[l][0], Ps[l], w, h, intr(Kl), cfg.normal_radius, cfg.normal_beta,
-                           (float*)pnraw, (float*)pnrm, nf, cfg.rho_deg, l == 0 ? conf : nullptr, st);
-        FM_TRY(launch_status(c, "level launch"));
-        dprev = (float*)pdmed;
-        nprev = (float*)pnrm;
-    }
-    return FASSMVS_OK;
+    fassmvs_frame f;
+    f.ref = ref; f.nbrs = nbrs; f.W = W; f.H = H; f.pitch = pitch; f.n_nb = n_nb;
+    f.K = c->K; f.R = c->R.data(); f.t = c->t.data(); f.side = c->side.data();
+    f.planes = *pl;
+    f.depth = depth; f.normal = normal; f.conf = conf;
+    return estimate_batch_impl(c, &f, 1, S(stream));
 }
 
 fassmvs_status fassmvs_profile_enable(fassmvs_ctx* c, int on)

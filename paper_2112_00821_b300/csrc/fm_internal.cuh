@@ -52,6 +52,11 @@ struct CostArgs {
     uint16_t* S;
 };
 void launch_cost(const CostArgs& a, cudaStream_t st);
+// persistent multi-frame form: items[i] = (frame, tile x, tile y, chunk | chunks << 16)
+void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas,
+                       cudaStream_t st);
+int cost_tiles_x(int W);
+int cost_tiles_y(int H);
 
 // ---------------------------------------------------------------- SGM
 struct SgmArgs {
@@ -64,8 +69,26 @@ struct SgmArgs {
     int use_lut;
     uint16_t lut[256];
     uint16_t* Sbar;
+    size_t part_stride;           // elements between partial sums (batch form)
 };
 void launch_sgm(const SgmArgs& a, cudaStream_t st);
+// path lines of direction r for a W x H image, padded to whole CTAs
+int sgm_lines(int W, int H, int r);
+// multi-frame, multi-direction form: up to kSgmBatch frames and 8 direction
+// slots per launch, passed by value.  Slot j runs direction r[j] (steps
+// dx[j], dy[j]) into partial sum part[j] (at Sbar + part * part_stride of each
+// frame), writing it when first[j], else adding to it.  seg[j][f] is the first
+// path line of (slot j, frame f), padded to whole CTAs; seg[j][nframes] ==
+// seg[j + 1][0] and seg[nslots - 1][nframes] is the total.
+constexpr int kSgmBatch = 32;
+struct SgmBatch {
+    SgmArgs a[kSgmBatch];
+    int nframes, nslots;
+    int r[8], dx[8], dy[8], part[8], first[8];
+    int seg[8][kSgmBatch + 1];
+};
+void sgm_dir_of(int r, int* dx, int* dy);
+void launch_sgm_batch(const SgmBatch& b, cudaStream_t st);
 
 // ---------------------------------------------------------------- per-pixel stages
 void launch_pyramid_down(const uint8_t* in, int W, int H, int pitch_in, uint8_t* out,
@@ -76,9 +99,10 @@ struct Intr {
     float fx, fy, cx, cy;
 };
 
+// Sbar may hold nparts partial sums, part_stride elements apart (summed here)
 void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
-                       cudaStream_t st);
+                       cudaStream_t st, int nparts = 1, size_t part_stride = 0);
 void launch_delta_table(double rho0, double drho, int G, float* delta, cudaStream_t st);
 void launch_median5(const float* in, int W, int H, float* out, cudaStream_t st);
 void launch_normals(const float* depth, const uint8_t* img, int img_pitch, int W, int H, Intr K,

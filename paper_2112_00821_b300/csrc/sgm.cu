@@ -68,14 +68,12 @@ constexpr uint32_t INF2 = INF16 | (INF16 << 16);
 
 __device__ __forceinline__ uint32_t dup2(uint32_t v) { return v | (v << 16); }
 
-__global__ void __launch_bounds__(WARPS * 32)
-sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
+// One path line of direction r (line index in the order described at the
+// launcher), run by one warp with its private shared buffers.
+__device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict__ Sb, int r, int dx, int dy,
+                                         int line, int first, uint16_t* buf, uint4 (*rg)[2][32])
 {
-    __shared__ uint16_t sT[WARPS][kMaxSlots + 4];
-    __shared__ uint4 ring[WARPS][PF][2][32];   // [step][S, S_bar][lane]
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int line = blockIdx.x * WARPS + warp;
-    if (line >= nlines) return;                // warp-uniform
+    const int lane = threadIdx.x & 31;
     const int W = a.W, H = a.H, D = a.D;
     int x0, y0;
     if (dy == 0) { x0 = dx > 0 ? 0 : W - 1; y0 = line; }
@@ -101,10 +99,12 @@ sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
     int g1 = 0, g2 = 0;                        // winning plane of p - r and p - 2r (path gradient)
     int lo_prev = 0, ipix_prev = 0;
     const uint32_t P1 = (uint32_t)a.p1, P1P1 = dup2(P1);
-    uint16_t* buf = sT[warp];
 
-    uint4(*rg)[2][32] = ring[warp];
-    StepScal q[PF];
+    // per-step scalars (window start, intensity, index jump) are fetched PF
+    // steps ahead and spread over the lanes: lane u holds those of the steps
+    // congruent to u modulo PF, broadcast when the step comes
+    StepScal q{0, 0, 0};
+    if (lane < PF && lane < n) load_scal(a, r, x0 + lane * dx, y0 + lane * dy, q);
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
         if (u < n) {
@@ -112,9 +112,8 @@ sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
             const size_t pp = ((size_t)yy * W + xx) * a.Ds + s0;
             if (act) {
                 cp_async16(&rg[u][0][lane], a.S + pp);
-                if (!first) cp_async16(&rg[u][1][lane], a.Sbar + pp);
+                if (!first) cp_async16(&rg[u][1][lane], Sb + pp);
             }
-            load_scal(a, r, xx, yy, q[u]);
         }
         cp_async_commit();
     }
@@ -126,7 +125,9 @@ sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
             if (step >= n) break;              // warp-uniform
             const int x = x0 + step * dx, y = y0 + step * dy;
             const size_t pix = (size_t)y * W + x;
-            const StepScal cur = q[u];
+            const int lo_p = __shfl_sync(FULL, q.lo, u);
+            const int pk = __shfl_sync(FULL, (q.ipix & 0xFF) | (q.dsn * 256), u);
+            const int cur_ipix = pk & 0xFF, cur_dsn = pk >> 8;
             cp_async_wait<PF - 1>();           // this step's group has landed
             const uint4 sraw = rg[u][0][lane];
             const uint4 acc = rg[u][1][lane];
@@ -136,26 +137,25 @@ sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
                 const size_t pp = ((size_t)yy * W + xx) * a.Ds + s0;
                 if (act) {
                     cp_async16(&rg[u][0][lane], a.S + pp);
-                    if (!first) cp_async16(&rg[u][1][lane], a.Sbar + pp);
+                    if (!first) cp_async16(&rg[u][1][lane], Sb + pp);
                 }
-                load_scal(a, r, xx, yy, q[u]);
+                if (lane == u) load_scal(a, r, xx, yy, q);
             }
             cp_async_commit();
             const uint32_t Sv[4] = {sraw.x, sraw.y, sraw.z, sraw.w};
-            const int lo_p = cur.lo;
             uint32_t L[4];
             if (step == 0) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) L[j] = (Sv[j] & vmask[j]) | (INF2 & ~vmask[j]);
             } else {
                 int di = 0;
-                if (a.variant == 1) di = cur.dsn;
+                if (a.variant == 1) di = cur_dsn;
                 else if (a.variant == 2 && step >= 2) di = g2 - g1;
                 di = min(max(di, -a.dmax), a.dmax);
                 const int sigma = lo_p - lo_prev + di;
                 int P2 = a.p2;
                 if (a.use_lut) {
-                    int d = cur.ipix - ipix_prev;
+                    int d = cur_ipix - ipix_prev;
                     P2 = a.lut[d < 0 ? -d : d];
                 }
                 P2 = max(P2, a.p1);
@@ -235,20 +235,78 @@ sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
                     o = make_uint4(acc.x + (L[0] & vmask[0]), acc.y + (L[1] & vmask[1]),
                                    acc.z + (L[2] & vmask[2]), acc.w + (L[3] & vmask[3]));
                 }
-                *reinterpret_cast<uint4*>(a.Sbar + pix * a.Ds + s0) = o;
+                *reinterpret_cast<uint4*>(Sb + pix * a.Ds + s0) = o;
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) Lp[j] = L[j];
             lo_prev = lo_p;
-            ipix_prev = cur.ipix;
+            ipix_prev = cur_ipix;
         }
     }
+}
+
+__global__ void __launch_bounds__(WARPS * 32, 4)
+sgm_dir_kernel(const SgmArgs a, int r, int dx, int dy, int nlines, int first)
+{
+    __shared__ uint16_t sT[WARPS][kMaxSlots + 4];
+    __shared__ uint4 ring[WARPS][PF][2][32];   // [step][S, S_bar][lane]
+    const int warp = threadIdx.x >> 5;
+    const int line = blockIdx.x * WARPS + warp;
+    if (line >= nlines) return;                // warp-uniform
+    sgm_line(a, a.Sbar, r, dx, dy, line, first, sT[warp], ring[warp]);
+}
+
+// Several directions of several frames in one launch.  Direction slot j of
+// the launch runs direction b.r[j] into partial sum b.part[j] of every frame
+// (b.first[j]: the slot writes that part instead of adding to it); the lines
+// of (slot j, frame f) start at CTA line b.seg[j][f], each range padded to
+// whole CTAs so the slot and frame are uniform across a CTA.  The arguments
+// are one by-value kernel parameter (grid constant, so indexed reads stay in
+// the constant bank).
+__global__ void __launch_bounds__(WARPS * 32, 4)
+sgm_batch_dir_kernel(const __grid_constant__ SgmBatch b)
+{
+    __shared__ uint16_t sT[WARPS][kMaxSlots + 4];
+    __shared__ uint4 ring[WARPS][PF][2][32];
+    const int cta_line = blockIdx.x * WARPS;
+    int j = 0;
+    while (j + 1 < b.nslots && b.seg[j + 1][0] <= cta_line) ++j;
+    int f = 0;
+    while (f + 1 < b.nframes && b.seg[j][f + 1] <= cta_line) ++f;
+    const SgmArgs& a = b.a[f];
+    const int r = b.r[j], dx = b.dx[j], dy = b.dy[j];
+    const int warp = threadIdx.x >> 5;
+    const int line = cta_line - b.seg[j][f] + warp;
+    const int nlines = dy == 0 ? a.H : (dx == 0 ? a.W : a.W + a.H - 1);
+    if (line >= nlines) return;                 // warp-uniform
+    sgm_line(a, a.Sbar + (size_t)b.part[j] * a.part_stride, r, dx, dy, line, b.first[j], sT[warp], ring[warp]);
 }
 
 const int kDX[8] = {1, -1, 0, 0, 1, -1, 1, -1};
 const int kDY[8] = {0, 0, 1, -1, 1, -1, -1, 1};
 
 }  // namespace
+
+int sgm_lines(int W, int H, int r)
+{
+    const int dx = kDX[r], dy = kDY[r];
+    const int n = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
+    return (n + WARPS - 1) / WARPS * WARPS;     // whole CTAs per frame
+}
+
+void sgm_dir_of(int r, int* dx, int* dy)
+{
+    *dx = kDX[r];
+    *dy = kDY[r];
+}
+
+void launch_sgm_batch(const SgmBatch& b, cudaStream_t st)
+{
+    const int blocks = b.seg[b.nslots - 1][b.nframes] / WARPS;
+    if (blocks == 0) return;
+    sgm_batch_dir_kernel<<<blocks, WARPS * 32, 0, st>>>(b);
+    count_launch();
+}
 
 void launch_sgm(const SgmArgs& a, cudaStream_t st)
 {

@@ -60,9 +60,12 @@ __global__ void census_kernel(const uint8_t* __restrict__ img, int W, int H, int
 }
 
 // ---------------------------------------------------------------- WTA + refinement
+// Sbar may be split into nparts partial sums (part_stride elements apart):
+// their packed pairs add without carries, as every total stays below 2^16.
 __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __restrict__ lo, int W,
                            int H, int D, int Ds, const float* __restrict__ delta, Intr K, float n0,
-                           float n1, float n2, float* __restrict__ depth, int32_t* __restrict__ gwin)
+                           float n1, float n2, float* __restrict__ depth, int32_t* __restrict__ gwin,
+                           int nparts, size_t part_stride)
 {
     const int lane = threadIdx.x & 31;
     const size_t p = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -70,7 +73,14 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
     const int s0 = lane * 8;
     uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (s0 < D) {
-        uint4 raw = __ldg(reinterpret_cast<const uint4*>(Sbar + p * Ds + s0));
+        const uint4* src = reinterpret_cast<const uint4*>(Sbar + p * Ds + s0);
+        uint4 raw = __ldg(src);
+#pragma unroll
+        for (int k = 1; k < 8; ++k)
+            if (k < nparts) {
+                const uint4 t = __ldg(reinterpret_cast<const uint4*>(Sbar + k * part_stride + p * Ds + s0));
+                raw.x += t.x; raw.y += t.y; raw.z += t.z; raw.w += t.w;
+            }
         v[0] = raw.x & 0xFFFF; v[1] = raw.x >> 16; v[2] = raw.y & 0xFFFF; v[3] = raw.y >> 16;
         v[4] = raw.z & 0xFFFF; v[5] = raw.z >> 16; v[6] = raw.w & 0xFFFF; v[7] = raw.w >> 16;
     }
@@ -298,12 +308,13 @@ void launch_census(const uint8_t* img, int W, int H, int pitch, uint64_t* out, c
 
 void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
-                       cudaStream_t st)
+                       cudaStream_t st, int nparts, size_t part_stride)
 {
     size_t np = (size_t)W * H;
     int per = 8;
     wta_kernel<<<(unsigned)((np + per - 1) / per), per * 32, 0, st>>>(Sbar, lo, W, H, D, Ds, delta, K, n[0],
-                                                                  n[1], n[2], depth, gwin);
+                                                                  n[1], n[2], depth, gwin, nparts,
+                                                                  part_stride);
     count_launch();
 }
 

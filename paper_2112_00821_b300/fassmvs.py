@@ -39,6 +39,17 @@ class Config(C.Structure):
                 ("rho_deg", C.c_float), ("dmax", C.c_int32)]
 
 
+class Frame(C.Structure):
+    _fields_ = [("ref", C.c_void_p), ("nbrs", C.c_void_p), ("W", C.c_int32), ("H", C.c_int32),
+                ("pitch", C.c_int32), ("n_nb", C.c_int32), ("K", C.c_void_p), ("R", C.c_void_p),
+                ("t", C.c_void_p), ("side", C.c_void_p), ("planes", Planes), ("depth", C.c_void_p),
+                ("normal", C.c_void_p), ("conf", C.c_void_p)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("chunk_planes", C.c_int32), ("ctas_per_sm", C.c_int32), ("sgm_parts", C.c_int32)]
+
+
 class SgmParams(C.Structure):
     _fields_ = [("paths", C.c_int32), ("variant", C.c_int32), ("p1", C.c_int32),
                 ("p2", C.c_int32), ("dmax", C.c_int32), ("p2_lut", C.c_void_p)]
@@ -69,6 +80,10 @@ _SIGS = {
                        C.c_double, C.c_int, C.c_int, _VP, _VP],
     "fassmvs_dsn": [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, C.c_double, C.c_int,
                     _VP, _VP],
+    "fassmvs_estimate_batch": [_VP, _VP, C.c_int, _VP],
+    "fassmvs_set_graph": [_VP, C.c_int],
+    "fassmvs_set_tuning": [_VP, _VP],
+    "fassmvs_autotune": [_VP, _VP, C.c_int, _VP, _VP],
     "fassmvs_profile_enable": [_VP, C.c_int],
     "fassmvs_profile_read": [_VP, _VP, _VP, C.c_int],
     "fassmvs_sync": [_VP],
@@ -178,6 +193,71 @@ class Context:
                                            C.byref(planes), _ptr(depth), _ptr(normal), _ptr(conf),
                                            _stream()))
         return depth, normal, conf
+
+    # ------------------------------------------------------------ batched form
+    @staticmethod
+    def _frames(items):
+        """fassmvs_frame array of `items`: dicts with ref, nbrs, K, R, t, side,
+        planes (a Planes) and optional depth / normal / conf tensors (allocated
+        here when absent).  Returns (array, keep-alive list, outputs)."""
+        import torch
+        arr = (Frame * len(items))()
+        keep, outs = [], []
+        for i, it in enumerate(items):
+            ref, nbrs = it["ref"], it["nbrs"]
+            H, W = ref.shape
+            pitch = ref.stride(0)
+            for x in nbrs:
+                if x.shape != ref.shape or x.stride(0) != pitch or x.dtype != torch.uint8:
+                    raise ValueError("neighbours must match the reference layout")
+            V = len(nbrs)
+            dev = ref.device
+            depth = it.get("depth")
+            depth = depth if depth is not None else torch.empty((H, W), dtype=torch.float32, device=dev)
+            normal = it.get("normal")
+            normal = normal if normal is not None else torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+            conf = it.get("conf")
+            conf = conf if conf is not None else torch.empty((H, W), dtype=torch.float32, device=dev)
+            nb = (C.c_void_p * V)(*[x.data_ptr() for x in nbrs])
+            k_, kp = _dbl(it["K"], 9)
+            r_, rp = _dbl(it["R"], 9 * V)
+            t_, tp = _dbl(it["t"], 3 * V)
+            s_ = np.ascontiguousarray(it["side"], dtype=np.int8)
+            if s_.size != V:
+                raise ValueError("one side per neighbour")
+            keep += [nb, k_, r_, t_, s_]
+            f = arr[i]
+            f.ref = ref.data_ptr()
+            f.nbrs = C.cast(nb, C.c_void_p)
+            f.W, f.H, f.pitch, f.n_nb = W, H, pitch, V
+            f.K, f.R, f.t = kp, rp, tp
+            f.side = s_.ctypes.data_as(C.c_void_p)
+            f.planes = it["planes"]
+            f.depth, f.normal, f.conf = depth.data_ptr(), normal.data_ptr(), conf.data_ptr()
+            outs.append((depth, normal, conf))
+        return arr, keep, outs
+
+    def estimate_batch(self, items):
+        """fassmvs_estimate_batch; returns [(depth, normal, conf)] per frame."""
+        arr, keep, outs = self._frames(items)
+        self._check(lib().fassmvs_estimate_batch(self._h, arr, len(items), _stream()))
+        return outs
+
+    def set_graph(self, on=True):
+        self._check(lib().fassmvs_set_graph(self._h, 1 if on else 0))
+
+    def set_tuning(self, chunk_planes=0, ctas_per_sm=2, sgm_parts=0):
+        t = Tuning(int(chunk_planes), int(ctas_per_sm), int(sgm_parts))
+        self._check(lib().fassmvs_set_tuning(self._h, C.byref(t)))
+
+    def autotune(self, items):
+        """Times the work decompositions on this batch; returns the chosen
+        (chunk_planes, ctas_per_sm, sgm_parts), kept for batches of the same
+        shapes."""
+        arr, keep, outs = self._frames(items)
+        t = Tuning()
+        self._check(lib().fassmvs_autotune(self._h, arr, len(items), _stream(), C.byref(t)))
+        return t.chunk_planes, t.ctas_per_sm, t.sgm_parts
 
     def sync(self):
         self._check(lib().fassmvs_sync(self._h))

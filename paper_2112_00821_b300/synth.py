@@ -31,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "Quad", "Frame", "Scene", "render_view", "make_scene", "make_frame",
-    "WORKLOADS", "workload", "box_quads", "trajectory_frames",
+    "WORKLOADS", "workload", "box_quads", "trajectory_frames", "BATCH_SIZES", "batch_frames",
 ]
 
 
@@ -478,6 +478,40 @@ def workload(name, seed=0, want_gt=True):
         cfg = dict(levels=4, D=[256, 256, 256, 256], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1)
         return sc, cfg
     raise KeyError(name)
+
+
+BATCH_SIZES = ((640, 480), (1280, 720), (1920, 1080), (2720, 1530))
+
+
+def batch_frames(seed=0, n=16):
+    """The mixed batch: n reference frames whose sizes are drawn from
+    BATCH_SIZES, plane counts from 64..256 (multiples of 32) and neighbour
+    counts from 3..6, all of the 45 deg oblique city (depth 20-300 m).
+
+    Frames of one size share the images of one rendered bundle (3 left + 3
+    right views): a frame with n_nb neighbours takes the n_nb // 2 nearest left
+    and the rest nearest right views of it, and its own plane list.  This keeps
+    the rendering at one bundle per size; the estimates of two such frames
+    differ through their views and planes."""
+    g = np.random.Generator(np.random.PCG64(seed + 271))
+    picks = [(int(g.integers(0, len(BATCH_SIZES))), int(g.integers(2, 9)) * 32, int(g.integers(3, 7)))
+             for _ in range(n)]
+    bundles = {}
+    out = []
+    for si, G0, nn in picks:
+        if si not in bundles:
+            W, H = BATCH_SIZES[si]
+            bundles[si] = make_frame("city", 7 * seed + si, W=W, H=H, G0=256, n_left=3, n_right=3,
+                                     want_gt=False)
+        b = bundles[si]
+        nl = nn // 2
+        nr = nn - nl
+        idx = list(range(3 - nl, 3)) + list(range(3, 3 + nr))
+        rho_far, drho = _sweep(20.0, 300.0, G0)
+        out.append(Scene(b.W, b.H, b.K, b.ref, [b.nbrs[i] for i in idx], b.R[idx].copy(), b.t[idx].copy(),
+                         b.side[idx].copy(), b.plane_n.copy(), rho_far, drho, G0,
+                         meta={"size_class": si, "bundle_views": idx}))
+    return out
 
 
 def trajectory_frames(n_frames, W, H, seed, speed=0.6, every=5, n_nb=(4, 6), G0=(128, 256)):

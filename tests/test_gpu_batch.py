@@ -1,0 +1,164 @@
+"""Batched form of the estimate (fassmvs_estimate_batch).
+
+A batch shares launches across frames (one persistent cost kernel over the
+(frame, tile, plane chunk) work items of every frame, one aggregation launch
+per direction over the path lines of every frame), so each result must equal,
+bit for bit, that of one fassmvs_estimate per frame; the per-frame estimate is
+itself checked against the oracle in test_gpu_parity.py, and one batched frame
+is checked against the oracle here as well.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _frames(seeds=(0, 1, 2, 3)):
+    """Frames of mixed size, view count and plane count (ragged sizes
+    included)."""
+    from paper_2112_00821_b300 import synth
+    return [
+        synth.make_frame("planes", 40 + seeds[0], W=200, H=150, G0=128, n_left=2, n_right=2, want_gt=False),
+        synth.make_frame("planes", 40 + seeds[1], W=131, H=97, G0=96, n_left=1, n_right=2, want_gt=False),
+        synth.make_frame("city", 40 + seeds[2], W=240, H=136, G0=256, n_left=2, n_right=3, want_gt=False),
+        synth.make_frame("tiny", 40 + seeds[3], W=160, H=120, G0=64, n_left=1, n_right=1),
+    ]
+
+
+def _item(sc):
+    from paper_2112_00821_b300 import fassmvs
+    return dict(ref=torch.from_numpy(sc.ref).cuda(), nbrs=[torch.from_numpy(x).cuda() for x in sc.nbrs],
+                K=sc.K, R=sc.R, t=sc.t, side=sc.side, planes=fassmvs.planes_of(sc))
+
+
+def _cfg(variant):
+    from paper_2112_00821_b300 import fassmvs
+    return fassmvs.default_config(levels=3, D=[32, 32, 32], paths=8, variant=variant, p1=24, p2=0,
+                                  adaptive_p2=1)
+
+
+def _single(cfg, items):
+    from paper_2112_00821_b300 import fassmvs
+    out = []
+    for it in items:
+        c = fassmvs.Context(cfg)
+        c.set_cameras(it["K"], it["R"], it["t"], it["side"])
+        out.append(c.estimate(it["ref"], it["nbrs"], it["planes"]))
+        c.sync()
+        c.close()
+    return out
+
+
+def _same(a, b):
+    for (d0, n0, c0), (d1, n1, c1) in zip(a, b):
+        assert torch.equal(d0, d1)
+        assert torch.equal(n0, n1)
+        assert torch.equal(c0, c1)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_batch_equals_one_estimate_per_frame(variant):
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs
+    items = [_item(sc) for sc in _frames()]
+    cfg = _cfg(variant)
+    ref = _single(cfg, items)
+    ctx = fassmvs.Context(cfg)
+    got = ctx.estimate_batch(items)
+    ctx.sync()
+    _same(got, ref)
+    # a second call on the same context (scratch and staging reused) and a
+    # call with the frames in another order
+    got2 = ctx.estimate_batch(items[::-1])[::-1]
+    ctx.sync()
+    _same(got2, ref)
+    ctx.close()
+
+
+def test_batched_frame_against_oracle(orc):
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs
+    scs = _frames()
+    items = [_item(sc) for sc in scs]
+    kw = dict(levels=3, D=[32, 32, 32], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1)
+    ctx = fassmvs.Context(fassmvs.default_config(**kw))
+    got = ctx.estimate_batch(items)
+    ctx.sync()
+    d = got[1][0].cpu().numpy()
+    d_e, n_e, c_e = orc.estimate(scs[1], orc.make_config(**kw))
+    rel = np.abs(d - d_e) / d_e
+    assert np.mean(rel) <= 1e-3, np.mean(rel)
+    assert np.mean(np.abs(got[1][2].cpu().numpy() - c_e)) < 2e-3
+    ctx.close()
+
+
+def test_graph_replay_matches_eager():
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs
+    cfg = _cfg(2)
+    A = [_item(sc) for sc in _frames((0, 1, 2, 3))]
+    B = [_item(sc) for sc in _frames((5, 6, 7, 8))]       # same shapes, other scenes
+    ref_a, ref_b = _single(cfg, A), _single(cfg, B)
+    ctx = fassmvs.Context(cfg)
+    ctx.set_graph(True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        first = ctx.estimate_batch(A)        # first run of these shapes: eager
+        ga = ctx.estimate_batch(A)           # captured, instantiated, launched
+        gb = ctx.estimate_batch(B)           # captured, executable graph updated
+        gb2 = ctx.estimate_batch(B)
+    s.synchronize()
+    _same(first, ref_a)
+    _same(ga, ref_a)
+    _same(gb, ref_b)
+    _same(gb2, ref_b)
+    ctx.close()
+
+
+def test_tuning_choices_do_not_change_results():
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs
+    cfg = _cfg(2)
+    items = [_item(sc) for sc in _frames()]
+    ref = _single(cfg, items)
+    ctx = fassmvs.Context(cfg)
+    for chunk, cps, parts in ((8, 1, 1), (256, 2, 2), (48, 2, 4), (0, 1, 8), (0, 2, 0)):
+        ctx.set_tuning(chunk, cps, parts)
+        got = ctx.estimate_batch(items)
+        ctx.sync()
+        _same(got, ref)
+    chunk, cps, parts = ctx.autotune(items)
+    assert chunk in (0, 64) and cps in (1, 2) and parts in (0, 2, 4, 8)
+    got = ctx.estimate_batch(items)
+    ctx.sync()
+    _same(got, ref)
+    ctx.close()
+
+
+def test_batch_rejects_bad_frames_by_index():
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs
+    items = [_item(sc) for sc in _frames()[:2]]
+    ctx = fassmvs.Context(_cfg(2))
+    bad = dict(items[1])
+    K = np.array(bad["K"], dtype=np.float64)
+    K[2, 0] = 0.5                     # not an intrinsic matrix
+    bad["K"] = K
+    with pytest.raises(fassmvs.FassmvsError) as ei:
+        ctx.estimate_batch([items[0], bad])
+    assert ei.value.status == fassmvs.EINVAL and "frame 1" in str(ei.value)
+    with pytest.raises(fassmvs.FassmvsError):
+        ctx.set_tuning(-1, 2)
+    with pytest.raises(fassmvs.FassmvsError):
+        ctx.set_tuning(0, 2, 3)
+    # the context stays usable
+    ctx.estimate_batch(items)
+    ctx.sync()
+    ctx.close()
