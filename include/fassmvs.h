@@ -176,7 +176,8 @@ FASSMVS_API fassmvs_status fassmvs_set_graph(fassmvs_ctx* ctx, int on);
 /* Work decomposition of the batched form; no setting changes any result.
  *   chunk_planes  planes per work item of the persistent cost kernel, 1..256,
  *                 or 0: enough items for about three waves (chunks >= 8)
- *   ctas_per_sm   resident cost CTAs per SM, 1 or 2
+ *   ctas_per_sm   persistent cost CTAs per SM, 1 or 2, or 0: one short-lived
+ *                 CTA per work item (lets stream priorities act per CTA)
  *   sgm_parts     partial sums of the aggregation, 1, 2, 4 or 8 (at most the
  *                 path count), or 0: one per path.  With P parts, P
  *                 directions run concurrently in each of paths/P launches. */
@@ -193,6 +194,88 @@ typedef struct {
 FASSMVS_API fassmvs_status fassmvs_set_tuning(fassmvs_ctx* ctx, const fassmvs_tuning* tuning);
 FASSMVS_API fassmvs_status fassmvs_autotune(fassmvs_ctx* ctx, const fassmvs_frame* frames, int n,
                                             void* stream, fassmvs_tuning* chosen);
+
+/* ---- serving form -------------------------------------------------------- */
+
+/* A server keeps the frames of a video stream resident on the device, each
+ * with its image pyramid built once on arrival, and runs keyframe requests
+ * (reference frame + neighbour frames + plane list) through the same
+ * coarse-to-fine estimate as fassmvs_estimate_batch.  Device memory for the
+ * resident frames and for every admitted request's scratch comes from one
+ * reservation of mem_budget bytes made at creation; a request is admitted, in
+ * submission order, once its scratch fits next to what is in use.  A worker
+ * thread batches admitted requests continuously: an idle lane (a stream with
+ * its own context) takes up to max_batch admitted requests at once; under a
+ * backlog (overlap_queue) it does so while batches on other lanes are still
+ * running, so their work overlaps on the device, the older batch on a stream
+ * of higher priority.  A request's results are independent of what it was batched
+ * with.  The paper has no serving form (its estimates run one keyframe at a
+ * time); this is the deployment shape of the same computation. */
+typedef struct fassmvs_server fassmvs_server;
+
+typedef struct {
+    int32_t lanes;            /* batches in flight at once, 1..4 */
+    int32_t max_batch;        /* requests per batch, 1..32 */
+    size_t mem_budget;        /* device bytes reserved for frames + request scratch */
+    int32_t deadline_ms;      /* a request not admitted within this fails with ETIMEOUT; 0: no limit */
+    int32_t overlap_queue;    /* a batch starts next to running ones only while at least this many
+                                 admitted requests wait (0 or 1: whenever a lane is idle) */
+    fassmvs_tuning tuning;    /* work decomposition of every batch */
+} fassmvs_server_config;
+
+typedef struct {
+    int64_t id;               /* caller's tag, returned in the result */
+    int64_t ref;              /* reference frame id */
+    const int64_t* nbrs;      /* HOST array of n_nb neighbour frame ids (copied) */
+    int32_t n_nb;             /* 1..16; a neighbour with a smaller id is a left view */
+    fassmvs_planes planes;
+    float* depth;             /* W*H, W*H*3, W*H outputs of the reference size: */
+    float* normal;            /* pinned host memory when host_outputs (copied */
+    float* conf;              /* back by the server), else device memory */
+    int32_t host_outputs;
+} fassmvs_request;
+
+typedef struct {
+    int64_t id;
+    int32_t status;           /* FASSMVS_OK, FASSMVS_ETIMEOUT (not admitted in time), FASSMVS_ECUDA ... */
+    int32_t batch_size;       /* requests in the batch it ran in (0: never ran) */
+    int64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns;   /* steady clock */
+} fassmvs_result;
+
+typedef struct {
+    int64_t capacity, bytes_in_use, peak_bytes;
+    int64_t frames, resident_frames;
+    int64_t submitted, completed, failed, queued;
+    int64_t batches, max_batch_seen;
+} fassmvs_server_stats;
+
+FASSMVS_API void fassmvs_server_config_default(fassmvs_server_config* cfg);
+/* Reserves mem_budget device bytes (FASSMVS_ENOMEM when the device cannot)
+ * and starts the worker thread. */
+FASSMVS_API fassmvs_status fassmvs_server_create(const fassmvs_config* cfg, const fassmvs_server_config* scfg,
+                                                 int device, fassmvs_server** out);
+/* Finishes every admissible request, then stops the worker and frees all. */
+FASSMVS_API void fassmvs_server_destroy(fassmvs_server* srv);
+/* Uploads a W x H uint8 frame from HOST memory (row pitch `pitch`) and builds
+ * its pyramid on the device; K (3x3) and the world -> camera pose
+ * X_cam = R X_world + t are HOST arrays.  FASSMVS_EBUSY when the budget has
+ * no room for it now (retry once requests complete). */
+FASSMVS_API fassmvs_status fassmvs_server_push_frame(fassmvs_server* srv, int64_t id, const uint8_t* img, int W,
+                                                     int H, int pitch, const double K[9], const double R[9],
+                                                     const double t[3]);
+/* The producer will name the frame in no further request; its memory returns
+ * once the requests naming it have completed. */
+FASSMVS_API fassmvs_status fassmvs_server_release_frame(fassmvs_server* srv, int64_t id);
+/* Queues a request; all its frames must be resident and share the reference's
+ * size and intrinsics.  FASSMVS_ENOMEM when its scratch exceeds the whole
+ * budget (it could never be admitted). */
+FASSMVS_API fassmvs_status fassmvs_server_submit(fassmvs_server* srv, const fassmvs_request* req);
+/* Takes up to max completed results (waiting up to timeout_ms for the first);
+ * *n_out receives the count.  Outputs of a completed request are in place. */
+FASSMVS_API fassmvs_status fassmvs_server_poll(fassmvs_server* srv, fassmvs_result* out, int max, int* n_out,
+                                               int timeout_ms);
+FASSMVS_API fassmvs_status fassmvs_server_get_stats(fassmvs_server* srv, fassmvs_server_stats* stats);
+FASSMVS_API const char* fassmvs_server_last_error(const fassmvs_server* srv);
 
 /* ---- stages of the hot path (used by the estimate and by parity tests) ---- */
 

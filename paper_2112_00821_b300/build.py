@@ -8,7 +8,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu")))
-HDRS = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh"))) + [
+HDRS = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cuh")) + glob.glob(os.path.join(HERE, "csrc", "*.h"))) + [
     os.path.join(os.path.dirname(HERE), "include", "fassmvs.h")]
 LIB = os.path.join(HERE, "libfassmvs.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

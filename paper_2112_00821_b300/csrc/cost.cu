@@ -337,9 +337,11 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
     cost_tile(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm);
 }
 
-// Persistent form for a batch of frames: every CTA pulls work items
-// (frame, tile x, tile y, chunk | chunks << 16) from one atomic counter; the
-// frame's arguments are staged in shared memory for the item.
+// Batched form: work items (frame, tile x, tile y, chunk | chunks << 16) of
+// any number of frames.  With a counter the CTAs are persistent and pull items
+// from it; without one, CTA i runs item i alone (short-lived CTAs, so that a
+// higher-priority stream can take SMs over at CTA granularity).  The frame's
+// arguments are staged in shared memory for the item.
 __global__ void __launch_bounds__(THREADS, 2)
 cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ items, int n_items, int* counter)
 {
@@ -347,10 +349,13 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
     SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
     __shared__ CostArgs sa;
     __shared__ int s_item;
+    int it = blockIdx.x;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
+        if (counter) {
+            if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+            __syncthreads();
+            it = s_item;
+        }
         if (it >= n_items) break;
         const int4 w = items[it];
         {
@@ -361,6 +366,7 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
         __syncthreads();
         cost_tile(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm);
         __syncthreads();
+        if (!counter) break;
     }
 }
 
@@ -399,8 +405,13 @@ void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int
                        cudaStream_t st)
 {
     cost_smem_optin();
-    cudaMemsetAsync(counter, 0, sizeof(int), st);
-    cost_batch_kernel<<<ctas, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, counter);
+    if (n_items <= 0) return;
+    if (ctas > 0) {
+        cudaMemsetAsync(counter, 0, sizeof(int), st);
+        cost_batch_kernel<<<ctas, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, counter);
+    } else {
+        cost_batch_kernel<<<n_items, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, nullptr);
+    }
     count_launch();
 }
 

@@ -14,6 +14,9 @@
 
 #include "../../include/fassmvs.h"
 #include "fm_internal.cuh"
+#include "host.h"
+
+using namespace fmh;
 
 namespace fm {
 static std::atomic<uint64_t> g_launches{0};
@@ -21,45 +24,10 @@ uint64_t launches() { return g_launches.load(); }
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n); }
 }  // namespace fm
 
-struct fassmvs_ctx {
-    fassmvs_config cfg;
-    int device = 0;
-    size_t budget = 0, used = 0;
-    std::string err;
-    int V = 0;
-    double K[9];
-    std::vector<double> R, t;
-    std::vector<int8_t> side;
-    bool cams = false;
-    struct Buf { void* p = nullptr; size_t n = 0; };
-    std::map<std::string, Buf> bufs;
-    cudaStream_t last = nullptr;
-    // stage timers
-    bool prof = false;
-    struct Rec { cudaEvent_t a, b; int stage; };
-    std::vector<cudaEvent_t> pool;
-    std::vector<Rec> pending;
-    double ms[FASSMVS_NSTAGES] = {};
-    uint64_t cnt[FASSMVS_NSTAGES] = {};
-    // batched form: work decomposition, graphs, pinned staging of the per-call
-    // argument blocks (two halves, each released by an event)
-    fassmvs_tuning tune{0, 2, 0};              // automatic chunks and parts
-    std::map<uint64_t, fassmvs_tuning> tuned;
-    bool graph = false;
-    std::map<uint64_t, cudaGraphExec_t> execs;
-    std::map<uint64_t, int> seen;
-    unsigned char* host_arena[2] = {nullptr, nullptr};
-    size_t host_cap = 0;
-    cudaEvent_t arena_ev[2] = {nullptr, nullptr};
-    int arena_half = 0;
-};
 
-namespace {
+namespace fmh {
 
 thread_local std::string t_err;
-
-fassmvs_status fail(fassmvs_ctx* c, fassmvs_status s, const char* fmt, ...)
-    __attribute__((format(printf, 3, 4)));
 
 fassmvs_status fail(fassmvs_ctx* c, fassmvs_status s, const char* fmt, ...)
 {
@@ -73,11 +41,11 @@ fassmvs_status fail(fassmvs_ctx* c, fassmvs_status s, const char* fmt, ...)
     return s;
 }
 
-}  // namespace
+}  // namespace fmh
 
-void fm::set_error(const char* msg) { t_err = msg; }
+void fm::set_error(const char* msg) { fmh::t_err = msg; }
 
-namespace {
+namespace fmh {
 
 fassmvs_status cuda_check(fassmvs_ctx* c, cudaError_t e, const char* what)
 {
@@ -318,7 +286,7 @@ void p2_table(int p1, double alpha, double beta, uint16_t* lut)
     }
 }
 
-}  // namespace
+}  // namespace fmh
 
 // ===================================================================== ABI
 extern "C" {
@@ -532,7 +500,7 @@ fassmvs_status fassmvs_dsn(fassmvs_ctx* c, const float* dc, const float* nc, int
 
 }  // extern "C"
 
-namespace {
+namespace fmh {
 
 // per-frame state of one batch call
 struct FrameRun {
@@ -577,25 +545,49 @@ fassmvs_status check_frame(fassmvs_ctx* c, const fassmvs_frame& f, int L, int id
     return FASSMVS_OK;
 }
 
-// bump allocator over the two mirrored staging blocks (pinned host, device)
-struct Stage {
-    unsigned char* host;
-    unsigned char* dev;
-    size_t off, cap;
-    int half;
-    void* take(size_t bytes, size_t& at)
-    {
-        at = (off + 255) & ~(size_t)255;
-        off = at + bytes;
-        return off <= cap ? host + at : nullptr;
-    }
-};
 
 std::string fname(int f, const char* what)
 {
     char b[48];
     snprintf(b, sizeof b, "f%d:%s", f, what);
     return b;
+}
+
+void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0, int parts,
+                          std::vector<std::pair<std::string, size_t>>& out)
+{
+    std::map<std::string, size_t> m;
+    auto need = [&](const char* name, size_t b) { m[name] = std::max(m[name], b); };
+    const int L = cfg.levels;
+    int w = W, h = H;
+    for (int l = 0; l < L; ++l) {
+        if (l > 0) { w = (w + 1) / 2; h = (h + 1) / 2; }
+        const size_t np = (size_t)w * h;
+        const int Gl = (G0 - 1) / (1 << l) + 1;
+        const int D = (l == L - 1) ? Gl : std::min(cfg.D[l], Gl);
+        const size_t Ds = (size_t)((D + 7) & ~7);
+        need("S", 2 * np * Ds);
+        need("Sbar", 2 * np * Ds * parts);
+        need("draw", 4 * np);
+        need("nraw", 12 * np);
+        need("cref", 8 * np);
+        need("htab", 72 * (size_t)Gl * V);
+        need("delta", 4 * (size_t)Gl);
+        if (l > 0) {
+            need((l & 1) ? "dmedA" : "dmedB", 4 * np);
+            need((l & 1) ? "nrmA" : "nrmB", 12 * np);
+        }
+        if (l < L - 1) need("lo", 4 * np);
+        if (cfg.variant == 1) need("dI", 8 * np);
+    }
+    out.assign(m.begin(), m.end());
+}
+
+// scratch buffer `name` of frame f of the batch
+fassmvs_status fscratch(fassmvs_ctx* c, int f, const char* name, size_t bytes, void** out)
+{
+    if (c->scratch_fn) return c->scratch_fn(c->scratch_user, f, name, bytes, out);
+    return ensure(c, fname(f, name).c_str(), bytes, out);
 }
 
 // partial sums of the aggregation: one per direction when automatic
@@ -643,7 +635,7 @@ fassmvs_status stage_prepare(fassmvs_ctx* c, const fassmvs_frame* frames, int n,
 }
 
 fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cudaStream_t st,
-                         const fassmvs_tuning& tn, const Stage& stage)
+                         const fassmvs_tuning& tn, const Stage& stage, const fm::PyrSet* pyrs)
 {
     const fassmvs_config& cfg = c->cfg;
     const int L = cfg.levels;
@@ -675,6 +667,13 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             F.Hs[l] = (F.Hs[l - 1] + 1) / 2;
             F.Ps[l] = F.Ws[l];
         }
+        if (pyrs) {
+            // resident pyramids (serving form): level l of view k, pitch W_l
+            for (int l = 0; l < L; ++l) {
+                if (l > 0) F.Ps[l] = pyrs[f].pitch[l];
+                for (int k = 0; k <= F.V; ++k) F.img[l][k] = pyrs[f].img[l][k];
+            }
+        }
     }
     void* counter;
     FM_TRY(ensure(c, "counter", 256, &counter));
@@ -683,14 +682,13 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
     static thread_local fm::SgmBatch sb;       // 20 KB: kept off the stack
 
     // ---- pyramids of every frame
-    {
+    if (!pyrs) {
         StageTimer tm(c, FASSMVS_STAGE_PYRAMID, st);
         for (int f = 0; f < n; ++f) {
             FrameRun& F = fr[f];
             for (int l = 1; l < L; ++l) {
                 void* p;
-                FM_TRY(ensure(c, fname(f, ("pyr" + std::to_string(l)).c_str()).c_str(),
-                              (size_t)(F.V + 1) * F.Ws[l] * F.Hs[l], &p));
+                FM_TRY(fscratch(c, f, ("pyr" + std::to_string(l)).c_str(), (size_t)(F.V + 1) * F.Ws[l] * F.Hs[l], &p));
                 for (int k = 0; k <= F.V; ++k) {
                     uint8_t* o = (uint8_t*)p + (size_t)k * F.Ws[l] * F.Hs[l];
                     fm::launch_pyramid_down(F.img[l - 1][k], F.Ws[l - 1], F.Hs[l - 1], F.Ps[l - 1], o, F.Ps[l], st);
@@ -699,11 +697,14 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             }
         }
     }
-    int ctas = 0;
+    // persistent cost CTAs (0: one short-lived CTA per work item); the
+    // automatic plane chunking aims at three waves of two CTAs per SM either way
+    int ctas = 0, wave = 0;
     {
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
         ctas = nsm * ctas_per_sm;
+        wave = nsm * (ctas_per_sm ? ctas_per_sm : 2);
     }
     for (int l = L - 1; l >= 0; --l) {
         const size_t block0 = (sg.off + 255) & ~(size_t)255;
@@ -725,24 +726,24 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             F.drl = X.planes.drho * sc;
             F.D = (l == L - 1) ? F.Gl : std::min(cfg.D[l], F.Gl);
             F.Ds = (F.D + 7) & ~7;
-            FM_TRY(ensure(c, fname(f, "S").c_str(), sizeof(uint16_t) * np * F.Ds, &F.pS));
-            FM_TRY(ensure(c, fname(f, "Sbar").c_str(), sizeof(uint16_t) * np * F.Ds * parts, &F.pSb));
-            FM_TRY(ensure(c, fname(f, "draw").c_str(), sizeof(float) * np, &F.pdraw));
-            FM_TRY(ensure(c, fname(f, "nraw").c_str(), sizeof(float) * 3 * np, &F.pnraw));
-            FM_TRY(ensure(c, fname(f, "cref").c_str(), sizeof(uint64_t) * np, &F.cref));
-            FM_TRY(ensure(c, fname(f, "htab").c_str(), sizeof(float) * 18 * (size_t)F.Gl * F.V, &F.htab));
-            FM_TRY(ensure(c, fname(f, "delta").c_str(), sizeof(float) * (size_t)F.Gl, &F.delta));
+            FM_TRY(fscratch(c, f, "S", sizeof(uint16_t) * np * F.Ds, &F.pS));
+            FM_TRY(fscratch(c, f, "Sbar", sizeof(uint16_t) * np * F.Ds * parts, &F.pSb));
+            FM_TRY(fscratch(c, f, "draw", sizeof(float) * np, &F.pdraw));
+            FM_TRY(fscratch(c, f, "nraw", sizeof(float) * 3 * np, &F.pnraw));
+            FM_TRY(fscratch(c, f, "cref", sizeof(uint64_t) * np, &F.cref));
+            FM_TRY(fscratch(c, f, "htab", sizeof(float) * 18 * (size_t)F.Gl * F.V, &F.htab));
+            FM_TRY(fscratch(c, f, "delta", sizeof(float) * (size_t)F.Gl, &F.delta));
             if (l > 0) {
-                FM_TRY(ensure(c, fname(f, (l & 1) ? "dmedA" : "dmedB").c_str(), sizeof(float) * np, &F.pdmed));
-                FM_TRY(ensure(c, fname(f, (l & 1) ? "nrmA" : "nrmB").c_str(), sizeof(float) * 3 * np, &F.pnrm));
+                FM_TRY(fscratch(c, f, (l & 1) ? "dmedA" : "dmedB", sizeof(float) * np, &F.pdmed));
+                FM_TRY(fscratch(c, f, (l & 1) ? "nrmA" : "nrmB", sizeof(float) * 3 * np, &F.pnrm));
             } else {
                 F.pdmed = X.depth;
                 F.pnrm = X.normal;
             }
             F.plo = nullptr;
             F.pdI = nullptr;
-            if (l < L - 1) FM_TRY(ensure(c, fname(f, "lo").c_str(), sizeof(int32_t) * np, &F.plo));
-            if (cfg.variant == 1) FM_TRY(ensure(c, fname(f, "dI").c_str(), 8 * np, &F.pdI));
+            if (l < L - 1) FM_TRY(fscratch(c, f, "lo", sizeof(int32_t) * np, &F.plo));
+            if (cfg.variant == 1) FM_TRY(fscratch(c, f, "dI", 8 * np, &F.pdI));
             const float nf[3] = {(float)X.planes.n[0], (float)X.planes.n[1], (float)X.planes.n[2]};
             if (l < L - 1) {
                 StageTimer tm(c, FASSMVS_STAGE_WINDOW, st);
@@ -805,7 +806,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
         // about three waves of the persistent CTAs, chunks of at least 8 planes
         long long tiles = 0;
         for (int f = 0; f < n; ++f) tiles += (long long)fm::cost_tiles_x(fr[f].w) * fm::cost_tiles_y(fr[f].h);
-        const int auto_nz = (int)std::max(1LL, (3LL * ctas + tiles - 1) / tiles);
+        const int auto_nz = (int)std::max(1LL, (3LL * wave + tiles - 1) / tiles);
         for (int f : order) {
             const FrameRun& F = fr[f];
             const int nz = chunk_planes > 0 ? std::max(1, (F.D + chunk_planes - 1) / chunk_planes)
@@ -912,8 +913,8 @@ uint64_t batch_signature(const fassmvs_ctx* c, const fassmvs_frame* fr, int n, c
 
 fassmvs_status check_tuning(fassmvs_ctx* c, const fassmvs_tuning& t)
 {
-    if (t.chunk_planes < 0 || t.chunk_planes > 256 || t.ctas_per_sm < 1 || t.ctas_per_sm > 2)
-        return fail(c, FASSMVS_EINVAL, "chunk_planes 0 (automatic) or 1..256, ctas_per_sm 1..2");
+    if (t.chunk_planes < 0 || t.chunk_planes > 256 || t.ctas_per_sm < 0 || t.ctas_per_sm > 2)
+        return fail(c, FASSMVS_EINVAL, "chunk_planes 0 (automatic) or 1..256, ctas_per_sm 0 (one CTA per item), 1 or 2");
     if (t.sgm_parts != 0 && t.sgm_parts != 1 && t.sgm_parts != 2 && t.sgm_parts != 4 && t.sgm_parts != 8)
         return fail(c, FASSMVS_EINVAL, "sgm_parts 0 (automatic), 1, 2, 4 or 8");
     return FASSMVS_OK;
@@ -934,12 +935,12 @@ fassmvs_status estimate_batch_impl(fassmvs_ctx* c, const fassmvs_frame* frames, 
     FM_TRY(stage_prepare(c, frames, n, tn.chunk_planes, &sg));
     if (!c->graph || st == nullptr || !c->seen.count(sig)) {
         // eager (and the first run of a shape: allocates all scratch)
-        FM_TRY(run_batch(c, frames, n, st, tn, sg));
+        FM_TRY(run_batch(c, frames, n, st, tn, sg, nullptr));
         c->seen[sig] = 1;
         return FASSMVS_OK;
     }
     FM_TRY(cuda_check(c, cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed), "begin capture"));
-    fassmvs_status rs = run_batch(c, frames, n, st, tn, sg);
+    fassmvs_status rs = run_batch(c, frames, n, st, tn, sg, nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t ce = cudaStreamEndCapture(st, &g);
     if (rs != FASSMVS_OK) { if (g) cudaGraphDestroy(g); return rs; }
@@ -961,7 +962,7 @@ fassmvs_status estimate_batch_impl(fassmvs_ctx* c, const fassmvs_frame* frames, 
     return cuda_check(c, cudaGraphLaunch(ex, st), "graph launch");
 }
 
-}  // namespace
+}  // namespace fmh
 
 extern "C" {
 
@@ -1004,6 +1005,7 @@ fassmvs_status fassmvs_autotune(fassmvs_ctx* c, const fassmvs_frame* frames, int
         for (int chunk : {0, 64}) cand.push_back({chunk, 2, parts});
     }
     cand.push_back({0, 1, 0});
+    cand.push_back({0, 0, 0});
     cudaEvent_t e0, e1;
     FM_TRY(cuda_check(c, cudaEventCreate(&e0), "event"));
     FM_TRY(cuda_check(c, cudaEventCreate(&e1), "event"));
@@ -1018,7 +1020,7 @@ fassmvs_status fassmvs_autotune(fassmvs_ctx* c, const fassmvs_frame* frames, int
         const fassmvs_tuning t = i == 0 ? c->tune : cand[i - 1];
         if ((rs = stage_prepare(c, frames, n, t.chunk_planes, &sg)) != FASSMVS_OK) break;
         cudaEventRecord(e0, st);
-        rs = run_batch(c, frames, n, st, t, sg);
+        rs = run_batch(c, frames, n, st, t, sg, nullptr);
         cudaEventRecord(e1, st);
         if (rs != FASSMVS_OK) break;
         if (cudaEventSynchronize(e1) != cudaSuccess) { rs = cuda_check(c, cudaGetLastError(), "autotune"); break; }

@@ -52,7 +52,8 @@ struct CostArgs {
     uint16_t* S;
 };
 void launch_cost(const CostArgs& a, cudaStream_t st);
-// persistent multi-frame form: items[i] = (frame, tile x, tile y, chunk | chunks << 16)
+// multi-frame form: items[i] = (frame, tile x, tile y, chunk | chunks << 16);
+// ctas > 0 persistent CTAs pulling items from *counter, else one CTA per item
 void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas,
                        cudaStream_t st);
 int cost_tiles_x(int W);
@@ -81,6 +82,13 @@ int sgm_lines(int W, int H, int r);
 // path line of (slot j, frame f), padded to whole CTAs; seg[j][nframes] ==
 // seg[j + 1][0] and seg[nslots - 1][nframes] is the total.
 constexpr int kSgmBatch = 32;
+// resident image pyramid of a reference frame and its views (serving form):
+// img[l][0] the reference, img[l][k + 1] view k, rows pitch[l] bytes apart
+// (level 0 too)
+struct PyrSet {
+    const uint8_t* img[8][kMaxViews + 1];
+    int pitch[8];
+};
 struct SgmBatch {
     SgmArgs a[kSgmBatch];
     int nframes, nslots;

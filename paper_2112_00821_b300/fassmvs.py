@@ -50,6 +50,29 @@ class Tuning(C.Structure):
     _fields_ = [("chunk_planes", C.c_int32), ("ctas_per_sm", C.c_int32), ("sgm_parts", C.c_int32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("lanes", C.c_int32), ("max_batch", C.c_int32), ("mem_budget", C.c_size_t),
+                ("deadline_ms", C.c_int32), ("overlap_queue", C.c_int32), ("tuning", Tuning)]
+
+
+class Request(C.Structure):
+    _fields_ = [("id", C.c_int64), ("ref", C.c_int64), ("nbrs", C.c_void_p), ("n_nb", C.c_int32),
+                ("planes", Planes), ("depth", C.c_void_p), ("normal", C.c_void_p), ("conf", C.c_void_p),
+                ("host_outputs", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("batch_size", C.c_int32),
+                ("t_submit_ns", C.c_int64), ("t_admit_ns", C.c_int64), ("t_launch_ns", C.c_int64),
+                ("t_done_ns", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("capacity", "bytes_in_use", "peak_bytes", "frames", "resident_frames",
+                                         "submitted", "completed", "failed", "queued", "batches",
+                                         "max_batch_seen")]
+
+
 class SgmParams(C.Structure):
     _fields_ = [("paths", C.c_int32), ("variant", C.c_int32), ("p1", C.c_int32),
                 ("p2", C.c_int32), ("dmax", C.c_int32), ("p2_lut", C.c_void_p)]
@@ -84,6 +107,15 @@ _SIGS = {
     "fassmvs_set_graph": [_VP, C.c_int],
     "fassmvs_set_tuning": [_VP, _VP],
     "fassmvs_autotune": [_VP, _VP, C.c_int, _VP, _VP],
+    "fassmvs_server_config_default": [_VP],
+    "fassmvs_server_create": [_VP, _VP, C.c_int, _VP],
+    "fassmvs_server_destroy": [_VP],
+    "fassmvs_server_push_frame": [_VP, C.c_int64, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP],
+    "fassmvs_server_release_frame": [_VP, C.c_int64],
+    "fassmvs_server_submit": [_VP, _VP],
+    "fassmvs_server_poll": [_VP, _VP, C.c_int, _VP, C.c_int],
+    "fassmvs_server_get_stats": [_VP, _VP],
+    "fassmvs_server_last_error": [_VP],
     "fassmvs_profile_enable": [_VP, C.c_int],
     "fassmvs_profile_read": [_VP, _VP, _VP, C.c_int],
     "fassmvs_sync": [_VP],
@@ -105,6 +137,9 @@ def lib():
             f.argtypes = args
             f.restype = C.c_int
         L.fassmvs_destroy.restype = None
+        L.fassmvs_server_destroy.restype = None
+        L.fassmvs_server_config_default.restype = None
+        L.fassmvs_server_last_error.restype = C.c_char_p
         L.fassmvs_last_error.restype = C.c_char_p
         L.fassmvs_launch_count.restype = C.c_uint64
         _lib = L
@@ -377,6 +412,87 @@ class Context:
         self._check(lib().fassmvs_dsn(self._h, _ptr(dc), _ptr(nc), Wc, Hc, W, H, kp, drho, int(dmax),
                                       _ptr(out), _stream()))
         return out
+
+
+def server_config(**kw):
+    c = ServerConfig()
+    lib().fassmvs_server_config_default(C.byref(c))
+    for k, v in kw.items():
+        if k == "tuning":
+            c.tuning = Tuning(*v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+class Server:
+    """A fassmvs_server: resident frames, admission by device memory,
+    continuous batching over lanes (see include/fassmvs.h)."""
+
+    def __init__(self, cfg=None, scfg=None, device=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("fassmvs needs a CUDA device; there is no CPU fallback")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._h = C.c_void_p()
+        cfg = cfg if cfg is not None else default_config()
+        scfg = scfg if scfg is not None else server_config()
+        self._check(lib().fassmvs_server_create(C.byref(cfg), C.byref(scfg), self.device, C.byref(self._h)),
+                    own=False)
+        self._keep = {}
+
+    def _check(self, st, own=True):
+        if st != OK:
+            msg = lib().fassmvs_server_last_error(self._h if own else None)
+            raise FassmvsError(st, (msg or b"").decode())
+
+    def close(self):
+        if self._h:
+            lib().fassmvs_server_destroy(self._h)
+            self._h = C.c_void_p()
+            self._keep.clear()
+
+    __del__ = close
+
+    def push_frame(self, fid, img, K, R, t):
+        """img: (H, W) uint8 numpy array (host); R, t: world -> camera."""
+        img = np.ascontiguousarray(img, dtype=np.uint8)
+        H, W = img.shape
+        k_, kp = _dbl(K, 9)
+        r_, rp = _dbl(R, 9)
+        t_, tp = _dbl(t, 3)
+        self._check(lib().fassmvs_server_push_frame(self._h, int(fid), img.ctypes.data_as(C.c_void_p), W, H,
+                                                    img.strides[0], kp, rp, tp))
+
+    def release_frame(self, fid):
+        self._check(lib().fassmvs_server_release_frame(self._h, int(fid)))
+
+    def submit(self, rid, ref, nbrs, planes, depth, normal, conf):
+        """Outputs: pinned host tensors (copied back) or CUDA tensors."""
+        host = not depth.is_cuda
+        nb = (C.c_int64 * len(nbrs))(*[int(x) for x in nbrs])
+        rq = Request(int(rid), int(ref), C.cast(nb, C.c_void_p), len(nbrs), planes, depth.data_ptr(),
+                     normal.data_ptr(), conf.data_ptr(), 1 if host else 0)
+        self._check(lib().fassmvs_server_submit(self._h, C.byref(rq)))
+        self._keep[int(rid)] = (depth, normal, conf)
+
+    def poll(self, max_results=64, timeout_ms=0):
+        """Completed results: list of dicts (id, status, batch_size, times in ns)."""
+        out = (Result * max_results)()
+        n = C.c_int()
+        self._check(lib().fassmvs_server_poll(self._h, out, max_results, C.byref(n), int(timeout_ms)))
+        res = []
+        for i in range(n.value):
+            r = out[i]
+            self._keep.pop(int(r.id), None)
+            res.append(dict(id=r.id, status=r.status, batch_size=r.batch_size, t_submit_ns=r.t_submit_ns,
+                            t_admit_ns=r.t_admit_ns, t_launch_ns=r.t_launch_ns, t_done_ns=r.t_done_ns))
+        return res
+
+    def stats(self):
+        st = ServerStats()
+        self._check(lib().fassmvs_server_get_stats(self._h, C.byref(st)))
+        return {n: int(getattr(st, n)) for n, _ in ServerStats._fields_}
 
 
 def wta_refine_noalloc(Sbar, D, K, n, rho0, drho, G, lo=None, depth=None, gwin=None):

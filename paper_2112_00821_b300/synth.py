@@ -32,6 +32,7 @@ import numpy as np
 __all__ = [
     "Quad", "Frame", "Scene", "render_view", "make_scene", "make_frame",
     "WORKLOADS", "workload", "box_quads", "trajectory_frames", "BATCH_SIZES", "batch_frames",
+    "render_view_torch", "city_sweep",
 ]
 
 
@@ -244,6 +245,75 @@ def render_view(quads, K, R, t, W, H, noise_sigma=0.0, noise_seed=None, return_g
         nn = np.where(flip[:, None], -nc[None, :], nc[None, :])
         normals[m] = nn
     return img8, depth, normals, who
+
+
+def render_view_torch(quads, K, R, t, W, H, device="cuda"):
+    """render_view (image only, no noise) with torch tensors on `device`, for
+    long synthetic streams; the same ray cast and texture in FP64, returned
+    as a uint8 numpy array."""
+    import torch
+    dt = torch.float64
+    Kn = np.asarray(K, dtype=np.float64)
+    Rn = np.asarray(R, dtype=np.float64)
+    tn = np.asarray(t, dtype=np.float64)
+    C = torch.as_tensor(-Rn.T @ tn, dtype=dt, device=device)
+    ys, xs = torch.meshgrid(torch.arange(H, dtype=dt, device=device), torch.arange(W, dtype=dt, device=device),
+                            indexing="ij")
+    Kinv = torch.as_tensor(np.linalg.inv(Kn), dtype=dt, device=device)
+    dc = torch.stack([xs, ys, torch.ones_like(xs)], dim=-1) @ Kinv.T
+    dref = dc @ torch.as_tensor(Rn, dtype=dt, device=device)
+    best = torch.full((H, W), math.inf, dtype=dt, device=device)
+    who = torch.full((H, W), -1, dtype=torch.int64, device=device)
+    for qi, q in enumerate(quads):
+        y0, y1, x0, x1 = _bbox(q, Kn, Rn, tn, W, H)
+        if y0 >= y1 or x0 >= x1:
+            continue
+        n = torch.as_tensor(q.normal, dtype=dt, device=device)
+        dsub = dref[y0:y1, x0:x1]
+        denom = dsub @ n
+        num = float(np.dot(q.normal, q.origin - (-Rn.T @ tn)))
+        lam = num / denom
+        bsub = best[y0:y1, x0:x1]
+        ok = torch.isfinite(lam) & (lam > 1e-9) & (lam < bsub)
+        if math.isfinite(q.su[0]) or math.isfinite(q.tv[0]):
+            rel = C + lam[..., None] * dsub - torch.as_tensor(q.origin, dtype=dt, device=device)
+            s = rel @ torch.as_tensor(q.au, dtype=dt, device=device)
+            tt = rel @ torch.as_tensor(q.av, dtype=dt, device=device)
+            ok &= (s >= q.su[0]) & (s <= q.su[1]) & (tt >= q.tv[0]) & (tt <= q.tv[1])
+        best[y0:y1, x0:x1] = torch.where(ok, lam, bsub)
+        who[y0:y1, x0:x1] = torch.where(ok, torch.full_like(who[y0:y1, x0:x1], qi), who[y0:y1, x0:x1])
+    if bool((who < 0).any()):
+        raise ValueError("scene has rays that hit nothing; add a backdrop quad")
+    img = torch.zeros((H, W), dtype=dt, device=device)
+    for qi, q in enumerate(quads):
+        m = who == qi
+        if not bool(m.any()):
+            continue
+        P = C + best[m][:, None] * dref[m]
+        rel = P - torch.as_tensor(q.origin, dtype=dt, device=device)
+        s = (rel @ torch.as_tensor(q.au, dtype=dt, device=device)) / q.cell
+        tt = (rel @ torch.as_tensor(q.av, dtype=dt, device=device)) / q.cell
+        nz = _Noise(q.tex_seed)
+        perm = torch.as_tensor(nz.perm, device=device)
+        vals = torch.as_tensor(nz.vals, dtype=dt, device=device)
+
+        def octave(a, b):
+            i0 = torch.floor(a).to(torch.int64)
+            j0 = torch.floor(b).to(torch.int64)
+            fa = a - i0
+            fb = b - j0
+            wa = fa * fa * (3.0 - 2.0 * fa)
+            wb = fb * fb * (3.0 - 2.0 * fb)
+
+            def lat(i, j):
+                return vals[perm[(perm[i & 255] + j) & 255]]
+            top = lat(i0, j0) + wa * (lat(i0 + 1, j0) - lat(i0, j0))
+            bot = lat(i0, j0 + 1) + wa * (lat(i0 + 1, j0 + 1) - lat(i0, j0 + 1))
+            return top + wb * (bot - top)
+        v = 0.60 * octave(s, tt) + 0.25 * octave(2.0 * s + 17.3, 2.0 * tt + 5.1) \
+            + 0.15 * octave(4.0 * s + 3.7, 4.0 * tt + 29.9)
+        img[m] = 128.0 + q.contrast * (v - 128.0)
+    return torch.clamp(torch.round(img), 0, 255).to(torch.uint8).cpu().numpy()
 
 
 # --------------------------------------------------------------------------
@@ -514,11 +584,18 @@ def batch_frames(seed=0, n=16):
     return out
 
 
-def trajectory_frames(n_frames, W, H, seed, speed=0.6, every=5, n_nb=(4, 6), G0=(128, 256)):
+def city_sweep(G0):
+    """(rho_far, drho) of G0 fronto planes uniform in inverse depth over the
+    oblique city's 20-300 m."""
+    return _sweep(20.0, 300.0, G0)
+
+
+def trajectory_frames(n_frames, W, H, seed, speed=0.6, every=5, n_nb=(4, 6), G0=(128, 256), device=None):
     """A simulated 30 fps UAV pass over the oblique city: camera centres move
     along x by `speed` metres per frame. Returns the list of keyframe requests
     (reference index, neighbour indices, plane count) and a render callback
-    rendering frame i (uint8) in the frame of frame 0's camera."""
+    rendering frame i (uint8) in the frame of frame 0's camera (with torch on
+    `device` when given)."""
     f = 0.9375 * W
     height = 60.0
     quads = _oblique_city_quads(seed, f, 45.0, height, zmax=300.0)
@@ -532,6 +609,8 @@ def trajectory_frames(n_frames, W, H, seed, speed=0.6, every=5, n_nb=(4, 6), G0=
 
     def render(i):
         R, t = pose(i)
+        if device is not None:
+            return render_view_torch(quads, K, R, t, W, H, device)
         return render_view(quads, K, R, t, W, H)
 
     reqs = []
