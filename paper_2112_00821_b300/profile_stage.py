@@ -1,8 +1,13 @@
 """Runs one stage of the hot path on a synthetic oblique-city frame, for
 profiling a single kernel (ncu -k ...) or timing it with CUDA events.
 
-  python -m paper_2112_00821_b300.profile_stage --stage cost|sgm|both \
+  python -m paper_2112_00821_b300.profile_stage --stage cost|sgm|both|estimate \
       [--W 960 --H 540 --planes 256 --views 5 --reps 2 --variant 2]
+
+cost / sgm: the single-level stage entry points (cost_kernel, sgm_dir_kernel).
+estimate: the full 4-level estimate (the kernels the benchmark runs:
+cost_batch_kernel, sgm_batch_dir_kernel, ...), one untimed warm-up call then
+`reps` timed calls, with the stage timers.
 
 Prints one JSON line with the per-launch time of the stage(s) (CUDA events on
 the launching stream, after one untimed launch).
@@ -21,7 +26,7 @@ if ROOT not in sys.path:
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--stage", default="both", choices=["cost", "sgm", "both"])
+    p.add_argument("--stage", default="both", choices=["cost", "sgm", "both", "estimate"])
     p.add_argument("--W", type=int, default=960)
     p.add_argument("--H", type=int, default=540)
     p.add_argument("--planes", type=int, default=256)
@@ -39,6 +44,30 @@ def main():
     nl = a.views // 2
     sc = synth.make_frame("city", a.seed, W=a.W, H=a.H, G0=a.planes, n_left=nl, n_right=a.views - nl,
                           want_gt=False)
+    if a.stage == "estimate":
+        cfg = fassmvs.default_config(levels=4, D=[256] * 4, paths=a.paths, variant=a.variant, p1=24, p2=0,
+                                     adaptive_p2=1)
+        ctx = fassmvs.Context(cfg)
+        ctx.set_cameras(sc.K, sc.R, sc.t, sc.side)
+        ref = torch.from_numpy(sc.ref).cuda()
+        nbrs = [torch.from_numpy(x).cuda() for x in sc.nbrs]
+        pl = fassmvs.planes_of(sc)
+        ctx.estimate(ref, nbrs, pl)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.reps):
+            ctx.estimate(ref, nbrs, pl)
+        e1.record()
+        torch.cuda.synchronize()
+        st = ctx.profile_read()
+        out = {"W": a.W, "H": a.H, "planes": a.planes, "views": a.views, "levels": 4,
+               "ms": round(e0.elapsed_time(e1) / a.reps, 3),
+               "stage_ms": {k: round(v[0] / a.reps, 3) for k, v in st.items()}}
+        print(json.dumps(out))
+        ctx.close()
+        return
     ctx = fassmvs.Context()
     G = D = a.planes
     Ds = ((D + 7) // 8) * 8
