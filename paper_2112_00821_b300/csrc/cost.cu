@@ -323,7 +323,8 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     // (x * ceil(2^32 / n)) >> 32 == x / n exactly for x < 2^16, n <= 16
                     if (a.nL > 0) vl = (uint32_t)(((uint64_t)(sl * a.nmax + (a.nL >> 1)) * a.mL) >> 32);
                     if (a.nR > 0) vr = (uint32_t)(((uint64_t)(sr * a.nmax + (a.nR >> 1)) * a.mR) >> 32);
-                    a.S[((size_t)py * W + tx0 + pc) * a.Ds + s] = (uint16_t)min(vl, vr);
+                    a.S[((size_t)py * W + tx0 + pc) * a.pstride + (size_t)(s >> a.bshift) * a.bstride +
+                        (s & ((1 << a.bshift) - 1))] = (uint16_t)min(vl, vr);
                 }
             }
         }

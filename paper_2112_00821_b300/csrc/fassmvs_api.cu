@@ -235,6 +235,9 @@ fassmvs_status cost_volume_impl(fassmvs_ctx* c, const uint8_t* ref, const uint8_
     a.htab = (const float*)htab;
     a.lo = lo;
     a.D = D; a.Ds = Ds; a.G = G;
+    a.pstride = (size_t)Ds;
+    a.bstride = 8;
+    a.bshift = 3;
     a.S = Sv;
     StageTimer tm(c, FASSMVS_STAGE_COST, st);
     fm::launch_cost(a, st);
@@ -271,6 +274,9 @@ fassmvs_status sgm_impl(fassmvs_ctx* c, const uint16_t* Sv, const int32_t* lo, c
         return fail(c, FASSMVS_EINVAL, "aggregated costs could exceed 16 bits: paths %d x (%d + %d)", prm->paths, Smax, p2max);
     a.S = Sv; a.lo = lo; a.dI = dI; a.img = img; a.img_pitch = img_pitch;
     a.W = W; a.H = H; a.D = D; a.Ds = Ds;
+    a.pstride = (size_t)Ds;
+    a.bstride = 8;
+    a.bshift = 3;
     a.paths = prm->paths; a.variant = prm->variant; a.p1 = prm->p1; a.p2 = prm->p2; a.dmax = prm->dmax;
     a.Sbar = Sbar;
     StageTimer tm(c, FASSMVS_STAGE_SGM, st);
@@ -515,7 +521,7 @@ struct FrameRun {
     int w = 0, h = 0, D = 0, Ds = 0, Gl = 0;
     double Kl[9];
     double drl = 0;
-    void *pS = nullptr, *pSb = nullptr, *pdraw = nullptr, *pdmed = nullptr, *pnraw = nullptr, *pnrm = nullptr;
+    void *pS = nullptr, *pSblk = nullptr, *pSb = nullptr, *pdraw = nullptr, *pdmed = nullptr, *pnraw = nullptr, *pnrm = nullptr;
     void *plo = nullptr, *pdI = nullptr, *htab = nullptr, *delta = nullptr, *cref = nullptr;
 };
 
@@ -565,8 +571,9 @@ void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0
         const size_t np = (size_t)w * h;
         const int Gl = (G0 - 1) / (1 << l) + 1;
         const int D = (l == L - 1) ? Gl : std::min(cfg.D[l], Gl);
-        const size_t Ds = (size_t)((D + 7) & ~7);
+        const size_t Ds = (size_t)((D + 15) & ~15);
         need("S", 2 * np * Ds);
+        need("Sblk", 2 * np * Ds);
         need("Sbar", 2 * np * Ds * parts);
         need("draw", 4 * np);
         need("nraw", 12 * np);
@@ -725,8 +732,9 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             F.Gl = (X.planes.G0 - 1) / (1 << l) + 1;
             F.drl = X.planes.drho * sc;
             F.D = (l == L - 1) ? F.Gl : std::min(cfg.D[l], F.Gl);
-            F.Ds = (F.D + 7) & ~7;
+            F.Ds = (F.D + 15) & ~15;          // whole 16-plane blocks
             FM_TRY(fscratch(c, f, "S", sizeof(uint16_t) * np * F.Ds, &F.pS));
+            FM_TRY(fscratch(c, f, "Sblk", sizeof(uint16_t) * np * F.Ds, &F.pSblk));
             FM_TRY(fscratch(c, f, "Sbar", sizeof(uint16_t) * np * F.Ds * parts, &F.pSb));
             FM_TRY(fscratch(c, f, "draw", sizeof(float) * np, &F.pdraw));
             FM_TRY(fscratch(c, f, "nraw", sizeof(float) * 3 * np, &F.pnraw));
@@ -778,7 +786,15 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             a.htab = (const float*)F.htab;
             a.lo = (const int32_t*)F.plo;
             a.D = F.D; a.Ds = F.Ds; a.G = F.Gl;
-            a.S = (uint16_t*)F.pS;
+            // the cost kernel writes 16-plane blocks [Ds / 16][h][w][16]: its
+            // per-plane 2-byte stores then complete their 32-byte sectors within
+            // 16 planes (with [h][w][Ds] an L2 line stays open over 64 planes
+            // and the ~110 MB of open lines of the resident CTAs thrash the
+            // L2); a relayout gives the aggregation [h][w][Ds]
+            a.pstride = 16;
+            a.bstride = 16 * np;
+            a.bshift = 4;
+            a.S = (uint16_t*)F.pSblk;
             // aggregation arguments
             fm::SgmArgs& g = sargs[f];
             memset(&g, 0, sizeof g);
@@ -793,6 +809,9 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             g.S = (const uint16_t*)F.pS; g.lo = (const int32_t*)F.plo; g.dI = (const int8_t*)F.pdI;
             g.img = F.img[l][0]; g.img_pitch = F.Ps[l];
             g.W = F.w; g.H = F.h; g.D = F.D; g.Ds = F.Ds;
+            g.pstride = (size_t)F.Ds;
+            g.bstride = 8;
+            g.bshift = 3;
             g.paths = cfg.paths; g.variant = cfg.variant; g.p1 = F.P1; g.p2 = cfg.p2 * F.nmax; g.dmax = cfg.dmax;
             g.Sbar = (uint16_t*)F.pSb;
             g.part_stride = np * F.Ds;
@@ -825,6 +844,12 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             StageTimer tm(c, FASSMVS_STAGE_COST, st);
             fm::launch_cost_batch((const fm::CostArgs*)(sg.dev + at_cargs), (const int4*)(sg.dev + at_items),
                                   (int)items.size(), (int*)counter, ctas, st);
+        }
+        {
+            StageTimer tm(c, FASSMVS_STAGE_COST, st);
+            for (int f = 0; f < n; ++f)
+                fm::launch_relayout16((const uint16_t*)fr[f].pSblk, (uint16_t*)fr[f].pS, (size_t)fr[f].w * fr[f].h,
+                                      fr[f].Ds, st);
         }
         {
             StageTimer tm(c, FASSMVS_STAGE_SGM, st);

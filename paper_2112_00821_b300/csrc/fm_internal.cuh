@@ -49,6 +49,12 @@ struct CostArgs {
     const float* htab;
     const int32_t* lo;            // may be null (window starts at 0)
     int D, Ds, G;
+    // voxel (pixel p, slot s) at S[p * pstride + (s >> bshift) * bstride +
+    // (s & (2^bshift - 1))]: [H][W][Ds] is pstride = Ds, bshift = 3,
+    // bstride = 8; the 16-plane-blocked [Ds / 16][H][W][16] (Ds a multiple of
+    // 16) is pstride = 16, bshift = 4, bstride = 16 W H
+    size_t pstride, bstride;
+    int bshift;
     uint16_t* S;
 };
 void launch_cost(const CostArgs& a, cudaStream_t st);
@@ -66,6 +72,8 @@ struct SgmArgs {
     const int8_t* dI;
     const uint8_t* img;
     int W, H, D, Ds, img_pitch;
+    size_t pstride, bstride;      // volume layout, as in CostArgs
+    int bshift;
     int paths, variant, p1, p2, dmax;
     int use_lut;
     uint16_t lut[256];
@@ -107,11 +115,16 @@ struct Intr {
     float fx, fy, cx, cy;
 };
 
-// Sbar may hold nparts partial sums, part_stride elements apart (summed here)
+// Sbar may hold nparts partial sums, part_stride elements apart (summed here);
+// pstride / bstride / bshift as in CostArgs (pstride 0: the [H][W][Ds] layout)
 void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
-                       cudaStream_t st, int nparts = 1, size_t part_stride = 0);
+                       cudaStream_t st, int nparts = 1, size_t part_stride = 0, size_t pstride = 0,
+                       size_t bstride = 0, int bshift = 3);
 void launch_delta_table(double rho0, double drho, int G, float* delta, cudaStream_t st);
+// cost volume [Ds / 16][np][16] (as the batched cost kernel writes it) ->
+// [np][Ds] (as the aggregation reads it); Ds a multiple of 16
+void launch_relayout16(const uint16_t* src, uint16_t* dst, size_t np, int Ds, cudaStream_t st);
 void launch_median5(const float* in, int W, int H, float* out, cudaStream_t st);
 void launch_normals(const float* depth, const uint8_t* img, int img_pitch, int W, int H, Intr K,
                     int radius, float beta, float* raw, float* normal, const float npl[3],

@@ -88,6 +88,8 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
 
     const int s0 = lane * 8;
     const bool act = s0 < D;
+    // offset of this lane's slots s0 .. s0 + 7 within a pixel's hypotheses
+    const size_t soff = (size_t)(s0 >> a.bshift) * a.bstride + (s0 & ((1 << a.bshift) - 1));
     // valid-slot masks per packed pair
     uint32_t vmask[4];
 #pragma unroll
@@ -109,7 +111,7 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
     for (int u = 0; u < PF; ++u) {
         if (u < n) {
             const int xx = x0 + u * dx, yy = y0 + u * dy;
-            const size_t pp = ((size_t)yy * W + xx) * a.Ds + s0;
+            const size_t pp = ((size_t)yy * W + xx) * a.pstride + soff;
             if (act) {
                 cp_async16(&rg[u][0][lane], a.S + pp);
                 if (!first) cp_async16(&rg[u][1][lane], Sb + pp);
@@ -134,7 +136,7 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
             __syncwarp();
             if (step + PF < n) {
                 const int xx = x + PF * dx, yy = y + PF * dy;
-                const size_t pp = ((size_t)yy * W + xx) * a.Ds + s0;
+                const size_t pp = ((size_t)yy * W + xx) * a.pstride + soff;
                 if (act) {
                     cp_async16(&rg[u][0][lane], a.S + pp);
                     if (!first) cp_async16(&rg[u][1][lane], Sb + pp);
@@ -235,7 +237,7 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
                     o = make_uint4(acc.x + (L[0] & vmask[0]), acc.y + (L[1] & vmask[1]),
                                    acc.z + (L[2] & vmask[2]), acc.w + (L[3] & vmask[3]));
                 }
-                *reinterpret_cast<uint4*>(Sb + pix * a.Ds + s0) = o;
+                *reinterpret_cast<uint4*>(Sb + pix * a.pstride + soff) = o;
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) Lp[j] = L[j];

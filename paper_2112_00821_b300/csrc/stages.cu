@@ -65,7 +65,7 @@ __global__ void census_kernel(const uint8_t* __restrict__ img, int W, int H, int
 __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __restrict__ lo, int W,
                            int H, int D, int Ds, const float* __restrict__ delta, Intr K, float n0,
                            float n1, float n2, float* __restrict__ depth, int32_t* __restrict__ gwin,
-                           int nparts, size_t part_stride)
+                           int nparts, size_t part_stride, size_t pstride, size_t bstride, int bshift)
 {
     const int lane = threadIdx.x & 31;
     const size_t p = (size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -73,12 +73,13 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
     const int s0 = lane * 8;
     uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (s0 < D) {
-        const uint4* src = reinterpret_cast<const uint4*>(Sbar + p * Ds + s0);
+        const size_t off = p * pstride + (size_t)(s0 >> bshift) * bstride + (s0 & ((1 << bshift) - 1));
+        const uint4* src = reinterpret_cast<const uint4*>(Sbar + off);
         uint4 raw = __ldg(src);
 #pragma unroll
         for (int k = 1; k < 8; ++k)
             if (k < nparts) {
-                const uint4 t = __ldg(reinterpret_cast<const uint4*>(Sbar + k * part_stride + p * Ds + s0));
+                const uint4 t = __ldg(reinterpret_cast<const uint4*>(Sbar + k * part_stride + off));
                 raw.x += t.x; raw.y += t.y; raw.z += t.z; raw.w += t.w;
             }
         v[0] = raw.x & 0xFFFF; v[1] = raw.x >> 16; v[2] = raw.y & 0xFFFF; v[3] = raw.y >> 16;
@@ -120,6 +121,25 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
     const float ray = n0 * ((x - K.cx) / K.fx) + n1 * ((y - K.cy) / K.fy) + n2;
     depth[p] = -xs / ray;
     if (gwin) gwin[p] = g;
+}
+
+// ---------------------------------------------------------------- volume relayout
+// [Ds / 16][np][16] -> [np][Ds]: warp w moves pixels 32 w .. 32 w + 31, lane l
+// pixel 32 w + l; per 16-plane block the warp reads 1 KB contiguous and every
+// lane writes one whole 32-byte sector of its pixel's row.
+__global__ void relayout16_kernel(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst, size_t np,
+                                  int Ds)
+{
+    const size_t p = ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (p >= np) return;
+    const uint4* s = reinterpret_cast<const uint4*>(src + p * 16);
+    uint4* d = reinterpret_cast<uint4*>(dst + p * (size_t)Ds);
+    const size_t bs = np * 2;                  // block stride in uint4
+    for (int b = 0; b < Ds / 16; ++b) {
+        const uint4 v0 = __ldcs(s + b * bs), v1 = __ldcs(s + b * bs + 1);
+        d[2 * b] = v0;
+        d[2 * b + 1] = v1;
+    }
 }
 
 // ---------------------------------------------------------------- median 5x5
@@ -308,13 +328,26 @@ void launch_census(const uint8_t* img, int W, int H, int pitch, uint64_t* out, c
 
 void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
-                       cudaStream_t st, int nparts, size_t part_stride)
+                       cudaStream_t st, int nparts, size_t part_stride, size_t pstride, size_t bstride,
+                       int bshift)
 {
+    if (pstride == 0) {
+        pstride = (size_t)Ds;
+        bstride = 8;
+        bshift = 3;
+    }
     size_t np = (size_t)W * H;
     int per = 8;
     wta_kernel<<<(unsigned)((np + per - 1) / per), per * 32, 0, st>>>(Sbar, lo, W, H, D, Ds, delta, K, n[0],
                                                                   n[1], n[2], depth, gwin, nparts,
-                                                                  part_stride);
+                                                                  part_stride, pstride, bstride, bshift);
+    count_launch();
+}
+
+void launch_relayout16(const uint16_t* src, uint16_t* dst, size_t np, int Ds, cudaStream_t st)
+{
+    if (np == 0) return;
+    relayout16_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(src, dst, np, Ds);
     count_launch();
 }
 
