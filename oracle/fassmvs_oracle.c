@@ -831,11 +831,11 @@ OR_EXPORT int or_estimate(const or_config* cfg, const uint8_t* ref, const uint8_
     int L = cfg->levels;
     if (L < 1 || L > 8) return -1;
     if ((G0 - 1) / (1 << (L - 1)) + 1 > 256) return -1;   /* 256-plane cap at the top (Sec. 3.2) */
-    const uint8_t* imgs[8][16];
+    const uint8_t* imgs[8][17];          /* reference + up to 16 views per level */
     int Ws[8], Hs[8];
     uint8_t* owned[8 * 17];
     int nowned = 0;
-    if (V > 15) return -1;
+    if (V < 1 || V > 16) return -1;
     imgs[0][0] = ref;
     for (int k = 0; k < V; ++k) imgs[0][k + 1] = nbrs[k];
     Ws[0] = W;
