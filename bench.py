@@ -504,7 +504,8 @@ def run_serve_form(a):
                                  device="cuda")
     t_render = time.perf_counter() - t0
     cfg = fassmvs.default_config(**BATCH_CFG)
-    scfg = fassmvs.server_config(lanes=2, max_batch=4, mem_budget=120 << 30, tuning=(32, 0, 0), overlap_queue=2)
+    scfg = fassmvs.server_config(lanes=2, max_batch=4, mem_budget=120 << 30, tuning=(0, 2, 0),
+                                 tuning_overlap=(32, 0, 0), overlap_queue=2)
     warm = serve.subset(streams, 2)
     serve.run_server(warm, cfg, scfg, fps=None)
     serve.run_plain(warm, cfg, fps=None)
@@ -528,7 +529,7 @@ def run_serve_form(a):
         "config": {"workload": "serve_2x30fps_1080p_2720x1530", "frames": 300, "keyframe_every": 5,
                    "levels": 4, "variant": "path-gradient", "paths": 8, "mem_budget_gb": 120,
                    "lanes": scfg.lanes, "max_batch": scfg.max_batch, "overlap_queue": scfg.overlap_queue,
-                   "tuning": {"chunk_planes": 32, "ctas_per_sm": 0, "sgm_parts": 8},
+                   "tuning": {"alone": [0, 2, 0], "next_to_running": [32, 0, 0]},
                    "render_s": round(t_render, 1)},
         "forms": res,
         "p99_plain_over_server": round(pp["latency_ms"]["p99"] / sp["latency_ms"]["p99"], 3),

@@ -220,7 +220,9 @@ typedef struct {
     int32_t deadline_ms;      /* a request not admitted within this fails with ETIMEOUT; 0: no limit */
     int32_t overlap_queue;    /* a batch starts next to running ones only while at least this many
                                  admitted requests wait (0 or 1: whenever a lane is idle) */
-    fassmvs_tuning tuning;    /* work decomposition of every batch */
+    fassmvs_tuning tuning;    /* work decomposition of a batch that starts alone */
+    fassmvs_tuning tuning_overlap;   /* ... of one that starts next to running batches (same
+                                        sgm_parts; ctas_per_sm 0 keeps the older batch first) */
 } fassmvs_server_config;
 
 typedef struct {
@@ -237,7 +239,8 @@ typedef struct {
 
 typedef struct {
     int64_t id;
-    int32_t status;           /* FASSMVS_OK, FASSMVS_ETIMEOUT (not admitted in time), FASSMVS_ECUDA ... */
+    int32_t status;           /* FASSMVS_OK, FASSMVS_ETIMEOUT (not admitted in time), FASSMVS_ENOMEM
+                                 (cannot fit even with nothing else in flight), FASSMVS_ECUDA ... */
     int32_t batch_size;       /* requests in the batch it ran in (0: never ran) */
     int64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns;   /* steady clock */
 } fassmvs_result;
@@ -246,7 +249,7 @@ typedef struct {
     int64_t capacity, bytes_in_use, peak_bytes;
     int64_t frames, resident_frames;
     int64_t submitted, completed, failed, queued;
-    int64_t batches, max_batch_seen;
+    int64_t batches, max_batch_seen, overlapped;
 } fassmvs_server_stats;
 
 FASSMVS_API void fassmvs_server_config_default(fassmvs_server_config* cfg);

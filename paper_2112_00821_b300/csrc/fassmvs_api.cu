@@ -590,6 +590,31 @@ void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0
     out.assign(m.begin(), m.end());
 }
 
+// grows both pinned staging halves to at least `bytes` now
+fassmvs_status stage_reserve(fassmvs_ctx* c, size_t bytes)
+{
+    if (bytes <= c->host_cap) return FASSMVS_OK;
+    for (int i = 0; i < 2; ++i) {
+        if (c->arena_ev[i]) FM_TRY(cuda_check(c, cudaEventSynchronize(c->arena_ev[i]), "staging wait"));
+        if (c->host_arena[i]) cudaFreeHost(c->host_arena[i]);
+        c->host_arena[i] = nullptr;
+        FM_TRY(cuda_check(c, cudaHostAlloc((void**)&c->host_arena[i], bytes, cudaHostAllocDefault), "cudaHostAlloc"));
+        if (!c->arena_ev[i])
+            FM_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->arena_ev[i], cudaEventDisableTiming), "event"));
+    }
+    c->host_cap = bytes;
+    return FASSMVS_OK;
+}
+
+fassmvs_status ctx_reserve(fassmvs_ctx* c, size_t bytes)
+{
+    void* p;
+    FM_TRY(stage_reserve(c, bytes));
+    FM_TRY(ensure(c, "stageA", bytes, &p));
+    FM_TRY(ensure(c, "stageB", bytes, &p));
+    return ensure(c, "counter", 256, &p);
+}
+
 // scratch buffer `name` of frame f of the batch
 fassmvs_status fscratch(fassmvs_ctx* c, int f, const char* name, size_t bytes, void** out)
 {
@@ -621,23 +646,15 @@ fassmvs_status stage_prepare(fassmvs_ctx* c, const fassmvs_frame* frames, int n,
         }
         need += 2 * 256 + n * sizeof(fm::CostArgs) + items * sizeof(int4);
     }
-    if (need > c->host_cap) {
-        for (int i = 0; i < 2; ++i) {
-            if (c->arena_ev[i]) FM_TRY(cuda_check(c, cudaEventSynchronize(c->arena_ev[i]), "staging wait"));
-            if (c->host_arena[i]) cudaFreeHost(c->host_arena[i]);
-            c->host_arena[i] = nullptr;
-            FM_TRY(cuda_check(c, cudaHostAlloc((void**)&c->host_arena[i], need, cudaHostAllocDefault), "cudaHostAlloc"));
-            if (!c->arena_ev[i])
-                FM_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->arena_ev[i], cudaEventDisableTiming), "event"));
-        }
-        c->host_cap = need;
-    }
+    FM_TRY(stage_reserve(c, need));
     const int half = c->arena_half;
     c->arena_half ^= 1;
     FM_TRY(cuda_check(c, cudaEventSynchronize(c->arena_ev[half]), "staging wait"));
     void* dstage;
-    FM_TRY(ensure(c, half ? "stageB" : "stageA", c->host_cap, &dstage));
-    *out = Stage{c->host_arena[half], (unsigned char*)dstage, 0, c->host_cap, half};
+    // the device mirror follows this call's need (the host halves may be
+    // reserved larger)
+    FM_TRY(ensure(c, half ? "stageB" : "stageA", need, &dstage));
+    *out = Stage{c->host_arena[half], (unsigned char*)dstage, 0, need, half};
     return FASSMVS_OK;
 }
 

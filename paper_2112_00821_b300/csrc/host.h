@@ -74,6 +74,10 @@ struct Stage {
     }
 };
 fassmvs_status stage_prepare(fassmvs_ctx* c, const fassmvs_frame* frames, int n, int chunk_planes, Stage* out);
+// grows both pinned staging halves to at least `bytes` now
+fassmvs_status stage_reserve(fassmvs_ctx* c, size_t bytes);
+// stage_reserve plus the device mirrors of `bytes` and the work counter
+fassmvs_status ctx_reserve(fassmvs_ctx* c, size_t bytes);
 
 // partial sums of the aggregation for a tuning
 int sgm_parts(const fassmvs_tuning& t, int paths);

@@ -19,6 +19,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "arena.h"
 #include "host.h"
 
 namespace {
@@ -30,66 +31,6 @@ int64_t now_ns()
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch()).count();
 }
-
-constexpr size_t kAlign = 256;
-size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
-
-// Best-fit allocator over one device allocation; bookkeeping on the host only,
-// so allocating and freeing never synchronises the device.
-class Arena {
-public:
-    bool init(size_t cap, void* base)
-    {
-        base_ = static_cast<unsigned char*>(base);
-        cap_ = cap;
-        free_.clear();
-        live_.clear();
-        if (cap) free_[0] = cap;
-        used_ = peak_ = 0;
-        return true;
-    }
-    // offset of a block of `bytes`, or SIZE_MAX when nothing fits
-    size_t alloc(size_t bytes)
-    {
-        bytes = align_up(bytes ? bytes : 1);
-        auto best = free_.end();
-        for (auto it = free_.begin(); it != free_.end(); ++it)
-            if (it->second >= bytes && (best == free_.end() || it->second < best->second)) best = it;
-        if (best == free_.end()) return SIZE_MAX;
-        const size_t off = best->first, sz = best->second;
-        free_.erase(best);
-        if (sz > bytes) free_[off + bytes] = sz - bytes;
-        live_[off] = bytes;
-        used_ += bytes;
-        peak_ = std::max(peak_, used_);
-        return off;
-    }
-    void release(size_t off)
-    {
-        auto it = live_.find(off);
-        if (it == live_.end()) return;
-        size_t sz = it->second;
-        live_.erase(it);
-        used_ -= sz;
-        auto nx = free_.lower_bound(off);
-        if (nx != free_.end() && off + sz == nx->first) { sz += nx->second; nx = free_.erase(nx); }
-        if (nx != free_.begin()) {
-            auto pv = std::prev(nx);
-            if (pv->first + pv->second == off) { pv->second += sz; return; }
-        }
-        free_[off] = sz;
-    }
-    unsigned char* at(size_t off) const { return base_ + off; }
-    size_t capacity() const { return cap_; }
-    size_t used() const { return used_; }
-    size_t peak() const { return peak_; }
-
-private:
-    unsigned char* base_ = nullptr;
-    size_t cap_ = 0, used_ = 0, peak_ = 0;
-    std::map<size_t, size_t> free_;
-    std::unordered_map<size_t, size_t> live_;
-};
 
 struct SFrame {
     int64_t id;
@@ -224,7 +165,7 @@ void complete(fassmvs_server* s, SReq* q, fassmvs_status st, int batch_size)
 
 // launches one batch on a lane (called by the worker without the lock; the
 // requests of the batch are owned by the lane meanwhile)
-fassmvs_status launch_batch(fassmvs_server* s, Lane& ln)
+fassmvs_status launch_batch(fassmvs_server* s, Lane& ln, const fassmvs_tuning& tn)
 {
     const int n = (int)ln.batch.size();
     std::vector<fassmvs_frame> fr(n);
@@ -258,8 +199,8 @@ fassmvs_status launch_batch(fassmvs_server* s, Lane& ln)
     ln.ctx->scratch_fn = lane_scratch;
     ln.ctx->scratch_user = &user;
     Stage sg;
-    fassmvs_status st = stage_prepare(ln.ctx, fr.data(), n, s->scfg.tuning.chunk_planes, &sg);
-    if (st == FASSMVS_OK) st = run_batch(ln.ctx, fr.data(), n, ln.st, s->scfg.tuning, sg, py.data());
+    fassmvs_status st = stage_prepare(ln.ctx, fr.data(), n, tn.chunk_planes, &sg);
+    if (st == FASSMVS_OK) st = run_batch(ln.ctx, fr.data(), n, ln.st, tn, sg, py.data());
     ln.ctx->scratch_fn = nullptr;
     ln.ctx->scratch_user = nullptr;
     if (st != FASSMVS_OK) return sfail(s, st, "%s", ln.ctx->err.c_str());
@@ -304,7 +245,20 @@ void worker(fassmvs_server* s)
                 continue;
             }
             const size_t off = s->arena.alloc(q->bytes);
-            if (off == SIZE_MAX) break;
+            if (off == SIZE_MAX) {
+                // with nothing admitted or running, no completion can free
+                // memory for it (the resident frames it needs stay): refuse it
+                // rather than wait forever
+                bool idle = s->admitted.empty();
+                for (Lane& ln : s->lanes) idle = idle && !ln.busy;
+                if (!idle) break;
+                s->err = "request " + std::to_string((long long)q->r.id) +
+                         ": its scratch does not fit next to the resident frames";
+                s->pending.pop_front();
+                complete(s, q, FASSMVS_ENOMEM, 0);
+                s->cv_done.notify_all();
+                continue;
+            }
             q->off = off;
             q->t_admit = t;
             if (q->r.host_outputs) {
@@ -339,8 +293,12 @@ void worker(fassmvs_server* s)
             for (SReq* r : ln.batch) r->t_launch = ln.t_launch;
             ++s->stats.batches;
             s->stats.max_batch_seen = std::max<int64_t>(s->stats.max_batch_seen, m);
+            // alone: the fastest decomposition; next to running batches: the
+            // one whose short-lived CTAs let the older batch keep priority
+            const fassmvs_tuning tn = others ? s->scfg.tuning_overlap : s->scfg.tuning;
+            if (others) ++s->stats.overlapped;
             lk.unlock();
-            fassmvs_status st = launch_batch(s, ln);
+            fassmvs_status st = launch_batch(s, ln, tn);
             if (st != FASSMVS_OK) cudaStreamSynchronize(ln.st);   // nothing of it stays in flight
             lk.lock();
             if (st != FASSMVS_OK) {
@@ -372,8 +330,8 @@ void fassmvs_server_config_default(fassmvs_server_config* c)
     c->mem_budget = (size_t)16 << 30;
     c->deadline_ms = 0;
     c->overlap_queue = 2;
-    // short-lived cost CTAs of 32 planes: lane priorities act per CTA
-    c->tuning = fassmvs_tuning{32, 0, 0};
+    c->tuning = fassmvs_tuning{0, 2, 0};
+    c->tuning_overlap = fassmvs_tuning{32, 0, 0};
 }
 
 fassmvs_status fassmvs_server_create(const fassmvs_config* cfg, const fassmvs_server_config* scfg, int device,
@@ -387,6 +345,8 @@ fassmvs_status fassmvs_server_create(const fassmvs_config* cfg, const fassmvs_se
     if (scfg->mem_budget < 4096) return sfail(nullptr, FASSMVS_EINVAL, "mem_budget below 4 KiB");
     if (scfg->deadline_ms < 0) return sfail(nullptr, FASSMVS_EINVAL, "deadline_ms must be >= 0");
     if (scfg->overlap_queue < 0) return sfail(nullptr, FASSMVS_EINVAL, "overlap_queue must be >= 0");
+    if (sgm_parts(scfg->tuning, cfg->paths) != sgm_parts(scfg->tuning_overlap, cfg->paths))
+        return sfail(nullptr, FASSMVS_EINVAL, "tuning and tuning_overlap must give the same sgm_parts");
     auto* s = new fassmvs_server();
     s->cfg = *cfg;
     s->scfg = *scfg;
@@ -402,6 +362,12 @@ fassmvs_status fassmvs_server_create(const fassmvs_config* cfg, const fassmvs_se
         fassmvs_status st = fassmvs_create(cfg, device, 0, &ln.ctx);
         if (st != FASSMVS_OK) return bail(st);
         st = fassmvs_set_tuning(ln.ctx, &scfg->tuning);
+        // staging (pinned halves and their device mirrors, 16 MB each: batches of
+        // several 4K frames) and the work counter reserved up front, outside the
+        // admission budget: growing them later would call cudaFree, which waits
+        // for every lane's running batch
+        if (st == FASSMVS_OK) st = ctx_reserve(ln.ctx, (size_t)16 << 20);
+        if (st == FASSMVS_OK) st = fassmvs_set_tuning(ln.ctx, &scfg->tuning_overlap);   // validates it
         // a batch launched while k others run goes to priority level k, so
         // the oldest batch keeps the SMs and newer ones fill what it leaves
         int least = 0, greatest = 0;
@@ -504,7 +470,7 @@ fassmvs_status fassmvs_server_push_frame(fassmvs_server* s, int64_t id, const ui
     {
         std::lock_guard<std::mutex> g(s->mu);
         if (s->frames.count(id)) return sfail(s, FASSMVS_EINVAL, "frame %lld pushed twice", (long long)id);
-        F->off = s->arena.alloc(total);
+        F->off = s->arena.alloc(total, true);
         if (F->off == SIZE_MAX)
             return sfail(s, FASSMVS_EBUSY, "no room for frame %lld (%zu of %zu bytes in use)", (long long)id,
                          s->arena.used(), s->arena.capacity());

@@ -52,7 +52,8 @@ class Tuning(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("lanes", C.c_int32), ("max_batch", C.c_int32), ("mem_budget", C.c_size_t),
-                ("deadline_ms", C.c_int32), ("overlap_queue", C.c_int32), ("tuning", Tuning)]
+                ("deadline_ms", C.c_int32), ("overlap_queue", C.c_int32), ("tuning", Tuning),
+                ("tuning_overlap", Tuning)]
 
 
 class Request(C.Structure):
@@ -70,7 +71,7 @@ class Result(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("capacity", "bytes_in_use", "peak_bytes", "frames", "resident_frames",
                                          "submitted", "completed", "failed", "queued", "batches",
-                                         "max_batch_seen")]
+                                         "max_batch_seen", "overlapped")]
 
 
 class SgmParams(C.Structure):
@@ -418,8 +419,8 @@ def server_config(**kw):
     c = ServerConfig()
     lib().fassmvs_server_config_default(C.byref(c))
     for k, v in kw.items():
-        if k == "tuning":
-            c.tuning = Tuning(*v)
+        if k in ("tuning", "tuning_overlap"):
+            setattr(c, k, Tuning(*v))
         else:
             setattr(c, k, v)
     return c

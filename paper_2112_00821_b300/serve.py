@@ -97,10 +97,11 @@ def _pinned(shape):
     return torch.empty(shape, dtype=torch.float32, pin_memory=True)
 
 
-def run_server(streams, cfg, scfg, fps=30.0, keep=False):
+def run_server(streams, cfg, scfg, fps=30.0, keep=False, wait_s=300.0):
     """Serves the streams through one fassmvs.Server.  fps=None: every frame
     is available at once (throughput).  Returns a summary dict and, with keep,
-    the outputs per (stream, request)."""
+    the outputs per (stream, request).  Raises if a frame stays refused or
+    results stay out for longer than the bounds."""
     srv = fassmvs.Server(cfg, scfg)
     lat, outs, pend = [], {}, {}
     last_use = [_last_use(s) for s in streams]
@@ -120,13 +121,13 @@ def run_server(streams, cfg, scfg, fps=30.0, keep=False):
         while fps and time.monotonic_ns() - t0 < t * 1e9:
             drain(0)
             time.sleep(0.0002)
-        while True:
+        for attempt in range(2001):
             try:
                 R, tv = s.poses[i]
                 srv.push_frame(s.fid(i), s.frames[i], s.K, R, tv)
                 break
             except fassmvs.FassmvsError as e:
-                if e.status != fassmvs.EBUSY:
+                if e.status != fassmvs.EBUSY or attempt == 2000:
                     raise
                 drain(5)
         for j in ready:
@@ -143,14 +144,18 @@ def run_server(streams, cfg, scfg, fps=30.0, keep=False):
         if i not in last_use[si]:
             srv.release_frame(s.fid(i))
         drain(0)
+    t_give_up = time.monotonic_ns() + int(wait_s * 1e9)
     while pend:
+        if time.monotonic_ns() > t_give_up:
+            raise TimeoutError("%d requests still pending after %.0f s" % (len(pend), wait_s))
         drain(50)
     t_end = time.monotonic_ns()
     st = srv.stats()
     srv.close()
     n_frames = sum(len(s.frames) for s in streams)
     res = _summary(lat, n_req, n_frames, (t_end - t0) * 1e-9)
-    res["server"] = {k: st[k] for k in ("capacity", "peak_bytes", "batches", "max_batch_seen", "completed")}
+    res["server"] = {k: st[k] for k in ("capacity", "peak_bytes", "batches", "max_batch_seen", "overlapped",
+                                        "completed")}
     return (res, outs) if keep else res
 
 

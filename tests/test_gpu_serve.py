@@ -33,7 +33,8 @@ def _cfg():
 
 def test_each_result_is_the_same_alone_and_in_the_mix(streams):
     from paper_2112_00821_b300 import fassmvs, serve
-    scfg = fassmvs.server_config(lanes=2, max_batch=3, mem_budget=4 << 30, tuning=(0, 2, 4))
+    scfg = fassmvs.server_config(lanes=2, max_batch=3, mem_budget=4 << 30, tuning=(0, 2, 4),
+                                 tuning_overlap=(16, 0, 4), overlap_queue=1)
     mix, outs = serve.run_server(streams, _cfg(), scfg, fps=None, keep=True)
     assert mix["server"]["max_batch_seen"] > 1          # requests really shared batches
     n_checked = 0
@@ -41,7 +42,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(streams):
         s = streams[si]
         r, idx, G0 = s.reqs[j]
         alone = fassmvs.Server(_cfg(), fassmvs.server_config(lanes=1, max_batch=1, mem_budget=1 << 30,
-                                                              tuning=(0, 2, 4)))
+                                                              tuning=(0, 2, 4), tuning_overlap=(0, 2, 4)))
         for k in sorted(idx + [r]):
             R, t = s.poses[k]
             alone.push_frame(s.fid(k), s.frames[k], s.K, R, t)
@@ -73,7 +74,8 @@ def test_served_results_match_the_plain_estimate(streams):
 def test_admission_keeps_memory_within_the_budget(streams):
     from paper_2112_00821_b300 import fassmvs, serve
     # room for the resident frames and about two requests of the larger stream
-    scfg = fassmvs.server_config(lanes=3, max_batch=4, mem_budget=48 << 20, tuning=(0, 2, 2))
+    scfg = fassmvs.server_config(lanes=3, max_batch=4, mem_budget=48 << 20, tuning=(0, 2, 2),
+                                 tuning_overlap=(32, 0, 2))
     res = serve.run_server(streams, _cfg(), scfg, fps=None)
     st = res["server"]
     assert st["completed"] == sum(len(s.reqs) for s in streams)
@@ -109,29 +111,61 @@ def test_request_larger_than_the_budget_is_rejected(streams):
     srv.close()
 
 
-def test_request_not_admitted_before_its_deadline_times_out(streams):
+def _need_bytes(s, req, cfg):
+    """Frame bytes and scratch bytes of one request, measured on a roomy
+    server."""
     from paper_2112_00821_b300 import fassmvs, serve
-    s = streams[1]
-    r, idx, G0 = s.reqs[1]
-    frames = sorted(idx + [r])
-    # measure the request's scratch on a roomy server
-    probe = _one_frame_server(1 << 30)
-    _push(probe, s, frames)
+    r, idx, G0 = req
+    probe = fassmvs.Server(cfg, fassmvs.server_config(lanes=1, max_batch=1, mem_budget=32 << 30))
+    _push(probe, s, sorted(idx + [r]))
     before = probe.stats()["bytes_in_use"]
     probe.submit(1, s.fid(r), [s.fid(k) for k in idx], serve._planes(G0), *_outs(s))
     assert probe.poll(4, 60000)[0]["status"] == fassmvs.OK
     need = probe.stats()["peak_bytes"] - before
     probe.close()
-    # a budget the request fits on its own but never next to its resident
-    # frames: it waits for memory until its deadline passes
-    srv = _one_frame_server(before + need - 4096, deadline_ms=20)
-    _push(srv, s, frames)
+    return before, need
+
+
+def test_request_that_can_never_fit_is_refused(streams):
+    from paper_2112_00821_b300 import fassmvs, serve
+    s = streams[1]
+    r, idx, G0 = s.reqs[1]
+    before, need = _need_bytes(s, s.reqs[1], _cfg())
+    # fits the budget on its own but never next to its own resident frames,
+    # with nothing else in flight: refused at once, not left waiting
+    srv = _one_frame_server(before + need - 4096)
+    _push(srv, s, sorted(idx + [r]))
     srv.submit(2, s.fid(r), [s.fid(k) for k in idx], serve._planes(G0), *_outs(s))
     got = srv.poll(4, 60000)
-    assert len(got) == 1 and got[0]["status"] == fassmvs.ETIMEOUT and got[0]["batch_size"] == 0
-    assert got[0]["t_done_ns"] - got[0]["t_submit_ns"] >= 20_000_000
-    st = srv.stats()
-    assert st["failed"] == 1 and st["queued"] == 0
+    assert len(got) == 1 and got[0]["status"] == fassmvs.ENOMEM and got[0]["batch_size"] == 0
+    assert srv.stats()["failed"] == 1 and srv.stats()["queued"] == 0
+    srv.close()
+
+
+def test_request_not_admitted_before_its_deadline_times_out():
+    from paper_2112_00821_b300 import fassmvs, serve
+    # a 1080p keyframe with 256 planes everywhere runs for tens of ms; a
+    # second one waits for its memory and passes its 2 ms deadline meanwhile
+    s = serve.make_streams(sizes=((1920, 1080),), n_frames=5, seed=5, device="cuda")[0]
+    r, idx, _ = s.reqs[0]
+    req = (r, idx, 256)
+    cfg = fassmvs.default_config(levels=3, D=[256, 256, 256], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1)
+    before, need = _need_bytes(s, req, cfg)
+    srv = fassmvs.Server(cfg, fassmvs.server_config(lanes=2, max_batch=1, mem_budget=before + need + need // 2,
+                                                    deadline_ms=2))
+    _push(srv, s, sorted(idx + [r]))
+    for q in (1, 2):
+        srv.submit(q, s.fid(r), [s.fid(k) for k in idx], serve._planes(256), *_outs(s))
+    got = {}
+    for _ in range(10):
+        for x in srv.poll(4, 60000):
+            got[x["id"]] = x
+        if len(got) == 2:
+            break
+    assert got[1]["status"] == fassmvs.OK and got[1]["batch_size"] == 1
+    assert got[2]["status"] == fassmvs.ETIMEOUT and got[2]["batch_size"] == 0
+    assert got[2]["t_done_ns"] - got[2]["t_submit_ns"] >= 2_000_000
+    assert got[2]["t_done_ns"] < got[1]["t_done_ns"]
     srv.close()
 
 
