@@ -45,10 +45,11 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--form", default="frame", choices=["frame", "batch", "serve"],
+    p.add_argument("--form", default="frame", choices=["frame", "batch", "serve", "ablation"],
                    help="frame: the 1080p per-frame workload (default line); batch: the mixed "
                         "16-frame batch, batched form against one estimate per frame; serve: two 30 fps "
-                        "streams through the server against one estimate per keyframe")
+                        "streams through the server against one estimate per keyframe; ablation: "
+                        "8 / 4 paths x plane-wise / surface-normal / path-gradient SGM at 1600x1200")
     return p.parse_args()
 
 
@@ -542,6 +543,62 @@ def run_serve_form(a):
     return 0
 
 
+# ---------------------------------------------------------------- SGM ablation
+# whole-pipeline time per depth map of the paper's run-time table (Tab.
+# sgmx_runtime: DTU 1600x1200, 5 images, 3 levels, NCC 5x5, on a Titan X),
+# quoted as context: other hardware, another matching cost
+PAPER_SGMX_MS = {(8, 0): 640, (8, 1): 895, (8, 2): 2079, (4, 0): 413, (4, 1): 546, (4, 2): 1132}
+
+
+def run_ablation(a):
+    """The 4 / 8-path x plane-wise / surface-normal / path-gradient sweep on a
+    synthetic 1600x1200 piecewise-planar frame with 4 neighbours, 3 levels,
+    512 planes (128 at the top, 128-plane windows below)."""
+    import torch
+    from paper_2112_00821_b300 import fassmvs, synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    sc, base = synth.workload("planes_1600x1200_g512_l3", a.seed, want_gt=False)
+    ref = torch.from_numpy(sc.ref).cuda()
+    nbrs = [torch.from_numpy(x).cuda() for x in sc.nbrs]
+    planes = fassmvs.planes_of(sc)
+    names = {0: "plane-wise", 1: "surface-normal", 2: "path-gradient"}
+    out = []
+    for paths in (8, 4):
+        for variant in (0, 1, 2):
+            ctx = fassmvs.Context(fassmvs.default_config(**dict(base, paths=paths, variant=variant)))
+            ctx.set_cameras(sc.K, sc.R, sc.t, sc.side)
+            for _ in range(max(a.warmup, 3)):
+                ctx.estimate(ref, nbrs, planes)
+            torch.cuda.synchronize()
+            ctx.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(a.steps):
+                ctx.estimate(ref, nbrs, planes)
+            e1.record()
+            torch.cuda.synchronize()
+            st = ctx.profile_read()
+            ctx.close()
+            ms = e0.elapsed_time(e1) / a.steps
+            out.append({"paths": paths, "variant": names[variant], "ms_per_depth_map": round(ms, 3),
+                        "sgm_ms": round(st["sgm"][0] / a.steps, 3), "cost_ms": round(st["cost"][0] / a.steps, 3),
+                        "paper_ms_titan_x_ncc": PAPER_SGMX_MS[(paths, variant)]})
+    if rank != 0:
+        return 0
+    by = {(r["paths"], r["variant"]): r["ms_per_depth_map"] for r in out}
+    line = {"form": "ablation", "metric": "ms per depth map, 1600x1200, 4 views, 3 levels, 512 planes",
+            "unit": "ms", "higher_is_better": False, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "dtype": "u16", "data": "synthetic",
+            "config": {"workload": "planes_1600x1200_g512_l3", "cost": "census 9x7", "levels": 3,
+                       "planes_finest": 512, "window": 128, "views": 4},
+            "runs": out,
+            "four_over_eight_paths": {v: round(by[(4, v)] / by[(8, v)], 3) for v in names.values()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -550,6 +607,8 @@ def main():
         return run_batch_form(a)
     if a.form == "serve":
         return run_serve_form(a)
+    if a.form == "ablation":
+        return run_ablation(a)
     return run_ours(a)
 
 

@@ -487,6 +487,8 @@ WORKLOADS = {
                            "G0=512 D=128, surface-normal SGM, adaptive P2",
     "fhd_1920x1080_g256_l4": "1920x1080, 45 deg oblique city, 2L+3R views, depth 20-300 m, "
                              "4 levels, G0=256 D=256, path-gradient SGM, 8 paths",
+    "planes_1600x1200_g512_l3": "1600x1200, 8-20 random planes, noise 2 DN, 2L+2R views, 3 levels, "
+                                "G0=512 D=128 (128 at the top), SGM variant / paths as run",
 }
 
 
@@ -546,6 +548,10 @@ def workload(name, seed=0, want_gt=True):
     if name == "fhd_1920x1080_g256_l4":
         sc = make_frame("city", seed, want_gt=want_gt)
         cfg = dict(levels=4, D=[256, 256, 256, 256], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1)
+        return sc, cfg
+    if name == "planes_1600x1200_g512_l3":
+        sc = make_frame("planes", seed, W=1600, H=1200, G0=512, n_left=2, n_right=2, want_gt=want_gt)
+        cfg = dict(levels=3, D=[128, 128, 128], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1)
         return sc, cfg
     raise KeyError(name)
 
