@@ -39,7 +39,7 @@ class Config(C.Structure):
                 ("variant", C.c_int32), ("p1", C.c_int32), ("p2", C.c_int32),
                 ("adaptive_p2", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double),
                 ("median5", C.c_int32), ("normal_radius", C.c_int32), ("normal_beta", C.c_double),
-                ("rho_deg", C.c_double), ("dmax", C.c_int32)]
+                ("rho_deg", C.c_double), ("dmax", C.c_int32), ("cost", C.c_int32)]
 
 
 def lib():
@@ -53,6 +53,7 @@ def lib():
         _lib.or_parabola_vertex.argtypes = [C.c_double] * 6
         _lib.or_warp_sample.restype = C.c_int32
         _lib.or_cost_volume.restype = C.c_int
+        _lib.or_ncc_window.restype = C.c_int
         _lib.or_sgm_aggregate.restype = C.c_int
         _lib.or_estimate.restype = C.c_int
     return _lib
@@ -112,7 +113,16 @@ def lr_combine(sL, nL, sR, nR):
     return lib().or_lr_combine(C.c_uint32(sL), nL, C.c_uint32(sR), nR)
 
 
-def cost_volume(ref, nbrs, side, K, R, t, n, rho0, drho, G, lo=None, D=None, Ds=None):
+def ncc_window(a, b):
+    """NCC cost of two 5x5 windows (reference uint8 values, warped values at
+    16 x grey level), reading of Sec. 2.2.1 in fassmvs_oracle.c."""
+    a = _c(np.asarray(a).ravel(), np.int32)
+    b = _c(np.asarray(b).ravel(), np.int32)
+    assert a.size == 25 and b.size == 25
+    return lib().or_ncc_window(_p(a), _p(b))
+
+
+def cost_volume(ref, nbrs, side, K, R, t, n, rho0, drho, G, lo=None, D=None, Ds=None, cost=0):
     ref = _c(ref, np.uint8)
     H, W = ref.shape
     V = len(nbrs)
@@ -125,13 +135,13 @@ def cost_volume(ref, nbrs, side, K, R, t, n, rho0, drho, G, lo=None, D=None, Ds=
     rc = lib().or_cost_volume(_p(ref), arr, V, _p(_c(side, np.int8)), W, H, _p(_c(K, np.float64)),
                               _p(_c(R, np.float64)), _p(_c(t, np.float64)), _p(_c(n, np.float64)),
                               C.c_double(rho0), C.c_double(drho), G,
-                              None if lo_a is None else _p(lo_a), D, Ds, _p(S))
+                              None if lo_a is None else _p(lo_a), D, Ds, int(cost), _p(S))
     if rc != 0:
         raise ValueError("or_cost_volume rc=%d" % rc)
     return S
 
 
-def cost_at(ref, nbrs, side, K, R, t, n, rho0, drho, xs, ys, gs):
+def cost_at(ref, nbrs, side, K, R, t, n, rho0, drho, xs, ys, gs, cost=0):
     ref = _c(ref, np.uint8)
     H, W = ref.shape
     V = len(nbrs)
@@ -141,7 +151,8 @@ def cost_at(ref, nbrs, side, K, R, t, n, rho0, drho, xs, ys, gs):
     out = np.zeros(xs.size, np.uint16)
     lib().or_cost_at(_p(ref), arr, V, _p(_c(side, np.int8)), W, H, _p(_c(K, np.float64)),
                      _p(_c(R, np.float64)), _p(_c(t, np.float64)), _p(_c(n, np.float64)),
-                     C.c_double(rho0), C.c_double(drho), int(xs.size), _p(xs), _p(ys), _p(gs), _p(out))
+                     C.c_double(rho0), C.c_double(drho), int(xs.size), _p(xs), _p(ys), _p(gs), int(cost),
+                     _p(out))
     return out
 
 
@@ -249,10 +260,10 @@ def dsn(dc, nc, W, H, K, drho, dmax=8):
 
 
 def make_config(levels=1, D=(64,), paths=8, variant=0, p1=10, p2=120, adaptive_p2=0, alpha=8.0,
-                beta=10.0, median5=1, normal_radius=2, normal_beta=10.0, rho_deg=60.0, dmax=8):
+                beta=10.0, median5=1, normal_radius=2, normal_beta=10.0, rho_deg=60.0, dmax=8, cost=0):
     Dl = (C.c_int32 * 8)(*(list(D) + [0] * (8 - len(D))))
     return Config(levels, Dl, paths, variant, p1, p2, adaptive_p2, alpha, beta, median5,
-                  normal_radius, normal_beta, rho_deg, dmax)
+                  normal_radius, normal_beta, rho_deg, dmax, cost)
 
 
 def estimate(scene, cfg):

@@ -258,6 +258,53 @@ OR_EXPORT uint16_t or_lr_combine(uint32_t sL, int nL, uint32_t sR, int nR)
     return (uint16_t)(a < b ? a : b);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.2.1, the NCC alternative to the census (Sec. 3.4 selects a 5x5     */
+/* support region; the maximal cost is normalised to 255).  Reading: the     */
+/* correlation of the reference window a (uint8) and the warped window b     */
+/* (1/16 grey level, as for the census), ncc = cov / sqrt(var_a var_b),      */
+/* negated, truncated at zero correlation and scaled:                        */
+/* C = round_half_up(255 (1 - max(ncc, 0))); a flat window (zero variance)   */
+/* costs 255, as does an invalid view.  The window sums are exact integers;  */
+/* the last steps are single precision, each correctly rounded, in the       */
+/* order written here (floating point decides an integer cost).              */
+/* ------------------------------------------------------------------------ */
+OR_EXPORT int or_ncc_window(const int32_t a[25], const int32_t b[25])
+{
+    int64_t Sa = 0, Saa = 0, Sb = 0, Sbb = 0, Sab = 0;
+    for (int i = 0; i < 25; ++i) {
+        Sa += a[i];
+        Saa += (int64_t)a[i] * a[i];
+        Sb += b[i];
+        Sbb += (int64_t)b[i] * b[i];
+        Sab += (int64_t)a[i] * b[i];
+    }
+    const int64_t cov = 25 * Sab - Sa * Sb;
+    const int64_t va = 25 * Saa - Sa * Sa;
+    const int64_t vb = 25 * Sbb - Sb * Sb;
+    if (va <= 0 || vb <= 0 || cov <= 0) return 255;
+    const float fa = (float)va, fb = (float)vb, fc = (float)cov;
+    const float ncc = fc / sqrtf(fa * fb);
+    const float c = 255.0f * (1.0f - ncc);
+    int ci = (int)floorf(c + 0.5f);
+    return ci < 0 ? 0 : (ci > 255 ? 255 : ci);
+}
+
+/* NCC cost of pixel (x, y): 5x5 windows with clamp-to-edge in the reference
+   grid over the reference image and the warped image (values 16 x grey). */
+static int ncc_at(const uint8_t* ref, const int32_t* wimg, int W, int H, int x, int y)
+{
+    int32_t a[25], b[25];
+    int i = 0;
+    for (int dy = -2; dy <= 2; ++dy)
+        for (int dx = -2; dx <= 2; ++dx, ++i) {
+            const int xx = clampi(x + dx, 0, W - 1), yy = clampi(y + dy, 0, H - 1);
+            a[i] = ref[(size_t)yy * W + xx];
+            b[i] = wimg[(size_t)yy * W + xx];
+        }
+    return or_ncc_window(a, b);
+}
+
 /* Plane list of a level (Sec. 2.2.3 and Sec. 2.1): planes uniform in inverse
    depth, 1/delta_g = rho0 + g * drho, g = 0 the farthest. */
 static double plane_delta(double rho0, double drho, int g) { return 1.0 / (rho0 + g * drho); }
@@ -267,14 +314,15 @@ static double plane_delta(double rho0, double drho, int g) { return 1.0 / (rho0 
  * every plane g of the level list needed by some pixel, the neighbour image is
  * warped into the reference view, its census is taken at the pixels whose
  * window [lo_p, lo_p + D) contains g, and the Hamming distance to the
- * reference census is accumulated into the left or right subset sum.
+ * reference census is accumulated into the left or right subset sum (cost
+ * 0), or the NCC cost of the 5x5 windows (cost 1) is.
  * R: V x 9 (row-major), t: V x 3, side: -1 left / +1 right.
  */
 OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int V,
                              const int8_t* side, int W, int H, const double K[9],
                              const double* R, const double* t, const double n[3],
                              double rho0, double drho, int G, const int32_t* lo,
-                             int D, int Ds, uint16_t* S)
+                             int D, int Ds, int cost, uint16_t* S)
 {
     if (W < 2 || H < 2 || D < 1 || Ds < D || G < D) return -1;
     size_t np = (size_t)W * H;
@@ -305,8 +353,10 @@ OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int
                         size_t p = (size_t)y * W + x;
                         int s = g - (lo ? lo[p] : 0);
                         if (s < 0 || s >= D) continue;
-                        int h = 62;
-                        if (wval[p]) h = or_hamming(cref[p], census_i32_at(wimg, W, H, x, y));
+                        int h = cost ? 255 : 62;
+                        if (wval[p])
+                            h = cost ? ncc_at(ref, wimg, W, H, x, y)
+                                     : or_hamming(cref[p], census_i32_at(wimg, W, H, x, y));
                         if (side[k] < 0) sL[p * D + s] += (uint32_t)h;
                         else sR[p * D + s] += (uint32_t)h;
                     }
@@ -330,7 +380,7 @@ OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int
 OR_EXPORT void or_cost_at(const uint8_t* ref, const uint8_t* const* nbrs, int V, const int8_t* side,
                           int W, int H, const double K[9], const double* R, const double* t,
                           const double n[3], double rho0, double drho, int npts, const int32_t* xs,
-                          const int32_t* ys, const int32_t* gs, uint16_t* out)
+                          const int32_t* ys, const int32_t* gs, int cost, uint16_t* out)
 {
     int nL = 0, nR = 0;
     for (int k = 0; k < V; ++k) { if (side[k] < 0) ++nL; else ++nR; }
@@ -350,8 +400,18 @@ OR_EXPORT void or_cost_at(const uint8_t* ref, const uint8_t* const* nbrs, int V,
             or_homography(K, R + 9 * k, t + 3 * k, n, plane_delta(rho0, drho, gs[i]), Hm);
             int32_t valid;
             int32_t cen = or_warp_sample(nbrs[k], W, H, Hm, x, y, &valid);
-            int h = 62;
-            if (valid) {
+            int h = cost ? 255 : 62;
+            if (valid && cost) {
+                int32_t a[25], b[25];
+                int i = 0;
+                for (int dy = -2; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx, ++i) {
+                        int xx = clampi(x + dx, 0, W - 1), yy = clampi(y + dy, 0, H - 1);
+                        a[i] = ref[(size_t)yy * W + xx];
+                        b[i] = or_warp_sample(nbrs[k], W, H, Hm, xx, yy, NULL);
+                    }
+                h = or_ncc_window(a, b);
+            } else if (valid) {
                 uint64_t bits = 0;
                 for (int dy = -3; dy <= 3; ++dy)
                     for (int dx = -4; dx <= 4; ++dx) {
@@ -821,6 +881,7 @@ typedef struct {
     double normal_beta;
     double rho_deg;
     int32_t dmax;
+    int32_t cost;          /* 0: census 9x7 (Hamming), 1: NCC 5x5 */
 } or_config;
 
 OR_EXPORT int or_estimate(const or_config* cfg, const uint8_t* ref, const uint8_t* const* nbrs,
@@ -879,7 +940,7 @@ OR_EXPORT int or_estimate(const or_config* cfg, const uint8_t* ref, const uint8_
         uint16_t* S = (uint16_t*)malloc(sizeof(uint16_t) * np * D);
         uint16_t* Sb = (uint16_t*)malloc(sizeof(uint16_t) * np * D);
         or_cost_volume(imgs[l][0], (const uint8_t* const*)&imgs[l][1], V, side, w, h, Kl, R, t, n,
-                       rho_far, drl, Gl, lo, D, D, S);
+                       rho_far, drl, Gl, lo, D, D, cfg->cost, S);
         or_sgm_params P = {w, h, D, D, Gl, cfg->paths, cfg->variant, P1, cfg->p2 * nmax, cfg->dmax};
         if (or_sgm_aggregate(S, lo, dI, imgs[l][0], cfg->adaptive_p2 ? lut : NULL, &P, Sb) != 0) rc = -2;
         float* draw = (float*)malloc(sizeof(float) * np);

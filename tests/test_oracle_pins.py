@@ -608,3 +608,60 @@ def test_normal_smoothing_stops_at_image_edges(orc):
     assert np.degrees(np.max(np.arccos(np.clip(sm[5:-5, 18] @ n2, -1, 1)))) < 0.05
     sm_u, _ = orc.normals(d, np.full_like(img, 128), K, radius=2, beta=10.0)
     assert np.degrees(np.arccos(np.clip(sm_u[10, 18] @ n2, -1, 1))) > 0.5
+
+
+# ------------------------------------------------------------------ NCC 5x5
+def test_ncc_perfect_affine_anti_and_flat_windows(orc):
+    g = np.random.default_rng(31)
+    a = g.integers(20, 120, 25)
+    assert orc.ncc_window(a, 16 * a) == 0                    # identical windows
+    assert orc.ncc_window(a, 16 * (2 * a + 3)) == 0          # positive affine map
+    assert orc.ncc_window(a, 16 * (255 - a)) == 255          # anti-correlated: truncated
+    assert orc.ncc_window(np.full(25, 77), 16 * a) == 255    # flat reference window
+    assert orc.ncc_window(a, np.full(25, 1600)) == 255       # flat warped window
+
+
+def test_ncc_matches_the_correlation_coefficient(orc):
+    """Against numpy's correlation coefficient in FP64: the oracle rounds in
+    single precision, so a cost may differ by one next to a .5 boundary."""
+    g = np.random.default_rng(32)
+    diffs = []
+    for _ in range(2000):
+        a = g.integers(0, 256, 25)
+        b = np.clip(16 * a + g.integers(-900, 900, 25), 0, 4080)
+        r = np.corrcoef(a.astype(float), b.astype(float))[0, 1]
+        want = int(np.floor(255.0 * (1.0 - max(r, 0.0)) + 0.5))
+        diffs.append(orc.ncc_window(a, b) - want)
+    diffs = np.abs(np.array(diffs))
+    assert diffs.max() <= 1 and np.mean(diffs == 0) > 0.99
+
+
+def test_ncc_cost_volume_identity_and_exact_plane(orc):
+    g = np.random.default_rng(33)
+    W, H, f = 40, 30, 64.0
+    K = np.array([[f, 0, (W - 1) / 2], [0, f, (H - 1) / 2], [0, 0, 1]])
+    ref = g.integers(0, 256, (H, W), dtype=np.uint8)
+    S = orc.cost_volume(ref, [ref], [1], K, np.eye(3)[None], np.zeros((1, 3)), [0, 0, -1.0], 0.1, 0.01, 4,
+                        cost=1)
+    assert np.all(S == 0)                                    # identity views: ncc = 1 everywhere
+    # exact-shift fronto scene (as for the census): the true plane costs 0
+    big = g.integers(0, 256, (H, W + 20), dtype=np.uint8)
+    ref = big[:, 10:10 + W]
+    gstar, G, z = 2, 6, 16.0
+    k1, k2 = 3 - 1 / 1024, -2 - 1 / 1024
+    nb1, nb2 = big[:, 13:13 + W], big[:, 8:8 + W]
+    ts = np.array([[-k1 * z / f, 0, 0], [-k2 * z / f, 0, 0]])
+    drho = 1.0 / (k1 * z)
+    rho0 = 1.0 / z - gstar * drho
+    S = orc.cost_volume(ref, [nb1, nb2], [1, -1], K, np.stack([np.eye(3)] * 2), ts, [0, 0, -1.0], rho0, drho, G,
+                        cost=1)
+    inner = (slice(3, -3), slice(8, -8))
+    assert np.all(S[inner][..., gstar] == 0)
+    assert np.mean(S[inner].argmin(axis=-1) == gstar) > 0.99
+    # sampled voxels agree with the full volume
+    ys, xs = np.nonzero(np.ones((H, W), bool))
+    sel = g.choice(xs.size, 200, replace=False)
+    gs = g.integers(0, G, 200)
+    v = orc.cost_at(ref, [nb1, nb2], [1, -1], K, np.stack([np.eye(3)] * 2), ts, [0, 0, -1.0], rho0, drho,
+                    xs[sel], ys[sel], gs, cost=1)
+    assert np.array_equal(v, S[ys[sel], xs[sel], gs])
