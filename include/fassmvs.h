@@ -89,6 +89,9 @@ typedef struct {
     float normal_beta;     /* beta of Eq. normal-smooth, 10 in the paper */
     float rho_deg;         /* critical angle of Eq. weight-normal, 60 */
     int32_t dmax;          /* clamp of the sn / pg index jumps */
+    int32_t cost;          /* matching cost (Sec. 2.2.1): 0 census 9x7 Hamming (at most 62 per
+                              view), 1 NCC 5x5, negated, truncated at zero correlation and
+                              scaled to 255 (the paper's phi1 for it is 100) */
 } fassmvs_config;
 
 /* SGM parameters of one aggregation (Eq. xsgm ... Eq. p2-grad). */
@@ -299,7 +302,8 @@ FASSMVS_API fassmvs_status fassmvs_census(fassmvs_ctx* ctx, const uint8_t* img, 
  * plane-induced homography H = K (R - t n^T / delta) K^-1, summed over the
  * left and the right views, each sum rescaled to max(n_left, n_right) images
  * (round half up), S = min of the two.  A view whose centre sample leaves the
- * image costs 62.  Samples are bilinear on a 1/256-pixel grid with 8-bit
+ * image costs 62.  With the context's cost set to NCC the per-view cost is
+ * the NCC 5x5 cost instead (255 for an invalid view or a flat window).  Samples are bilinear on a 1/256-pixel grid with 8-bit
  * weights.  K, R, t, n are host arrays.  Slots D..Ds-1 are left untouched. */
 FASSMVS_API fassmvs_status fassmvs_cost_volume(fassmvs_ctx* ctx, const uint8_t* ref, const uint8_t* const* nbrs,
                                    int n_nb, const int8_t* side, int W, int H, const double K[9],

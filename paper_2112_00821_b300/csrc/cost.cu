@@ -40,9 +40,15 @@ constexpr int MAGIC_BITS = 0x4B400000;
 constexpr uint32_t LAYOUT_MASK = 0x03FF03FFu;
 
 struct SmemCost {
-    uint32_t pair[2][SH][SW];            // FP16x2 (V(x) - 2040, V(x+1) - 2040)
+    uint32_t pair[2][SH][SW];            // census: FP16x2 (V(x) - 2040, V(x+1) - 2040); NCC: u16x2 (V(x), V(x+1))
     uint32_t okm[2][PH][2];              // centre-in-image bit per pixel column
-    uint4 refl[PH][PW];                  // reference census in the accumulator layout
+    union {
+        uint4 refl[PH][PW];              // census: reference census in the accumulator layout
+        struct {
+            uint32_t refp[SH][SW];       // NCC: reference values (a(x), a(x+1)) on the sample grid
+            int2 refs[PH][PW];           // NCC: (sum a, 25 sum a^2 - (sum a)^2) of each 5x5 window
+        } ncc;
+    };
     int32_t lo[PH][PW];
     int glo, ghi;
 };
@@ -115,11 +121,11 @@ __device__ __forceinline__ int fix_pos(df N, df Dn, float r)
     return __float_as_int(t1) + __float_as_int(t2) - 2 * MAGIC_BITS;
 }
 
-// one warped sample: FP16-ready value V - 2040 and whether the position lies
-// on the image grid
+// one warped sample: its value V = 16 x grey level in [0, 4080] and whether
+// the position lies on the image grid
 template <bool WANT_OK>
-__device__ __forceinline__ float sample(const uint8_t* __restrict__ img, int W, int H, int pitch, df Nu,
-                                        df Nv, df Dn, bool& ok)
+__device__ __forceinline__ int sample(const uint8_t* __restrict__ img, int W, int H, int pitch, df Nu,
+                                      df Nv, df Dn, bool& ok)
 {
     int Pu = -PMAX, Pv = -PMAX;
     const bool front = Dn.hi > 0.0f || (Dn.hi == 0.0f && Dn.lo > 0.0f);
@@ -138,9 +144,11 @@ __device__ __forceinline__ float sample(const uint8_t* __restrict__ img, int W, 
     const int i10 = __ldg(r0 + pitch), i11 = __ldg(r0 + pitch + 1);
     const int top = (i00 << 8) + A * (i01 - i00);
     const int bot = (i10 << 8) + A * (i11 - i10);
-    const int v16 = ((top << 8) + B * (bot - top) + 2048) >> 12;     // [0, 4080]
-    return __int_as_float(MAGIC_BITS + v16) - (MAGIC + 2040.0f);
+    return ((top << 8) + B * (bot - top) + 2048) >> 12;     // [0, 4080]
 }
+
+// V - 2040 as a float (exact), ready for FP16
+__device__ __forceinline__ float v16_centred(int v16) { return __int_as_float(MAGIC_BITS + v16) - (MAGIC + 2040.0f); }
 
 // canonical 9x7 census word -> four accumulator words: window row dy, pair p
 // (columns 2p, 2p+1) is packed-FMA number m = 5 dy + p, which lands in word
@@ -167,8 +175,10 @@ __device__ __forceinline__ uint4 to_layout(uint64_t c)
 __device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
 __device__ __forceinline__ uint32_t as_u32(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
-// One tile (bx, by) of one frame, plane chunk bz of nz.  Called by the
-// single-frame grid kernel and by the persistent multi-frame kernel.
+// One tile (bx, by) of one frame, plane chunk bz of nz, with the census (NCC
+// false) or NCC 5x5 cost.  Called by the single-frame grid kernel and by the
+// multi-frame kernel.
+template <bool NCC>
 __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int bz, int nz, SmemCost& sm)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -187,7 +197,31 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             atomicMin(&sm.glo, l);
             atomicMax(&sm.ghi, l + a.D);
         }
-        sm.refl[r][c] = to_layout(in ? a.cref[(size_t)py * W + px] : 0ull);
+        if constexpr (!NCC) sm.refl[r][c] = to_layout(in ? a.cref[(size_t)py * W + px] : 0ull);
+    }
+    if constexpr (NCC) {
+        // reference values on the sample grid (clamp-to-edge), then each pixel's
+        // 5x5 window sums
+        for (int i = tid; i < SH * SW; i += THREADS) {
+            const int j = i / SW, c = i % SW;
+            const uint8_t* row = a.ref + (size_t)min(max(ty0 - 3 + j, 0), H - 1) * a.ref_pitch;
+            const int x0 = min(max(tx0 - 4 + c, 0), W - 1), x1 = min(max(tx0 - 3 + c, 0), W - 1);
+            sm.ncc.refp[j][c] = (uint32_t)__ldg(row + x0) | ((uint32_t)__ldg(row + x1) << 16);
+        }
+        __syncthreads();
+        for (int i = tid; i < PH * PW; i += THREADS) {
+            const int r = i / PW, c = i % PW;
+            int sa = 0, saa = 0;
+#pragma unroll
+            for (int dy = 0; dy < 5; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 5; ++dx) {
+                    const int v = (int)(sm.ncc.refp[r + 1 + dy][c + 2 + dx] & 0xFFFFu);
+                    sa += v;
+                    saa += v * v;
+                }
+            sm.ncc.refs[r][c] = make_int2(sa, 25 * saa - sa * sa);
+        }
     }
     __syncthreads();
     // planes of this tile (guarded against an out-of-range window map), split
@@ -240,20 +274,30 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     }
                     bool ok0 = false, ok1 = false;
                     const bool centre_row = j >= 3 && j < 3 + PH;
-                    float q0, q1;
+                    int i0, i1;
                     if (centre_row) {
-                        q0 = sample<true>(img, W, H, a.pitch, u0, v0, d0, ok0);
-                        q1 = sample<true>(img, W, H, a.pitch, u1, v1, d1, ok1);
+                        i0 = sample<true>(img, W, H, a.pitch, u0, v0, d0, ok0);
+                        i1 = sample<true>(img, W, H, a.pitch, u1, v1, d1, ok1);
                     } else {
-                        q0 = sample<false>(img, W, H, a.pitch, u0, v0, d0, ok0);
-                        q1 = sample<false>(img, W, H, a.pitch, u1, v1, d1, ok1);
+                        i0 = sample<false>(img, W, H, a.pitch, u0, v0, d0, ok0);
+                        i1 = sample<false>(img, W, H, a.pitch, u1, v1, d1, ok1);
                     }
-                    float n0 = __shfl_sync(0xFFFFFFFFu, q0, (lane + 1) & 31);
-                    const float t1 = __shfl_sync(0xFFFFFFFFu, q1, 0);
-                    float n1 = __shfl_sync(0xFFFFFFFFu, q1, (lane + 1) & 31);
-                    if (lane == 31) { n0 = t1; n1 = 0.0f; }
-                    prow[j][lane] = as_u32(__floats2half2_rn(q0, n0));
-                    prow[j][32 + lane] = as_u32(__floats2half2_rn(q1, n1));
+                    if constexpr (NCC) {
+                        int n0 = __shfl_sync(0xFFFFFFFFu, i0, (lane + 1) & 31);
+                        const int t1 = __shfl_sync(0xFFFFFFFFu, i1, 0);
+                        int n1 = __shfl_sync(0xFFFFFFFFu, i1, (lane + 1) & 31);
+                        if (lane == 31) { n0 = t1; n1 = 0; }
+                        prow[j][lane] = (uint32_t)i0 | ((uint32_t)n0 << 16);
+                        prow[j][32 + lane] = (uint32_t)i1 | ((uint32_t)n1 << 16);
+                    } else {
+                        const float q0 = v16_centred(i0), q1 = v16_centred(i1);
+                        float n0 = __shfl_sync(0xFFFFFFFFu, q0, (lane + 1) & 31);
+                        const float t1 = __shfl_sync(0xFFFFFFFFu, q1, 0);
+                        float n1 = __shfl_sync(0xFFFFFFFFu, q1, (lane + 1) & 31);
+                        if (lane == 31) { n0 = t1; n1 = 0.0f; }
+                        prow[j][lane] = as_u32(__floats2half2_rn(q0, n0));
+                        prow[j][32 + lane] = as_u32(__floats2half2_rn(q1, n1));
+                    }
                     if (centre_row) {
                         const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, ok0);
                         const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, ok1);
@@ -265,6 +309,57 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 }
             }
             __syncthreads();
+            // ---------------------------------------------------------- NCC 5x5
+            if constexpr (NCC) {
+                if (cact) {
+                    // window of output row r: sample rows pr0 + r + 1 .. + 5,
+                    // columns pc + 2 .. pc + 6; row sums slide down the column
+                    const uint32_t* bp = &sm.pair[buf][pr0 + 1][pc + 2];
+                    const uint32_t* ap = &sm.ncc.refp[pr0 + 1][pc + 2];
+                    int hb[5], hbb[5], hab[5];
+                    int Sb = 0, Sbb = 0, Sab = 0;
+                    const int sh = a.views.side[k] < 0 ? 0 : 16;
+#pragma unroll
+                    for (int jr = 0; jr < CH + 4; ++jr) {
+                        const uint32_t w0 = bp[jr * SW], w1 = bp[jr * SW + 2], w2 = bp[jr * SW + 4];
+                        const uint32_t x0 = ap[jr * SW], x1 = ap[jr * SW + 2], x2 = ap[jr * SW + 4];
+                        const int b0 = w0 & 0xFFFF, b1 = w0 >> 16, b2 = w1 & 0xFFFF, b3 = w1 >> 16, b4 = w2 & 0xFFFF;
+                        const int a0 = x0 & 0xFFFF, a1 = x0 >> 16, a2 = x1 & 0xFFFF, a3 = x1 >> 16, a4 = x2 & 0xFFFF;
+                        const int rb = b0 + b1 + b2 + b3 + b4;
+                        const int rbb = b0 * b0 + b1 * b1 + b2 * b2 + b3 * b3 + b4 * b4;
+                        const int rab = a0 * b0 + a1 * b1 + a2 * b2 + a3 * b3 + a4 * b4;
+                        Sb += rb;
+                        Sbb += rbb;
+                        Sab += rab;
+                        if (jr >= 5) {
+                            Sb -= hb[jr % 5];
+                            Sbb -= hbb[jr % 5];
+                            Sab -= hab[jr % 5];
+                        }
+                        hb[jr % 5] = rb;
+                        hbb[jr % 5] = rbb;
+                        hab[jr % 5] = rab;
+                        if (jr >= 4) {
+                            const int r = jr - 4;
+                            const int2 rs = sm.ncc.refs[pr0 + r][pc];
+                            const long long cov = 25LL * Sab - (long long)rs.x * Sb;
+                            const long long vb = 25LL * Sbb - (long long)Sb * Sb;
+                            uint32_t c = 255u;
+                            if (rs.y > 0 && vb > 0 && cov > 0) {
+                                // single precision, each step correctly rounded, in the
+                                // oracle's order
+                                const float fa = __int2float_rn(rs.y), fb = __ll2float_rn(vb);
+                                const float ncc = __fdiv_rn(__ll2float_rn(cov), __fsqrt_rn(__fmul_rn(fa, fb)));
+                                const float cf = __fmul_rn(255.0f, __fsub_rn(1.0f, ncc));
+                                c = (uint32_t)min(max((int)floorf(__fadd_rn(cf, 0.5f)), 0), 255);
+                            }
+                            const bool ok = (sm.okm[buf][pr0 + r][pc >> 5] >> (pc & 31)) & 1u;
+                            if (!ok) c = 255u;
+                            slr[r] += c << sh;
+                        }
+                    }
+                }
+            } else
             // ---------------------------------------------------------- census
             if (cact) {
                 const uint32_t* base = &sm.pair[buf][pr0][pc];
@@ -331,11 +426,12 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     }
 }
 
+template <bool NCC>
 __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
-    cost_tile(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm);
+    cost_tile<NCC>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm);
 }
 
 // Batched form: work items (frame, tile x, tile y, chunk | chunks << 16) of
@@ -343,6 +439,7 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
 // from it; without one, CTA i runs item i alone (short-lived CTAs, so that a
 // higher-priority stream can take SMs over at CTA granularity).  The frame's
 // arguments are staged in shared memory for the item.
+template <bool NCC>
 __global__ void __launch_bounds__(THREADS, 2)
 cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ items, int n_items, int* counter)
 {
@@ -365,7 +462,7 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
             for (int i = threadIdx.x; i < (int)(sizeof(CostArgs) / sizeof(int)); i += THREADS) dst[i] = src[i];
         }
         __syncthreads();
-        cost_tile(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm);
+        cost_tile<NCC>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm);
         __syncthreads();
         if (!counter) break;
     }
@@ -385,8 +482,10 @@ void cost_smem_optin()
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[dev]) return;
     const int smem = (int)sizeof(SmemCost);
-    cudaFuncSetAttribute(cost_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(cost_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(cost_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(cost_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(cost_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(cost_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     done[dev] = true;
 }
 }  // namespace
@@ -398,20 +497,22 @@ void launch_cost(const CostArgs& a, cudaStream_t st)
     // enough CTAs for about three waves of two CTAs per SM on 148 SMs
     const int tiles = (int)(grid.x * grid.y);
     grid.z = (unsigned)max(1, min((3 * 2 * 148 + tiles - 1) / tiles, (a.D + 7) / 8));
-    cost_kernel<<<grid, THREADS, sizeof(SmemCost), st>>>(a);
+    if (a.cost) cost_kernel<true><<<grid, THREADS, sizeof(SmemCost), st>>>(a);
+    else cost_kernel<false><<<grid, THREADS, sizeof(SmemCost), st>>>(a);
     count_launch();
 }
 
-void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas,
+void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas, bool ncc,
                        cudaStream_t st)
 {
     cost_smem_optin();
     if (n_items <= 0) return;
+    auto kern = ncc ? cost_batch_kernel<true> : cost_batch_kernel<false>;
     if (ctas > 0) {
         cudaMemsetAsync(counter, 0, sizeof(int), st);
-        cost_batch_kernel<<<ctas, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, counter);
+        kern<<<ctas, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, counter);
     } else {
-        cost_batch_kernel<<<n_items, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, nullptr);
+        kern<<<n_items, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, nullptr);
     }
     count_launch();
 }

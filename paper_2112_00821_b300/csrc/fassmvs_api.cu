@@ -118,6 +118,9 @@ struct StageTimer {
 
 fassmvs_status set_device(fassmvs_ctx* c) { return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"); }
 
+// largest cost one view can contribute (census Hamming or NCC)
+int cost_max(int cost) { return cost ? 255 : fm::kCensusMax; }
+
 fassmvs_status check_config(fassmvs_ctx* c, const fassmvs_config* cfg)
 {
     if (!cfg) return fail(c, FASSMVS_EINVAL, "config is NULL");
@@ -131,6 +134,7 @@ fassmvs_status check_config(fassmvs_ctx* c, const fassmvs_config* cfg)
     if (cfg->normal_radius < 0 || cfg->normal_radius > 8) return fail(c, FASSMVS_EINVAL, "normal_radius must be 0..8");
     if (cfg->dmax < 0 || cfg->dmax > 127) return fail(c, FASSMVS_EINVAL, "dmax must be 0..127");
     if (!(cfg->beta > 0) || !(cfg->normal_beta > 0)) return fail(c, FASSMVS_EINVAL, "beta must be > 0");
+    if (cfg->cost != 0 && cfg->cost != 1) return fail(c, FASSMVS_EINVAL, "cost must be 0 (census) or 1 (NCC)");
     return FASSMVS_OK;
 }
 
@@ -221,6 +225,9 @@ fassmvs_status cost_volume_impl(fassmvs_ctx* c, const uint8_t* ref, const uint8_
     }
     fm::CostArgs a;
     memset(&a, 0, sizeof a);
+    a.cost = c->cfg.cost;
+    a.ref = ref;
+    a.ref_pitch = pitch;
     a.cref = (const uint64_t*)cref;
     int nL = 0, nR = 0;
     for (int k = 0; k < V; ++k) {
@@ -315,6 +322,7 @@ fassmvs_status fassmvs_config_default(fassmvs_config* cfg)
     cfg->normal_beta = 10.0f;
     cfg->rho_deg = 60.0f;
     cfg->dmax = 8;
+    cfg->cost = 0;
     return FASSMVS_OK;
 }
 
@@ -429,7 +437,8 @@ fassmvs_status fassmvs_sgm_aggregate(fassmvs_ctx* c, const uint16_t* Sv, const i
     if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
     FM_TRY(set_device(c));
     c->last = S(stream);
-    return sgm_impl(c, Sv, lo, dI, img, W, W, H, D, Ds, prm, fm::kCensusMax * fm::kMaxViews, Sbar, S(stream));
+    return sgm_impl(c, Sv, lo, dI, img, W, W, H, D, Ds, prm, cost_max(c->cfg.cost) * fm::kMaxViews, Sbar,
+                    S(stream));
 }
 
 fassmvs_status fassmvs_wta_refine(fassmvs_ctx* c, const uint16_t* Sbar, const int32_t* lo, int W, int H, int D,
@@ -791,6 +800,9 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             // cost arguments
             fm::CostArgs& a = cargs[f];
             memset(&a, 0, sizeof a);
+            a.cost = cfg.cost;
+            a.ref = F.img[l][0];
+            a.ref_pitch = F.Ps[l];
             a.cref = (const uint64_t*)F.cref;
             for (int k = 0; k < F.V; ++k) {
                 a.views.img[k] = F.img[l][k + 1];
@@ -821,7 +833,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 for (int i = 0; i < 256; ++i) { g.lut[i] = F.lut[i]; p2max = std::max(p2max, (int)F.lut[i]); }
             }
             p2max = std::max(p2max, F.P1);
-            if ((long long)cfg.paths * (fm::kCensusMax * F.nmax + p2max) >= 65536)
+            if ((long long)cfg.paths * (cost_max(cfg.cost) * F.nmax + p2max) >= 65536)
                 return fail(c, FASSMVS_EINVAL, "frame %d: aggregated costs could exceed 16 bits", f);
             g.S = (const uint16_t*)F.pS; g.lo = (const int32_t*)F.plo; g.dI = (const int8_t*)F.pdI;
             g.img = F.img[l][0]; g.img_pitch = F.Ps[l];
@@ -860,7 +872,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
         {
             StageTimer tm(c, FASSMVS_STAGE_COST, st);
             fm::launch_cost_batch((const fm::CostArgs*)(sg.dev + at_cargs), (const int4*)(sg.dev + at_items),
-                                  (int)items.size(), (int*)counter, ctas, st);
+                                  (int)items.size(), (int*)counter, ctas, cfg.cost != 0, st);
         }
         {
             StageTimer tm(c, FASSMVS_STAGE_COST, st);

@@ -41,7 +41,10 @@ struct ViewPtrs {
 };
 
 struct CostArgs {
-    const uint64_t* cref;         // reference census [H][W]
+    int cost;                     // 0: census 9x7 Hamming, 1: NCC 5x5
+    const uint64_t* cref;         // reference census [H][W] (census)
+    const uint8_t* ref;           // reference image, rows ref_pitch bytes apart (NCC)
+    int ref_pitch;
     ViewPtrs views;
     int V, W, H, pitch;
     int nL, nR, nmax;
@@ -59,8 +62,9 @@ struct CostArgs {
 };
 void launch_cost(const CostArgs& a, cudaStream_t st);
 // multi-frame form: items[i] = (frame, tile x, tile y, chunk | chunks << 16);
-// ctas > 0 persistent CTAs pulling items from *counter, else one CTA per item
-void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas,
+// ctas > 0 persistent CTAs pulling items from *counter, else one CTA per item;
+// ncc: every frame's args use the NCC cost (else the census)
+void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas, bool ncc,
                        cudaStream_t st);
 int cost_tiles_x(int W);
 int cost_tiles_y(int H);

@@ -36,7 +36,7 @@ class Config(C.Structure):
                 ("variant", C.c_int32), ("p1", C.c_int32), ("p2", C.c_int32),
                 ("adaptive_p2", C.c_int32), ("alpha", C.c_float), ("beta", C.c_float),
                 ("median5", C.c_int32), ("normal_radius", C.c_int32), ("normal_beta", C.c_float),
-                ("rho_deg", C.c_float), ("dmax", C.c_int32)]
+                ("rho_deg", C.c_float), ("dmax", C.c_int32), ("cost", C.c_int32)]
 
 
 class Frame(C.Structure):
