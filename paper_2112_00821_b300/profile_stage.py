@@ -35,6 +35,7 @@ def main():
     p.add_argument("--paths", type=int, default=8)
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--cost", type=int, default=0, help="0 census 9x7, 1 NCC 5x5 (estimate stage)")
     a = p.parse_args()
 
     import numpy as np
@@ -45,8 +46,8 @@ def main():
     sc = synth.make_frame("city", a.seed, W=a.W, H=a.H, G0=a.planes, n_left=nl, n_right=a.views - nl,
                           want_gt=False)
     if a.stage == "estimate":
-        cfg = fassmvs.default_config(levels=4, D=[256] * 4, paths=a.paths, variant=a.variant, p1=24, p2=0,
-                                     adaptive_p2=1)
+        cfg = fassmvs.default_config(levels=4, D=[256] * 4, paths=a.paths, variant=a.variant,
+                                     p1=100 if a.cost else 24, p2=0, adaptive_p2=1, cost=a.cost)
         ctx = fassmvs.Context(cfg)
         ctx.set_cameras(sc.K, sc.R, sc.t, sc.side)
         ref = torch.from_numpy(sc.ref).cuda()
