@@ -259,6 +259,51 @@ def dsn(dc, nc, W, H, K, drho, dmax=8):
     return out
 
 
+def dog_weights():
+    w = np.zeros(7, np.int32)
+    lib().or_dog_weights(_p(w))
+    return w
+
+
+def speckle(mask, val, minsize):
+    m = _c(mask, np.uint8).copy()
+    H, W = m.shape
+    lib().or_speckle(_p(m), W, H, int(val), int(minsize))
+    return m
+
+
+def dog_mask(img):
+    """Alg. 3 mask of a reference image: 1 where the texture suffices."""
+    img = _c(img, np.uint8)
+    H, W = img.shape
+    m = np.zeros((H, W), np.uint8)
+    lib().or_dog_mask(_p(img), W, H, _p(m))
+    return m
+
+
+def apply_mask(mask, depth, normal, conf):
+    d, n, c = (_c(a, np.float32).copy() for a in (depth, normal, conf))
+    H, W = d.shape
+    lib().or_apply_mask(_p(_c(mask, np.uint8)), W, H, _p(d), _p(n), _p(c))
+    return d, n, c
+
+
+def geo_hits(dref, K, dks, R, t, eta_r=10.0):
+    """Alg. 4 hit counts of a reference depth map against neighbour maps
+    (R, t: reference -> neighbour)."""
+    dref = _c(dref, np.float32)
+    H, W = dref.shape
+    dk = [_c(x, np.float32) for x in dks]
+    arr = (C.c_void_p * max(1, len(dk)))(*[x.ctypes.data for x in dk])
+    hits = np.zeros((H, W), np.uint8)
+    rc = lib().or_geo_hits(_p(dref), W, H, _p(_c(K, np.float64)), len(dk), arr,
+                           _p(_c(np.asarray(R, np.float64).reshape(-1, 9), np.float64)),
+                           _p(_c(np.asarray(t, np.float64).reshape(-1, 3), np.float64)), C.c_double(eta_r), _p(hits))
+    if rc != 0:
+        raise ValueError("or_geo_hits rc=%d" % rc)
+    return hits
+
+
 def make_config(levels=1, D=(64,), paths=8, variant=0, p1=10, p2=120, adaptive_p2=0, alpha=8.0,
                 beta=10.0, median5=1, normal_radius=2, normal_beta=10.0, rho_deg=60.0, dmax=8, cost=0):
     Dl = (C.c_int32 * 8)(*(list(D) + [0] * (8 - len(D))))

@@ -867,6 +867,169 @@ OR_EXPORT void or_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, i
 /* the depth and normal maps of level l, upscaled by nearest neighbour,     */
 /* initialise level l-1.  Level l uses every 2^l-th plane of the finest     */
 /* list (reading): G_l = floor((G0 - 1) / 2^l) + 1, drho_l = 2^l drho.      */
+
+/* ------------------------------------------------------------------------ */
+/* Post-filters (Sec. 2.6).                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Alg. 3 (DoG mask), readings: the 7x7 Gaussian has sigma 1.4 (the usual     */
+/* value for 7 taps), quantised per axis to integer weights summing to 256   */
+/* (as the pyramid's, R1) with clamp-to-edge; DoG = I - I_smooth, marked     */
+/* where |DoG| > 0.5 grey level; speckles are 4-connected components; the    */
+/* 3x3 dilation takes the maximum over the in-image neighbours; the          */
+/* estimates are invalidated where the final mask is 0 (the algorithm's last */
+/* step names the mask value 1, at odds with its stated purpose of removing  */
+/* weakly textured areas).                                                   */
+OR_EXPORT void or_dog_weights(int32_t w[7])
+{
+    double g[7], s = 0.0;
+    for (int i = 0; i < 7; ++i) {
+        const double x = i - 3;
+        g[i] = exp(-x * x / (2.0 * 1.4 * 1.4));
+        s += g[i];
+    }
+    int tot = 0;
+    for (int i = 0; i < 7; ++i) {
+        w[i] = (int32_t)floor(256.0 * g[i] / s + 0.5);
+        tot += w[i];
+    }
+    w[3] += 256 - tot;                   /* exact unit sum, the centre absorbs the rounding */
+}
+
+/* components (4-connected) of pixels equal to `val` smaller than minsize take
+   the other value */
+static void speckle(uint8_t* m, int W, int H, uint8_t val, int minsize);
+OR_EXPORT void or_speckle(uint8_t* m, int W, int H, int val, int minsize) { speckle(m, W, H, (uint8_t)val, minsize); }
+
+static void speckle(uint8_t* m, int W, int H, uint8_t val, int minsize)
+{
+    const size_t np = (size_t)W * H;
+    int32_t* stack = (int32_t*)malloc(np * sizeof(int32_t));
+    int32_t* comp = (int32_t*)malloc(np * sizeof(int32_t));
+    uint8_t* seen = (uint8_t*)calloc(np, 1);
+    for (size_t s0 = 0; s0 < np; ++s0) {
+        if (m[s0] != val || seen[s0]) continue;
+        int top = 0, n = 0;
+        stack[top++] = (int32_t)s0;
+        seen[s0] = 1;
+        while (top > 0) {
+            const int32_t p = stack[--top];
+            comp[n++] = p;
+            const int x = p % W, y = p / W;
+            const int nx[4] = {x - 1, x + 1, x, x}, ny[4] = {y, y, y - 1, y + 1};
+            for (int k = 0; k < 4; ++k) {
+                if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
+                const int32_t q = ny[k] * W + nx[k];
+                if (m[q] == val && !seen[q]) {
+                    seen[q] = 1;
+                    stack[top++] = q;
+                }
+            }
+        }
+        if (n < minsize)
+            for (int i = 0; i < n; ++i) m[comp[i]] = (uint8_t)(1 - val);
+    }
+    free(stack);
+    free(comp);
+    free(seen);
+}
+
+OR_EXPORT void or_dog_mask(const uint8_t* img, int W, int H, uint8_t* mask)
+{
+    int32_t w[7];
+    or_dog_weights(w);
+    const size_t np = (size_t)W * H;
+    int64_t* tmp = (int64_t*)malloc(np * sizeof(int64_t));
+    for (int y = 0; y < H; ++y)            /* horizontal pass (x 256) */
+        for (int x = 0; x < W; ++x) {
+            int64_t a = 0;
+            for (int i = -3; i <= 3; ++i) a += (int64_t)w[i + 3] * img[(size_t)y * W + clampi(x + i, 0, W - 1)];
+            tmp[(size_t)y * W + x] = a;
+        }
+    for (int y = 0; y < H; ++y)            /* vertical pass (x 65536) and threshold */
+        for (int x = 0; x < W; ++x) {
+            int64_t a = 0;
+            for (int j = -3; j <= 3; ++j) a += (int64_t)w[j + 3] * tmp[(size_t)clampi(y + j, 0, H - 1) * W + x];
+            const int64_t dog = ((int64_t)img[(size_t)y * W + x] << 16) - a;
+            mask[(size_t)y * W + x] = (dog > 32768 || dog < -32768) ? 1 : 0;
+        }
+    free(tmp);
+    speckle(mask, W, H, 1, 7);             /* activation areas below 7 px */
+    uint8_t* d = (uint8_t*)malloc(np);
+    for (int y = 0; y < H; ++y)            /* 3x3 dilation */
+        for (int x = 0; x < W; ++x) {
+            uint8_t v = 0;
+            for (int j = -1; j <= 1; ++j)
+                for (int i = -1; i <= 1; ++i) {
+                    const int xx = x + i, yy = y + j;
+                    if (xx >= 0 && xx < W && yy >= 0 && yy < H && mask[(size_t)yy * W + xx]) v = 1;
+                }
+            d[(size_t)y * W + x] = v;
+        }
+    memcpy(mask, d, np);
+    free(d);
+    speckle(mask, W, H, 0, 21);            /* deactivation areas below 21 px */
+}
+
+/* invalidates (sets to 0) the estimates where mask == 0 */
+OR_EXPORT void or_apply_mask(const uint8_t* mask, int W, int H, float* depth, float* normal, float* conf)
+{
+    for (size_t p = 0; p < (size_t)W * H; ++p)
+        if (!mask[p]) {
+            depth[p] = 0.0f;
+            normal[3 * p] = normal[3 * p + 1] = normal[3 * p + 2] = 0.0f;
+            conf[p] = 0.0f;
+        }
+}
+
+/* Alg. 4 (geometric consistency by mutual reprojection), readings: pixel p
+   with depth d (z in the reference frame) is lifted to X = d K^-1 (x, y, 1),
+   moved into view k (X_k = R_k X + t_k) and projected to p_k; the depth of
+   map k is read at the pixel nearest to p_k (round half up), the point p_k is
+   lifted with it and brought back: p~ = pi(R_k^T (X'_k - t_k)); a hit when
+   |p - p~| < eta_r (pixels).  A point behind a camera, outside map k or on
+   an invalid (<= 0) depth is a miss.  Fewer than eta_h hits invalidate p
+   (depth, normal and confidence set to 0).  Every step in FP64 in the order
+   written (the decision is an integer one).  K is shared by all maps. */
+OR_EXPORT int or_geo_hits(const float* dref, int W, int H, const double K[9], int n,
+                          const float* const* dk, const double* R, const double* t, double eta_r,
+                          uint8_t* hits)
+{
+    const double fx = K[0], fy = K[4], cx = K[2], cy = K[5];
+    if (K[1] != 0.0 || K[3] != 0.0 || K[6] != 0.0 || K[7] != 0.0 || K[8] != 1.0) return -1;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const size_t p = (size_t)y * W + x;
+            int h = 0;
+            const double d = dref[p];
+            if (d > 0.0) {
+                const double X0 = (x - cx) / fx * d, X1 = (y - cy) / fy * d, X2 = d;
+                for (int k = 0; k < n; ++k) {
+                    const double* Rk = R + 9 * k;
+                    const double* tk = t + 3 * k;
+                    const double Y0 = Rk[0] * X0 + Rk[1] * X1 + Rk[2] * X2 + tk[0];
+                    const double Y1 = Rk[3] * X0 + Rk[4] * X1 + Rk[5] * X2 + tk[1];
+                    const double Y2 = Rk[6] * X0 + Rk[7] * X1 + Rk[8] * X2 + tk[2];
+                    if (!(Y2 > 0.0)) continue;
+                    const double u = fx * Y0 / Y2 + cx, v = fy * Y1 / Y2 + cy;
+                    const double ru = floor(u + 0.5), rv = floor(v + 0.5);
+                    if (!(ru >= 0.0 && ru <= W - 1 && rv >= 0.0 && rv <= H - 1)) continue;
+                    const double e = dk[k][(size_t)rv * W + (size_t)ru];
+                    if (!(e > 0.0)) continue;
+                    const double Z0 = (u - cx) / fx * e - tk[0], Z1 = (v - cy) / fy * e - tk[1], Z2 = e - tk[2];
+                    const double B0 = Rk[0] * Z0 + Rk[3] * Z1 + Rk[6] * Z2;
+                    const double B1 = Rk[1] * Z0 + Rk[4] * Z1 + Rk[7] * Z2;
+                    const double B2 = Rk[2] * Z0 + Rk[5] * Z1 + Rk[8] * Z2;
+                    if (!(B2 > 0.0)) continue;
+                    const double du = fx * B0 / B2 + cx - x, dv = fy * B1 / B2 + cy - y;
+                    if (sqrt(du * du + dv * dv) < eta_r) ++h;
+                }
+            }
+            hits[p] = (uint8_t)h;
+        }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int32_t levels;

@@ -665,3 +665,78 @@ def test_ncc_cost_volume_identity_and_exact_plane(orc):
     v = orc.cost_at(ref, [nb1, nb2], [1, -1], K, np.stack([np.eye(3)] * 2), ts, [0, 0, -1.0], rho0, drho,
                     xs[sel], ys[sel], gs, cost=1)
     assert np.array_equal(v, S[ys[sel], xs[sel], gs])
+
+
+# ------------------------------------------------------------------ post-filters (Sec. 2.6)
+def test_dog_weights_quantise_a_7_tap_gaussian(orc):
+    w = orc.dog_weights()
+    g = np.exp(-0.5 * (np.arange(-3, 4) / 1.4) ** 2)
+    assert w.sum() == 256 and np.array_equal(w, w[::-1])
+    assert np.all(np.abs(w - 256 * g / g.sum()) <= 1.0)
+
+
+def test_speckle_removes_small_4_connected_components(orc):
+    m = np.zeros((12, 20), np.uint8)
+    m[1, 1:7] = 1                         # 6 pixels: removed
+    m[4, 1:8] = 1                         # 7 pixels: kept
+    m[8, 8] = m[9, 9] = m[10, 10] = 1     # diagonal neighbours are separate components
+    m[6:9, 14:17] = 1                     # 9 pixels: kept
+    out = orc.speckle(m, 1, 7)
+    assert out[1, 1:7].sum() == 0 and out[4, 1:8].all() and out[6:9, 14:17].all()
+    assert out[8, 8] == out[9, 9] == out[10, 10] == 0
+    # holes (0-components) below 21 pixels are filled, from 21 on they stay
+    h = np.ones((12, 30), np.uint8)
+    h[2:6, 2:7] = 0                       # 20 pixels: filled
+    h[2:5, 12:19] = 0                     # 21 pixels: kept
+    out = orc.speckle(h, 0, 21)
+    assert out[2:6, 2:7].all() and not out[2:5, 12:19].any()
+
+
+def test_dog_mask_flat_textured_and_island(orc):
+    g = np.random.default_rng(41)
+    assert orc.dog_mask(np.full((40, 50), 90, np.uint8)).sum() == 0          # no texture anywhere
+    noise = g.integers(0, 256, (40, 50), dtype=np.uint8)
+    assert orc.dog_mask(noise).mean() > 0.99                                 # textured everywhere
+    img = np.full((60, 80), 100, np.uint8)
+    img[20:40, 30:50] = g.integers(0, 256, (20, 20), dtype=np.uint8)         # a textured island
+    m = orc.dog_mask(img)
+    assert m[20:40, 30:50].all()                                             # kept (and dilated)
+    assert m[:10].sum() == 0 and m[:, :15].sum() == 0                        # far flat areas masked out
+    d = np.ones((60, 80), np.float32)
+    n = np.ones((60, 80, 3), np.float32)
+    c = np.ones((60, 80), np.float32)
+    d2, n2, c2 = orc.apply_mask(m, d, n, c)
+    assert np.all(d2[m == 0] == 0) and np.all(n2[m == 0] == 0) and np.all(c2[m == 0] == 0)
+    assert np.all(d2[m == 1] == 1)
+
+
+def _plane_maps(W, H, f, z, ts):
+    """Depth maps of a fronto plane at depth z seen from translated cameras
+    (a translation parallel to the plane keeps the depth z)."""
+    K = np.array([[f, 0, (W - 1) / 2], [0, f, (H - 1) / 2], [0, 0, 1]])
+    return K, [np.full((H, W), z, np.float32) for _ in ts]
+
+
+def test_geometric_consistency_on_a_plane_and_its_outliers(orc):
+    W, H, f, z = 64, 48, 60.0, 10.0
+    ts = np.array([[0.5, 0, 0], [-0.5, 0, 0], [0, 0.4, 0], [0, -0.4, 0]])
+    K, dks = _plane_maps(W, H, f, z, ts)
+    R = np.stack([np.eye(3)] * 4)
+    dref = np.full((H, W), z, np.float32)
+    hits = orc.geo_hits(dref, K, dks, R, ts, eta_r=1.0)
+    # shifts of f b / z = 3 (x) and 2.4 (y) pixels: a pixel is seen by every
+    # view whose projection stays inside the image
+    yy, xx = np.mgrid[0:H, 0:W]
+    inside = [(xx + 3 <= W - 1 + 0.5), (xx - 3 >= -0.5), (yy + 2.4 <= H - 0.5), (yy - 2.4 >= -0.5)]
+    assert np.array_equal(hits, sum(m.astype(np.uint8) for m in inside))
+    # a wrong depth reprojects off: at 0.7 z the shifts are 4.29 (x) and 3.43
+    # (y) px instead of 3 and 2.4, errors of 1.29 and 1.03 px: with eta_r = 1
+    # every view misses
+    bad = dref.copy()
+    bad[10:20, 10:20] = 0.7 * z
+    h2 = orc.geo_hits(bad, K, dks, R, ts, eta_r=1.0)
+    assert np.all(h2[10:20, 10:20] == 0)
+    assert np.array_equal(h2[30:, 30:], hits[30:, 30:])
+    zero = dref.copy()
+    zero[0:5] = 0.0
+    assert orc.geo_hits(zero, K, dks, R, ts)[0:5].sum() == 0                 # invalid depth: no hits
