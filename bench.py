@@ -45,11 +45,12 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--form", default="frame", choices=["frame", "batch", "serve", "ablation"],
+    p.add_argument("--form", default="frame", choices=["frame", "batch", "serve", "ablation", "filters"],
                    help="frame: the 1080p per-frame workload (default line); batch: the mixed "
                         "16-frame batch, batched form against one estimate per frame; serve: two 30 fps "
                         "streams through the server against one estimate per keyframe; ablation: "
-                        "8 / 4 paths x plane-wise / surface-normal / path-gradient SGM at 1600x1200")
+                        "8 / 4 paths x plane-wise / surface-normal / path-gradient SGM at 1600x1200; filters: "
+                        "the DoG and geometric post-filters on 1920x1080 maps")
     return p.parse_args()
 
 
@@ -603,6 +604,54 @@ def run_ablation(a):
     return 0
 
 
+# ---------------------------------------------------------------- post-filters
+def run_filters(a):
+    """Alg. 3 (DoG mask + invalidation) and Alg. 4 (geometric consistency
+    against 4 neighbour maps, FP64) on 1920x1080 maps: ms per map."""
+    import numpy as np
+    import torch
+    from paper_2112_00821_b300 import fassmvs, synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    sc, _ = synth.workload("fhd_1920x1080_g256_l4", a.seed, want_gt=False)
+    H, W = sc.ref.shape
+    g = np.random.default_rng(a.seed)
+    ref = torch.from_numpy(sc.ref).cuda()
+    d0 = torch.from_numpy(g.uniform(20, 300, (H, W)).astype(np.float32)).cuda()
+    # geometric check on consistent maps (a fronto plane seen from translated
+    # views) and eta_h = 0, so every call does the full work on every pixel
+    dz = torch.full((H, W), 50.0, dtype=torch.float32, device="cuda")
+    nrm = torch.zeros((H, W, 3), dtype=torch.float32, device="cuda")
+    cf = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    maps = [dz.clone() for _ in range(4)]
+    R = np.stack([np.eye(3)] * 4)
+    t = np.array([[0.5, 0, 0], [-0.5, 0, 0], [1.0, 0, 0], [-1.0, 0, 0]])
+    ctx = fassmvs.Context()
+    res = {}
+    for name, fn in (("dog", lambda d: ctx.dog_filter(ref, d, nrm, cf)),
+                     ("geometric", lambda d: ctx.geo_filter(d, sc.K, maps, R, t, normal=nrm, conf=cf, eta_h=0))):
+        d = (d0 if name == "dog" else dz).clone()
+        for _ in range(max(a.warmup, 3)):
+            fn(d)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            fn(d)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = round(e0.elapsed_time(e1) / a.steps, 4)
+    ctx.sync()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps({"form": "filters", "metric": "ms per 1920x1080 map", "unit": "ms", "higher_is_better": False,
+                          "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "data": "synthetic",
+                          "config": {"workload": "fhd_1920x1080_g256_l4", "geometric_maps": 4},
+                          "dog_ms": res["dog"], "geometric_ms": res["geometric"]}), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -613,6 +662,8 @@ def main():
         return run_serve_form(a)
     if a.form == "ablation":
         return run_ablation(a)
+    if a.form == "filters":
+        return run_filters(a)
     return run_ours(a)
 
 

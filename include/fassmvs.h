@@ -283,6 +283,37 @@ FASSMVS_API fassmvs_status fassmvs_server_poll(fassmvs_server* srv, fassmvs_resu
 FASSMVS_API fassmvs_status fassmvs_server_get_stats(fassmvs_server* srv, fassmvs_server_stats* stats);
 FASSMVS_API const char* fassmvs_server_last_error(const fassmvs_server* srv);
 
+/* ---- post-filters (Sec. 2.6) ---------------------------------------------- */
+
+/* Difference-of-Gaussian texture mask (Alg. 3) of the reference image (W x H
+ * uint8, row pitch `pitch`, device): 7x7 Gaussian of sigma 1.4 (integer
+ * weights summing to 256 per axis, clamp-to-edge), |I - I_smooth| > 0.5 grey
+ * level marks texture, 4-connected marked areas below 7 pixels are dropped,
+ * a 3x3 dilation, unmarked areas below 21 pixels are filled.  `mask` (device
+ * W*H bytes, may be NULL) receives the mask (1 = enough texture); depth,
+ * normal (x3) and conf (device, all or none) are set to 0 where it is 0
+ * (read as the algorithm's purpose: its last step names the value 1).  A
+ * labelling walk that reaches its bound is reported by fassmvs_sync
+ * (FASSMVS_EINTERNAL); it cannot happen on a valid image. */
+FASSMVS_API fassmvs_status fassmvs_dog_filter(fassmvs_ctx* ctx, const uint8_t* ref, int W, int H, int pitch,
+                                              float* depth, float* normal, float* conf, uint8_t* mask,
+                                              void* stream);
+
+/* Geometric consistency by mutual reprojection (Alg. 4): every pixel of the
+ * reference depth map (z depth, device, W x H) is lifted with its depth,
+ * moved into each of the n (0..16) neighbour depth maps (device pointers in
+ * the HOST array `depths`, same size and K; R (n x 9), t (n x 3) HOST arrays,
+ * reference -> map k) and projected; the depth of map k at the nearest pixel
+ * lifts that point back into the reference, and the reprojection error is
+ * the distance to the pixel.  Fewer than eta_h maps within eta_r pixels (the
+ * paper: 3 and 10) set depth, normal and conf (normal / conf may be NULL) to
+ * 0.  FP64 throughout.  `hits` (device W*H bytes, may be NULL) receives the
+ * counts. */
+FASSMVS_API fassmvs_status fassmvs_geo_filter(fassmvs_ctx* ctx, float* depth, float* normal, float* conf, int W,
+                                              int H, const double K[9], int n, const float* const* depths,
+                                              const double* R, const double* t, double eta_r, int eta_h,
+                                              uint8_t* hits, void* stream);
+
 /* ---- stages of the hot path (used by the estimate and by parity tests) ---- */
 
 /* Sec. 2.1 pyramid level: 3x3 Gaussian (sigma 1, integer weights 70/116/70

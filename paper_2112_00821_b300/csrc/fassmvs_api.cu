@@ -1155,7 +1155,92 @@ fassmvs_status fassmvs_sync(fassmvs_ctx* c)
     FM_TRY(set_device(c));
     cudaError_t e = c->last ? cudaStreamSynchronize(c->last) : cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    return cuda_check(c, e, "device error");
+    FM_TRY(cuda_check(c, e, "device error"));
+    // deferred device-side flags: a connected-component walk that hit its cap
+    auto it = c->bufs.find("ccl_err");
+    if (it != c->bufs.end() && it->second.p) {
+        int flag = 0;
+        FM_TRY(cuda_check(c, cudaMemcpy(&flag, it->second.p, sizeof flag, cudaMemcpyDeviceToHost), "flag read"));
+        if (flag) {
+            cudaMemset(it->second.p, 0, sizeof flag);
+            return fail(c, FASSMVS_EINTERNAL, "a connected-component walk reached its bound (DoG filter)");
+        }
+    }
+    return FASSMVS_OK;
+}
+
+// Alg. 3 weights: a 7-tap Gaussian of sigma 1.4, quantised to integers that
+// sum to 256 (the rounding remainder goes to the centre tap)
+static fm::DogWeights dog_weights()
+{
+    fm::DogWeights w;
+    double g[7], sum = 0.0;
+    for (int i = 0; i < 7; ++i) {
+        g[i] = std::exp(-(double)((i - 3) * (i - 3)) / (2.0 * 1.4 * 1.4));
+        sum += g[i];
+    }
+    int tot = 0;
+    for (int i = 0; i < 7; ++i) {
+        w.w[i] = (int32_t)std::floor(256.0 * g[i] / sum + 0.5);
+        tot += w.w[i];
+    }
+    w.w[3] += 256 - tot;
+    return w;
+}
+
+fassmvs_status fassmvs_dog_filter(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch, float* depth,
+                                  float* normal, float* conf, uint8_t* mask, void* stream)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (!ref || W < 1 || H < 1 || pitch < W) return fail(c, FASSMVS_EINVAL, "bad reference image");
+    if ((depth || normal || conf) && !(depth && normal && conf))
+        return fail(c, FASSMVS_EINVAL, "depth, normal and conf go together");
+    if ((size_t)W * H >= ((size_t)1 << 31)) return fail(c, FASSMVS_EINVAL, "image too large");
+    FM_TRY(set_device(c));
+    cudaStream_t st = S(stream);
+    c->last = st;
+    const size_t np = (size_t)W * H;
+    void *m, *tmp, *parent, *size, *err;
+    if (mask) m = mask;
+    else FM_TRY(ensure(c, "dog_mask", np, &m));
+    FM_TRY(ensure(c, "dog_tmp", np, &tmp));
+    FM_TRY(ensure(c, "ccl_parent", np * sizeof(int), &parent));
+    FM_TRY(ensure(c, "ccl_size", np * sizeof(int), &size));
+    const bool fresh = !c->bufs.count("ccl_err");
+    FM_TRY(ensure(c, "ccl_err", sizeof(int), &err));
+    if (fresh) FM_TRY(cuda_check(c, cudaMemsetAsync(err, 0, sizeof(int), st), "memset"));
+    fm::launch_dog_mask(ref, W, H, pitch, dog_weights(), (uint8_t*)m, (uint8_t*)tmp, (int*)parent, (int*)size,
+                        (int*)err, st);
+    if (depth) fm::launch_apply_mask((const uint8_t*)m, W, H, depth, normal, conf, st);
+    return launch_status(c, "dog filter launch");
+}
+
+fassmvs_status fassmvs_geo_filter(fassmvs_ctx* c, float* depth, float* normal, float* conf, int W, int H,
+                                  const double K[9], int n, const float* const* depths, const double* R,
+                                  const double* t, double eta_r, int eta_h, uint8_t* hits, void* stream)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (!depth || !K || (n > 0 && (!depths || !R || !t))) return fail(c, FASSMVS_EINVAL, "NULL argument");
+    if (W < 1 || H < 1 || n < 0 || n > fm::kMaxViews) return fail(c, FASSMVS_EINVAL, "bad size or map count");
+    if (!(eta_r > 0.0) || eta_h < 0) return fail(c, FASSMVS_EINVAL, "eta_r must be > 0, eta_h >= 0");
+    if (K[1] != 0.0 || K[3] != 0.0 || K[6] != 0.0 || K[7] != 0.0 || K[8] != 1.0 || K[0] == 0.0 || K[4] == 0.0)
+        return fail(c, FASSMVS_EINVAL, "K must be [[fx 0 cx][0 fy cy][0 0 1]]");
+    fm::GeoArgs g;
+    memset(&g, 0, sizeof g);
+    g.W = W; g.H = H; g.n = n; g.eta_h = eta_h; g.eta_r = eta_r;
+    g.fx = K[0]; g.fy = K[4]; g.cx = K[2]; g.cy = K[5];
+    for (int k = 0; k < n; ++k) {
+        if (!depths[k]) return fail(c, FASSMVS_EINVAL, "depth map %d is NULL", k);
+        if (depths[k] == depth) return fail(c, FASSMVS_EINVAL, "depth map %d is the filtered map", k);
+        g.dk[k] = depths[k];
+        for (int i = 0; i < 9; ++i) g.R[k][i] = R[9 * k + i];
+        for (int i = 0; i < 3; ++i) g.t[k][i] = t[3 * k + i];
+    }
+    FM_TRY(set_device(c));
+    cudaStream_t st = S(stream);
+    c->last = st;
+    fm::launch_geo_filter(g, depth, normal, conf, hits, st);
+    return launch_status(c, "geometric filter launch");
 }
 
 const char* fassmvs_last_error(const fassmvs_ctx* c)

@@ -125,6 +125,21 @@ void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, in
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
                        cudaStream_t st, int nparts = 1, size_t part_stride = 0, size_t pstride = 0,
                        size_t bstride = 0, int bshift = 3);
+// post-filters (Sec. 2.6): DoG mask (Alg. 3; 1 = enough texture, scratch:
+// tmp W*H bytes, parent / size W*H ints, err one int set on a capped walk),
+// estimates zeroed where the mask is 0, and the geometric consistency check
+// (Alg. 4) zeroing pixels with fewer than eta_h hits
+struct DogWeights { int32_t w[7]; };
+void launch_dog_mask(const uint8_t* img, int W, int H, int pitch, const DogWeights& dw, uint8_t* mask, uint8_t* tmp,
+                     int* parent, int* size, int* err, cudaStream_t st);
+void launch_apply_mask(const uint8_t* mask, int W, int H, float* depth, float* normal, float* conf, cudaStream_t st);
+struct GeoArgs {
+    int W, H, n, eta_h;
+    double fx, fy, cx, cy, eta_r;
+    const float* dk[kMaxViews];
+    double R[kMaxViews][9], t[kMaxViews][3];   // reference -> map k
+};
+void launch_geo_filter(const GeoArgs& g, float* depth, float* normal, float* conf, uint8_t* hits, cudaStream_t st);
 void launch_delta_table(double rho0, double drho, int G, float* delta, cudaStream_t st);
 // cost volume [Ds / 16][np][16] (as the batched cost kernel writes it) ->
 // [np][Ds] (as the aggregation reads it); Ds a multiple of 16

@@ -117,6 +117,9 @@ _SIGS = {
     "fassmvs_server_poll": [_VP, _VP, C.c_int, _VP, C.c_int],
     "fassmvs_server_get_stats": [_VP, _VP],
     "fassmvs_server_last_error": [_VP],
+    "fassmvs_dog_filter": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP],
+    "fassmvs_geo_filter": [_VP, _VP, _VP, _VP, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, C.c_double, C.c_int,
+                           _VP, _VP],
     "fassmvs_profile_enable": [_VP, C.c_int],
     "fassmvs_profile_read": [_VP, _VP, _VP, C.c_int],
     "fassmvs_sync": [_VP],
@@ -297,6 +300,31 @@ class Context:
 
     def sync(self):
         self._check(lib().fassmvs_sync(self._h))
+
+    # ------------------------------------------------------------ post-filters
+    def dog_filter(self, ref, depth=None, normal=None, conf=None):
+        """Alg. 3: returns the texture mask (uint8 tensor); depth / normal /
+        conf (if given) are zeroed in place where it is 0."""
+        import torch
+        H, W = ref.shape
+        mask = torch.empty((H, W), dtype=torch.uint8, device=ref.device)
+        self._check(lib().fassmvs_dog_filter(self._h, _ptr(ref), W, H, ref.stride(0), _ptr(depth), _ptr(normal),
+                                             _ptr(conf), _ptr(mask), _stream()))
+        return mask
+
+    def geo_filter(self, depth, K, depths, R, t, normal=None, conf=None, eta_r=10.0, eta_h=3):
+        """Alg. 4 in place on depth (and normal / conf); returns the hit counts."""
+        import torch
+        H, W = depth.shape
+        hits = torch.empty((H, W), dtype=torch.uint8, device=depth.device)
+        n = len(depths)
+        arr = (C.c_void_p * max(1, n))(*[x.data_ptr() for x in depths])
+        k_, kp = _dbl(K, 9)
+        r_, rp = _dbl(np.asarray(R, np.float64).reshape(-1), 9 * n) if n else (None, None)
+        t_, tp = _dbl(np.asarray(t, np.float64).reshape(-1), 3 * n) if n else (None, None)
+        self._check(lib().fassmvs_geo_filter(self._h, _ptr(depth), _ptr(normal), _ptr(conf), W, H, kp, n, arr, rp,
+                                             tp, float(eta_r), int(eta_h), _ptr(hits), _stream()))
+        return hits
 
     STAGES = ("pyramid", "census", "cost", "sgm", "wta", "median", "normals", "window")
 
