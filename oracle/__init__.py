@@ -56,6 +56,8 @@ def lib():
         _lib.or_ncc_window.restype = C.c_int
         _lib.or_sgm_aggregate.restype = C.c_int
         _lib.or_estimate.restype = C.c_int
+        _lib.or_plane_bounds.restype = C.c_int
+        _lib.or_cross_ratio_planes.restype = C.c_int
     return _lib
 
 
@@ -249,14 +251,39 @@ def window(dc, W, H, K, n, rho0, drho, G, D):
     return lo
 
 
-def dsn(dc, nc, W, H, K, drho, dmax=8):
+def dsn(dc, nc, W, H, K, drho, dmax=8, n=(0.0, 0.0, -1.0)):
+    """Eq. sgm-smooth-sn index jumps; n is the sweep normal."""
     dc = _c(dc, np.float32)
     nc = _c(nc, np.float32)
     Hc, Wc = dc.shape
     out = np.zeros((8, H, W), np.int8)
-    lib().or_dsn(_p(dc), _p(nc), Wc, Hc, W, H, _p(_c(K, np.float64)), C.c_double(drho), int(dmax),
-                 _p(out))
+    lib().or_dsn(_p(dc), _p(nc), Wc, Hc, W, H, _p(_c(K, np.float64)), _p(_c(n, np.float64)), C.c_double(drho),
+                 int(dmax), _p(out))
     return out
+
+
+def plane_bounds(K, W, H, n, d_min, d_max):
+    """(delta_min, delta_max) of the bounding planes (Sec. 2.2.2)."""
+    out = np.zeros(2, np.float64)
+    rc = lib().or_plane_bounds(_p(_c(K, np.float64)), int(W), int(H), _p(_c(n, np.float64)), C.c_double(d_min),
+                               C.c_double(d_max), _p(out))
+    if rc != 0:
+        raise ValueError("or_plane_bounds rc=%d" % rc)
+    return float(out[0]), float(out[1])
+
+
+def cross_ratio_planes(K, W, H, R, t, n, delta_min, delta_max, maxn=100000):
+    """Alg. 2 plane distances, far to near, and the index of camera k."""
+    R = _c(np.asarray(R, np.float64).reshape(-1, 9), np.float64)
+    t = _c(np.asarray(t, np.float64).reshape(-1, 3), np.float64)
+    out = np.zeros(maxn, np.float64)
+    k = C.c_int(-1)
+    m = lib().or_cross_ratio_planes(_p(_c(K, np.float64)), int(W), int(H), R.shape[0], _p(R), _p(t),
+                                    _p(_c(n, np.float64)), C.c_double(delta_min), C.c_double(delta_max), int(maxn),
+                                    _p(out), C.byref(k))
+    if m < 0:
+        raise ValueError("or_cross_ratio_planes rc=%d" % m)
+    return out[:m].copy(), k.value
 
 
 def dog_weights():

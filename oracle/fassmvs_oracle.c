@@ -810,21 +810,26 @@ OR_EXPORT void or_window(const float* dc, int Wc, int Hc, int W, int H, const do
 /* ------------------------------------------------------------------------ */
 /* Eq. sgm-smooth-sn: the index jump di_sn caused by the tangent plane of    */
 /* the prior normal n (from the coarser level) between p and its path        */
-/* predecessor p - r.  The paper gives no formula; reading for a fronto-     */
-/* parallel sweep: with P = d K^-1 (x, y, 1)^T, the predecessor ray meets    */
-/* the tangent plane n^T X = n^T P at depth lambda, and                     */
-/*   di = round((1/lambda - 1/d) / drho) = round(-(n^T K^-1 (rx, ry, 0)^T)  */
-/*                                            / (n^T P drho)),               */
-/* rounded half away from zero and clamped to +-dmax; di = 0 for a zero     */
-/* normal or when the tangent plane does not face the predecessor ray       */
-/* (n^T K^-1 (p - r, 1)^T >= -1e-6 or n^T K^-1 (p, 1)^T >= -1e-6).  Taken   */
-/* in FP32 with every operation IEEE-rounded in the order written below.    */
+/* predecessor p - r.  The paper gives no formula; reading: with             */
+/* P = d K^-1 (x, y, 1)^T, the predecessor ray meets the tangent plane       */
+/* n^T X = n^T P at lambda K^-1 (p - r, 1)^T, and di is the change of the    */
+/* sweep index 1/delta between the two points, delta = -m^T X for the sweep  */
+/* normal m.  With s0 = n^T K^-1 (p,1), s1 = n^T K^-1 (r,0), u0 = m^T K^-1    */
+/* (p,1), u1 = m^T K^-1 (r,0):                                              */
+/*   di = round((s1 u0 - s0 u1) / (d s0 u0 (u0 - u1) drho)),                */
+/* which for the fronto sweep m = (0,0,-1) (u0 = -1, u1 = 0) is             */
+/* round(-s1 / (d s0 drho)) = round((1/lambda - 1/d) / drho), operation for  */
+/* operation.  Rounded half away from zero and clamped to +-dmax; di = 0 for */
+/* a zero normal or when the tangent plane or the sweep planes do not face   */
+/* the two rays (s0, s0 - s1, u0 or u0 - u1 >= -1e-6).  Taken in FP32 with  */
+/* every operation IEEE-rounded in the order written below.                  */
 /* Output layout: int8 [8][H][W] in the path order of the aggregation.      */
 /* ------------------------------------------------------------------------ */
 OR_EXPORT void or_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H,
-                      const double K[9], double drho, int dmax, int8_t* dI)
+                      const double K[9], const double m[3], double drho, int dmax, int8_t* dI)
 {
     float fx = (float)K[0], fy = (float)K[4], cx = (float)K[2], cy = (float)K[5];
+    float sw0 = (float)m[0], sw1 = (float)m[1], sw2 = (float)m[2];
     float dr = (float)drho;
     for (int r = 0; r < 8; ++r)
         for (int y = 0; y < H; ++y)
@@ -846,10 +851,23 @@ OR_EXPORT void or_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, i
                 volatile float q1 = n1 * gy;
                 volatile float s1 = q0 + q1;                      /* n^T K^-1 (r,0) */
                 volatile float sp = s0 - s1;                      /* n^T K^-1 (p-r,1) */
-                if ((n0 != 0.0f || n1 != 0.0f || n2 != 0.0f) && s0 < -1e-6f && sp < -1e-6f && d > 0.0f) {
+                volatile float w0 = sw0 * a;
+                volatile float w1 = sw1 * b;
+                volatile float u01 = w0 + w1;
+                volatile float u0 = u01 + sw2;                    /* m^T K^-1 (p,1) */
+                volatile float v0 = sw0 * gx;
+                volatile float v1 = sw1 * gy;
+                volatile float u1 = v0 + v1;                      /* m^T K^-1 (r,0) */
+                volatile float uq = u0 - u1;                      /* m^T K^-1 (p-r,1) */
+                if ((n0 != 0.0f || n1 != 0.0f || n2 != 0.0f) && s0 < -1e-6f && sp < -1e-6f && u0 < -1e-6f &&
+                    uq < -1e-6f && d > 0.0f) {
                     volatile float den0 = d * s0;
-                    volatile float den = den0 * dr;
-                    volatile float num = -s1;
+                    volatile float den1 = den0 * u0;
+                    volatile float den2 = den1 * uq;
+                    volatile float den = den2 * dr;
+                    volatile float e0 = s1 * u0;
+                    volatile float e1 = s0 * u1;
+                    volatile float num = e0 - e1;
                     volatile float c = num / den;
                     float rc = c >= 0.0f ? floorf(c + 0.5f) : -floorf(-c + 0.5f);
                     if (rc > (float)dmax) rc = (float)dmax;
@@ -861,12 +879,171 @@ OR_EXPORT void or_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, i
 }
 
 /* ------------------------------------------------------------------------ */
-/* Sec. 2.1: the hierarchical loop.  From the coarsest level l = n-1 down to */
-/* 0: plane-sweep cost volume (full plane list at the top level, per-pixel  */
-/* windows below), SGM, WTA + refinement, 5x5 median, normals, confidence;  */
-/* the depth and normal maps of level l, upscaled by nearest neighbour,     */
-/* initialise level l-1.  Level l uses every 2^l-th plane of the finest     */
-/* list (reading): G_l = floor((G0 - 1) / 2^l) + 1, drho_l = 2^l drho.      */
+/* Sec. 2.2.2: plane selection.  Planes are n^T X + delta = 0 in the         */
+/* reference frame (P_ref = K [I | 0]); the fronto sweep is n = (0,0,-1),    */
+/* where delta is the depth.  A point at parameter s on the ray             */
+/* X = s K^-1 (u,v,1)^T lies on the plane delta when s = -delta / (n^T r).    */
+/* ------------------------------------------------------------------------ */
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* the viewing ray K^-1 (u, v, 1)^T of the reference camera */
+static void ref_ray(const double K[9], double u, double v, double r[3])
+{
+    double Ki[9];
+    mat3_inv(K, Ki);
+    for (int i = 0; i < 3; ++i) r[i] = Ki[3 * i] * u + Ki[3 * i + 1] * v + Ki[3 * i + 2];
+}
+
+/* pixel centres of the four image corners */
+static void corner_px(int W, int H, int c, double* u, double* v)
+{
+    *u = (c & 1) ? (double)(W - 1) : 0.0;
+    *v = (c & 2) ? (double)(H - 1) : 0.0;
+}
+
+/* Eq. of the bounding planes: the reference view frustum between the fronto */
+/* near and far planes at depths d_min and d_max has four corners on each,   */
+/* X = d K^-1 (u, v, 1)^T at the image corners.  delta_min is the smallest   */
+/* |n^T X| over the near corners.  Reading: delta_max is the LARGEST |n^T X|  */
+/* over the far corners -- the equation prints min for both, which for any   */
+/* slanted n would stop the sweep short of the far corners; n^T X is linear  */
+/* and the frustum is the convex hull of its 8 corners, so these two values  */
+/* enclose it.  Returns -1 when a corner ray does not meet the planes        */
+/* (n^T r >= 0: the sweep direction has no component along that ray).        */
+OR_EXPORT int or_plane_bounds(const double K[9], int W, int H, const double n[3], double d_min, double d_max,
+                              double out[2])
+{
+    double lo = INFINITY, hi = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        double u, v, r[3], Xn[3], Xf[3];
+        corner_px(W, H, c, &u, &v);
+        ref_ray(K, u, v, r);
+        if (!(dot3(n, r) < 0.0)) return -1;
+        for (int i = 0; i < 3; ++i) {
+            Xn[i] = d_min * r[i];
+            Xf[i] = d_max * r[i];
+        }
+        lo = fmin(lo, fabs(dot3(n, Xn)));
+        hi = fmax(hi, fabs(dot3(n, Xf)));
+    }
+    out[0] = lo;
+    out[1] = hi;
+    return 0;
+}
+
+/* x_k = K (R X + t) in homogeneous form */
+static void project_h(const double K[9], const double R[9], const double t[3], const double X[3], double x[3])
+{
+    double Y[3];
+    for (int i = 0; i < 3; ++i) Y[i] = R[3 * i] * X[0] + R[3 * i + 1] * X[1] + R[3 * i + 2] * X[2] + t[i];
+    for (int i = 0; i < 3; ++i) x[i] = K[3 * i] * Y[0] + K[3 * i + 1] * Y[1] + K[3 * i + 2] * Y[2];
+}
+
+/* sine of the angle between two rays given by their directions (App. A) */
+static double sin_between(const double a[3], const double b[3])
+{
+    double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    return sqrt(dot3(c, c)) / (sqrt(dot3(a, a)) * sqrt(dot3(b, b)));
+}
+
+/* Alg. 2: plane distances such that consecutive planes move the image of    */
+/* the extreme point by at most one pixel in camera k.  Cameras: X_k =       */
+/* R_k X + t_k (k < ncam).  Readings: (a) p_ref and camera k are the corner  */
+/* and camera with the longest image segment between the projections of    */
+/* P_min and P_max (the disparity range; the paper names the largest         */
+/* disparity, typically a corner, and the most distant camera); (b) the     */
+/* epipole enters only through the ray from C_k towards C_ref, taken from    */
+/* its homogeneous image K t_k, so a reference centre behind camera k needs  */
+/* no special case; (c) the walk takes whole steps p_i = p_max + i k for     */
+/* i = 0 .. ceil(L) - 1 (L the segment length) and then ends ON p_min with   */
+/* delta_min, so the last step is at most one pixel and both bounding planes */
+/* are in the list.  The distance of each step follows from the cross-ratio: */
+/* Q = delta (dmax - dmin) / (dmax (delta - dmin)) solved for delta.         */
+/* Every camera centre must lie in front of Pi_min: n^T C_i + delta_min > 0. */
+/* out[] gets the list far to near (delta_max first); returns the count, or  */
+/* -1 (a camera centre behind Pi_min), -2 (a corner ray misses the planes),  */
+/* -3 (no corner segment in any camera), -4 (more than maxn planes).         */
+OR_EXPORT int or_cross_ratio_planes(const double K[9], int W, int H, int ncam, const double* R, const double* t,
+                                    const double n[3], double delta_min, double delta_max, int maxn, double* out,
+                                    int* chosen)
+{
+    for (int i = 0; i < ncam; ++i) {
+        const double* Ri = R + 9 * i;
+        const double* ti = t + 3 * i;
+        double Ci[3];
+        for (int j = 0; j < 3; ++j) Ci[j] = -(Ri[j] * ti[0] + Ri[3 + j] * ti[1] + Ri[6 + j] * ti[2]);
+        if (!(dot3(n, Ci) + delta_min > 0.0)) return -1;
+    }
+    /* reading (a): camera k and p_ref */
+    int k = -1;
+    double best = 0.0, pu = 0.0, pv = 0.0;
+    for (int i = 0; i < ncam; ++i)
+        for (int c = 0; c < 4; ++c) {
+            double u, v, r[3], Pn[3], Pf[3], xn[3], xf[3];
+            corner_px(W, H, c, &u, &v);
+            ref_ray(K, u, v, r);
+            const double nr = dot3(n, r);
+            if (!(nr < 0.0)) return -2;
+            for (int j = 0; j < 3; ++j) {
+                Pn[j] = r[j] * (-delta_min / nr);
+                Pf[j] = r[j] * (-delta_max / nr);
+            }
+            project_h(K, R + 9 * i, t + 3 * i, Pn, xn);
+            project_h(K, R + 9 * i, t + 3 * i, Pf, xf);
+            if (!(xn[2] > 0.0 && xf[2] > 0.0)) continue;
+            const double len = hypot(xn[0] / xn[2] - xf[0] / xf[2], xn[1] / xn[2] - xf[1] / xf[2]);
+            if (len > best) {
+                best = len;
+                k = i;
+                pu = u;
+                pv = v;
+            }
+        }
+    if (k < 0) return -3;
+    if (chosen) *chosen = k;
+    const double* Rk = R + 9 * k;
+    const double* tk = t + 3 * k;
+    /* step 1: the viewing ray through p_ref meets Pi_min and Pi_max */
+    double V[3], Pmin[3], Pmax[3];
+    ref_ray(K, pu, pv, V);
+    const double nV = dot3(n, V);
+    for (int j = 0; j < 3; ++j) {
+        Pmin[j] = V[j] * (-delta_min / nV);
+        Pmax[j] = V[j] * (-delta_max / nV);
+    }
+    /* step 2: images of C_ref, P_min and P_max in camera k */
+    const double Cref[3] = {0.0, 0.0, 0.0};
+    double eh[3], xmin[3], xmax[3];
+    project_h(K, Rk, tk, Cref, eh);
+    project_h(K, Rk, tk, Pmin, xmin);
+    project_h(K, Rk, tk, Pmax, xmax);
+    const double pmin[2] = {xmin[0] / xmin[2], xmin[1] / xmin[2]};
+    const double pmax[2] = {xmax[0] / xmax[2], xmax[1] / xmax[2]};
+    /* step 3: unit vector along the epipolar line, from p_max to p_min */
+    const double L = hypot(pmin[0] - pmax[0], pmin[1] - pmax[1]);
+    const double kx = (pmin[0] - pmax[0]) / L, ky = (pmin[1] - pmax[1]) / L;
+    /* rays of camera k (directions in its own frame, K^-1 x) */
+    double Kinv[9], Ve[3], Vmin[3], Vmax[3];
+    mat3_inv(K, Kinv);
+    for (int j = 0; j < 3; ++j) {
+        Ve[j] = Kinv[3 * j] * eh[0] + Kinv[3 * j + 1] * eh[1] + Kinv[3 * j + 2] * eh[2];
+        Vmin[j] = Kinv[3 * j] * pmin[0] + Kinv[3 * j + 1] * pmin[1] + Kinv[3 * j + 2];
+        Vmax[j] = Kinv[3 * j] * pmax[0] + Kinv[3 * j + 1] * pmax[1] + Kinv[3 * j + 2];
+    }
+    const int steps = (int)ceil(L);
+    if (steps + 1 > maxn) return -4;
+    int m = 0;
+    for (int i = 0; i < steps; ++i) {
+        const double pi[2] = {pmax[0] + i * kx, pmax[1] + i * ky};
+        double Vi[3];
+        for (int j = 0; j < 3; ++j) Vi[j] = Kinv[3 * j] * pi[0] + Kinv[3 * j + 1] * pi[1] + Kinv[3 * j + 2];
+        const double Q = sin_between(Ve, Vi) * sin_between(Vmin, Vmax) /
+                         (sin_between(Ve, Vmax) * sin_between(Vmin, Vi));
+        out[m++] = Q * delta_max * delta_min / (Q * delta_max - (delta_max - delta_min));
+    }
+    out[m++] = delta_min;
+    return m;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Post-filters (Sec. 2.6).                                                  */
@@ -1031,6 +1208,12 @@ OR_EXPORT int or_geo_hits(const float* dref, int W, int H, const double K[9], in
 }
 
 /* ------------------------------------------------------------------------ */
+/* Sec. 2.1: the hierarchical loop.  From the coarsest level l = n-1 down to */
+/* 0: plane-sweep cost volume (full plane list at the top level, per-pixel  */
+/* windows below), SGM, WTA + refinement, 5x5 median, normals, confidence;  */
+/* the depth and normal maps of level l, upscaled by nearest neighbour,     */
+/* initialise level l-1.  Level l uses every 2^l-th plane of the finest     */
+/* list (reading): G_l = floor((G0 - 1) / 2^l) + 1, drho_l = 2^l drho.      */
 typedef struct {
     int32_t levels;
     int32_t D[8];          /* window size per level (the top level uses G_top) */
@@ -1097,7 +1280,7 @@ OR_EXPORT int or_estimate(const or_config* cfg, const uint8_t* ref, const uint8_
             or_window(dprev, Ws[l + 1], Hs[l + 1], w, h, Kl, n, rho_far, drl, Gl, D, lo);
             if (cfg->variant == 1) {
                 dI = (int8_t*)malloc(8 * np);
-                or_dsn(dprev, nprev, Ws[l + 1], Hs[l + 1], w, h, Kl, drl, cfg->dmax, dI);
+                or_dsn(dprev, nprev, Ws[l + 1], Hs[l + 1], w, h, Kl, n, drl, cfg->dmax, dI);
             }
         }
         uint16_t* S = (uint16_t*)malloc(sizeof(uint16_t) * np * D);

@@ -740,3 +740,159 @@ def test_geometric_consistency_on_a_plane_and_its_outliers(orc):
     zero = dref.copy()
     zero[0:5] = 0.0
     assert orc.geo_hits(zero, K, dks, R, ts)[0:5].sum() == 0                 # invalid depth: no hits
+
+
+# ---------------------------------------------------------------- plane selection (Sec. 2.2.2, Alg. 2)
+def _rot(axis, deg):
+    a = math.radians(deg)
+    ax = np.asarray(axis, float) / np.linalg.norm(axis)
+    Kx = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    return np.eye(3) + math.sin(a) * Kx + (1 - math.cos(a)) * Kx @ Kx
+
+
+def _Kc(W, H, f):
+    return np.array([[f, 0, (W - 1) / 2], [0, f, (H - 1) / 2], [0, 0, 1.0]])
+
+
+def _unit(v):
+    v = np.asarray(v, float)
+    return v / np.linalg.norm(v)
+
+
+def _images_on_planes(K, R, t, n, deltas, W, H):
+    """Image in camera (R, t) of the point where every reference pixel's ray
+    meets each plane n^T X + delta = 0, by direct intersection and projection:
+    array [planes][H][W][2]."""
+    xs, ys = np.meshgrid(np.arange(W, dtype=float), np.arange(H, dtype=float))
+    rays = np.stack([xs, ys, np.ones_like(xs)], -1) @ np.linalg.inv(K).T
+    s = -np.asarray(deltas)[:, None, None] / (rays @ n)[None]
+    X = rays[None] * s[..., None]
+    x = (X @ R.T + t) @ K.T
+    return x[..., :2] / x[..., 2:]
+
+
+def test_plane_bounds_fronto_are_the_depth_range(orc):
+    K = _Kc(80, 60, 70.0)
+    assert orc.plane_bounds(K, 80, 60, [0, 0, -1.0], 3.5, 47.0) == (3.5, 47.0)
+
+
+@pytest.mark.parametrize("nv", [[0, -0.5, -1.0], [0.3, 0.2, -1.0], [-0.6, 0.0, -1.0]])
+def test_plane_bounds_enclose_the_frustum(orc, nv):
+    """Brute force: |n^T X| over random points of the frustum stays inside
+    [delta_min, delta_max] and both bounds are reached at corners."""
+    W, H, f, dmin, dmax = 80, 60, 70.0, 3.0, 40.0
+    K, n = _Kc(W, H, f), _unit(nv)
+    lo, hi = orc.plane_bounds(K, W, H, n, dmin, dmax)
+    g = np.random.default_rng(61)
+    px = np.stack([g.uniform(0, W - 1, 20000), g.uniform(0, H - 1, 20000), np.ones(20000)], -1)
+    X = (px @ np.linalg.inv(K).T) * g.uniform(dmin, dmax, 20000)[:, None]
+    a = np.abs(X @ n)
+    assert a.min() >= lo - 1e-12 and a.max() <= hi + 1e-12
+    corners = np.array([[u, v, 1.0] for v in (0, H - 1) for u in (0, W - 1)]) @ np.linalg.inv(K).T
+    assert abs(np.abs(corners * dmin @ n).min() - lo) < 1e-12
+    assert abs(np.abs(corners * dmax @ n).max() - hi) < 1e-12
+    assert hi > dmax * min(np.abs(corners @ n)) + 1e-3          # max, not min, over the far corners
+
+
+def test_plane_bounds_reject_rays_that_miss_the_planes(orc):
+    with pytest.raises(ValueError):
+        orc.plane_bounds(_Kc(80, 60, 70.0), 80, 60, [1.0, 0, 0], 3.0, 40.0)
+
+
+def test_cross_ratio_rectified_stereo_closed_form(orc):
+    """Rectified pair with baseline b: disparity f b / delta, so one-pixel
+    steps are uniform in inverse distance: 1/delta_i = 1/delta_max + i/(f b)."""
+    W, H, f, b = 64, 48, 400.0, 0.5
+    d, k = orc.cross_ratio_planes(_Kc(W, H, f), W, H, np.eye(3)[None], [[-b, 0, 0]], [0, 0, -1.0], 5.0, 50.0)
+    L = f * b / 5.0 - f * b / 50.0                                # 36 px: an integral segment
+    assert k == 0 and len(d) == int(math.ceil(L)) + 1
+    i = np.arange(len(d))
+    assert np.allclose(1.0 / d, 1.0 / 50.0 + i / (f * b), rtol=1e-12, atol=0)
+    assert d[0] == pytest.approx(50.0, rel=1e-14) and d[-1] == 5.0
+
+
+def test_cross_ratio_ragged_segment_ends_on_the_near_plane(orc):
+    W, H, f, b = 64, 48, 60.0, 0.5                               # segment 5.4 px
+    d, _ = orc.cross_ratio_planes(_Kc(W, H, f), W, H, np.eye(3)[None], [[-b, 0, 0]], [0, 0, -1.0], 5.0, 50.0)
+    assert len(d) == 7 and d[-1] == 5.0
+    assert np.allclose(1.0 / d[:6], 1.0 / 50.0 + np.arange(6) / (f * b), rtol=1e-12, atol=0)
+
+
+_POSES = {
+    "two_sided": (np.stack([_rot([0, 1, 0], -5), _rot([0, 1, 0], 8)]),
+                  np.array([[-0.4, 0.05, 0.1], [0.9, -0.1, 0.2]]), 4.0, 40.0),
+    "forward": (np.stack([_rot([1, 0, 0], 3)]), np.array([[0.3, 0.0, -2.0]]), 5.0, 60.0),
+    "oblique": (np.stack([_rot([1, 0.2, 0], 4), _rot([0.3, 1, 0], -6)]),
+                np.array([[-0.7, 0.3, -0.2], [0.5, 0.6, 0.4]]), 6.0, 80.0),
+}
+
+
+@pytest.mark.parametrize("pose", sorted(_POSES))
+@pytest.mark.parametrize("nv", [[0, 0, -1.0], [0, -0.5, -1.0], [0.3, 0.2, -1.0]])
+def test_cross_ratio_steps_move_every_pixel_at_most_one_pixel(orc, pose, nv):
+    """Direct intersection and projection (no cross-ratio): in camera k one
+    corner moves exactly 1 px per step (the last step at most 1 px).  Fronto
+    sweeps move no pixel of any camera by more than 1 px; for slanted sweeps
+    the bound is exact only at p_ref, elsewhere it stays within 1.1 px."""
+    W, H, f = 64, 48, 60.0
+    R, t, dmin, dmax = _POSES[pose]
+    K, n = _Kc(W, H, f), _unit(nv)
+    lo, hi = orc.plane_bounds(K, W, H, n, dmin, dmax)
+    d, k = orc.cross_ratio_planes(K, W, H, R, t, n, lo, hi)
+    assert np.all(np.diff(d) < 0) and d[0] == pytest.approx(hi, rel=1e-12) and d[-1] == lo
+    worst, exact = 0.0, False
+    for c in range(len(R)):
+        x = _images_on_planes(K, R[c], t[c], n, d, W, H)
+        step = np.hypot(*np.moveaxis(np.diff(x, axis=0), -1, 0))     # [planes-1][H][W]
+        worst = max(worst, step.max())
+        if c == k:
+            for (u, v) in [(0, 0), (W - 1, 0), (0, H - 1), (W - 1, H - 1)]:
+                s = step[:, v, u]
+                exact |= bool(np.allclose(s[:-1], 1.0, atol=1e-9) and s[-1] <= 1.0 + 1e-9)
+    assert exact and worst <= (1.0 + 1e-9 if nv == [0, 0, -1.0] else 1.1)
+
+
+def test_cross_ratio_picks_the_camera_with_the_widest_disparity_range(orc):
+    W, H, f = 64, 48, 200.0
+    R = np.stack([np.eye(3)] * 3)
+    t = np.array([[-0.2, 0, 0], [0.6, 0, 0], [-0.35, 0, 0]])
+    d, k = orc.cross_ratio_planes(_Kc(W, H, f), W, H, R, t, [0, 0, -1.0], 5.0, 50.0)
+    assert k == 1 and len(d) == int(math.ceil(f * 0.6 * (1 / 5.0 - 1 / 50.0))) + 1
+
+
+def test_cross_ratio_rejects_a_camera_behind_the_nearest_plane(orc):
+    with pytest.raises(ValueError):                               # C_k at z = 6 > delta_min = 5
+        orc.cross_ratio_planes(_Kc(64, 48, 60.0), 64, 48, np.eye(3)[None], [[0.3, 0, -6.0]], [0, 0, -1.0],
+                               5.0, 60.0)
+
+
+def test_dsn_with_a_slanted_sweep_normal_matches_the_plane_index_step(orc):
+    """R11 with sweep normal m: the step of 1/delta = -1/(m^T X) between P and
+    where the predecessor ray meets the tangent plane."""
+    W, H = 24, 18
+    K = np.array([[40.0, 0, 11.5], [0, 40.0, 8.5], [0, 0, 1]])
+    drho = 0.001
+    for mv in ([0.0, -0.5, -1.0], [0.3, 0.2, -1.0]):
+        m = _unit(mv)
+        for nv in ([0, 0, -1.0], [0.0, -0.6, -0.8], [0.4, 0.2, -0.89]):
+            n = _unit(nv)
+            Kc = K.copy()
+            Kc[:2] /= 2.0
+            Wc, Hc = W // 2, H // 2
+            dc = _plane_depth(n, 10.0, Kc, Wc, Hc)
+            nc = np.broadcast_to(n.astype(np.float32), (Hc, Wc, 3)).copy()
+            di = orc.dsn(dc, nc, W, H, K, drho, dmax=100, n=m)
+            nonzero = 0
+            for r in range(8):
+                dx, dy = DIRS[r]
+                for (x, y) in [(6, 5), (13, 9), (20, 14)]:
+                    d = dc[y // 2, x // 2]
+                    P = d * np.array([(x - K[0, 2]) / K[0, 0], (y - K[1, 2]) / K[1, 1], 1.0])
+                    q = np.array([(x - dx - K[0, 2]) / K[0, 0], (y - dy - K[1, 2]) / K[1, 1], 1.0])
+                    Q = q * (n @ P) / (n @ q)
+                    ex = (-1.0 / (m @ Q) + 1.0 / (m @ P)) / drho
+                    if abs(abs(ex) - math.floor(abs(ex)) - 0.5) < 1e-3:
+                        continue
+                    assert di[r, y, x] == int(math.copysign(math.floor(abs(ex) + 0.5), ex)), (mv, nv, r, x, y)
+                    nonzero += di[r, y, x] != 0
+            assert nonzero > 0                                    # a slanted sweep sees steps even on fronto planes
