@@ -283,6 +283,43 @@ FASSMVS_API fassmvs_status fassmvs_server_poll(fassmvs_server* srv, fassmvs_resu
 FASSMVS_API fassmvs_status fassmvs_server_get_stats(fassmvs_server* srv, fassmvs_server_stats* stats);
 FASSMVS_API const char* fassmvs_server_last_error(const fassmvs_server* srv);
 
+/* ---- plane selection (Sec. 2.2.2, Alg. 2; host-side, no device work) ------- */
+
+/* Distances of the bounding planes n^T X + delta = 0 (n unit, reference
+ * frame, P_ref = K [I | 0]) of the reference view frustum cut by the fronto
+ * near and far planes at depths d_min < d_max (Eq. of the bounding planes):
+ * delta_min is the smallest |n^T X| over the four near corners, delta_max the
+ * largest over the four far corners (read so that the sweep encloses the
+ * frustum; the equation prints min for both).  Corners: the rays through pixel
+ * centres (0,0), (W-1,0), (0,H-1), (W-1,H-1).  All arguments on the HOST.
+ * FASSMVS_EINVAL when n is not a unit vector or a corner ray does not meet the
+ * planes (n^T r >= 0). */
+FASSMVS_API fassmvs_status fassmvs_plane_bounds(const double K[9], int W, int H, const double n[3], double d_min,
+                                                double d_max, double* delta_min, double* delta_max);
+
+/* Plane distances by the cross-ratio (Alg. 2) for n_cams matching cameras,
+ * X_k = R_k X + t_k (R: n_cams x 9 row-major, t: n_cams x 3; HOST).  p_ref and
+ * camera k are the image corner and camera with the longest image segment
+ * between the projections of the bounding planes; that segment is walked in
+ * whole pixels from the far to the near plane, each step's distance following
+ * from the cross-ratio of the rays of camera k through the epipole, the two
+ * ends and the step, and the walk ends on delta_min (the last step is at most
+ * one pixel).  deltas (HOST, max_planes entries, or NULL to count) receives
+ * the list far to near, delta_max first; *count its length; *camera (may be
+ * NULL) the index of camera k.  `uniform` (may be NULL) receives the sweep
+ * the estimate takes: G0 planes uniform in inverse distance from 1/delta_max
+ * to 1/delta_min, whose step is at most the smaller of the one-pixel steps of
+ * p_ref at the two ends of its segment (its image moves as a projective
+ * function of 1/delta, so no step then moves p_ref by more than a pixel).
+ * FASSMVS_EINVAL when a camera centre is not in front of Pi_min
+ * (n^T C_i + delta_min <= 0), a corner ray misses the planes, no camera sees
+ * a segment, or deltas is given and more than max_planes planes are needed
+ * (*count is set). */
+FASSMVS_API fassmvs_status fassmvs_cross_ratio_planes(const double K[9], int W, int H, int n_cams, const double* R,
+                                                      const double* t, const double n[3], double delta_min,
+                                                      double delta_max, int max_planes, double* deltas, int* count,
+                                                      int* camera, fassmvs_planes* uniform);
+
 /* ---- post-filters (Sec. 2.6) ---------------------------------------------- */
 
 /* Difference-of-Gaussian texture mask (Alg. 3) of the reference image (W x H
@@ -411,11 +448,13 @@ FASSMVS_API fassmvs_status fassmvs_window(fassmvs_ctx* ctx, const float* dc, int
                               int G, int D, int32_t* lo, void* stream);
 
 /* Eq. sgm-smooth-sn index jumps from the upscaled coarse depth dc and normal
- * nc (Wc x Hc): di = round_half_away((1/lambda - 1/d) / drho), clamped to
- * +-dmax, 0 when the tangent plane does not face the rays (FP32). */
+ * nc (Wc x Hc) for the sweep normal n: the predecessor ray meets the tangent
+ * plane at Q, di = round_half_away((1/delta(Q) - 1/delta(P)) / drho) with
+ * delta(X) = -n^T X, clamped to +-dmax, 0 when the tangent plane or the sweep
+ * planes do not face the rays (FP32; for n = (0,0,-1) delta is the depth). */
 FASSMVS_API fassmvs_status fassmvs_dsn(fassmvs_ctx* ctx, const float* dc, const float* nc, int Wc, int Hc,
-                           int W, int H, const double K[9], double drho, int dmax, int8_t* dI,
-                           void* stream);
+                           int W, int H, const double K[9], const double n[3], double drho, int dmax,
+                           int8_t* dI, void* stream);
 
 /* Stage timers.  While enabled, the library brackets each stage it launches
  * with CUDA events on the call's stream and accumulates the elapsed time

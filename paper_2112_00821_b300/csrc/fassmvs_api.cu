@@ -502,13 +502,14 @@ fassmvs_status fassmvs_window(fassmvs_ctx* c, const float* dc, int Wc, int Hc, i
 }
 
 fassmvs_status fassmvs_dsn(fassmvs_ctx* c, const float* dc, const float* nc, int Wc, int Hc, int W, int H,
-                           const double K[9], double drho, int dmax, int8_t* dI, void* stream)
+                           const double K[9], const double n[3], double drho, int dmax, int8_t* dI, void* stream)
 {
     if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
-    if (!dc || !nc || !dI || !K || Wc < 1 || Hc < 1 || W < 1 || H < 1 || dmax < 0 || dmax > 127)
+    if (!dc || !nc || !dI || !K || !n || Wc < 1 || Hc < 1 || W < 1 || H < 1 || dmax < 0 || dmax > 127)
         return fail(c, FASSMVS_EINVAL, "bad dsn arguments");
     FM_TRY(set_device(c));
-    fm::launch_dsn(dc, nc, Wc, Hc, W, H, intr(K), (float)drho, dmax, dI, S(stream));
+    const float nf[3] = {(float)n[0], (float)n[1], (float)n[2]};
+    fm::launch_dsn(dc, nc, Wc, Hc, W, H, intr(K), nf, (float)drho, dmax, dI, S(stream));
     c->last = S(stream);
     return launch_status(c, "dsn launch");
 }
@@ -784,8 +785,8 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 fm::launch_window(F.dprev, F.Ws[l + 1], F.Hs[l + 1], F.w, F.h, intr(F.Kl), nf, (float)X.planes.rho_far,
                                   (float)F.drl, F.Gl, F.D, (int32_t*)F.plo, st);
                 if (cfg.variant == 1)
-                    fm::launch_dsn(F.dprev, F.nprev, F.Ws[l + 1], F.Hs[l + 1], F.w, F.h, intr(F.Kl), (float)F.drl,
-                                   cfg.dmax, (int8_t*)F.pdI, st);
+                    fm::launch_dsn(F.dprev, F.nprev, F.Ws[l + 1], F.Hs[l + 1], F.w, F.h, intr(F.Kl), nf,
+                                   (float)F.drl, cfg.dmax, (int8_t*)F.pdI, st);
             } else if (cfg.variant == 1) {
                 FM_TRY(cuda_check(c, cudaMemsetAsync(F.pdI, 0, 8 * np, st), "memset dI"));
             }
@@ -1186,6 +1187,155 @@ static fm::DogWeights dog_weights()
     }
     w.w[3] += 256 - tot;
     return w;
+}
+
+// ---------------------------------------------------------------- plane selection
+// Sec. 2.2.2 and Alg. 2: host-side FP64 geometry, no device work.  Planes are
+// n^T X + delta = 0 in the reference frame; the ray X = s K^-1 (u, v, 1)^T
+// meets the plane delta at s = -delta / (n^T r).
+
+namespace {
+struct V3 {
+    double x, y, z;
+};
+V3 v3(double x, double y, double z) { return V3{x, y, z}; }
+V3 mul(V3 a, double s) { return v3(a.x * s, a.y * s, a.z * s); }
+double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+V3 cross(V3 a, V3 b) { return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+double vlen(V3 a) { return std::sqrt(dot(a, a)); }
+V3 mat_vec(const double M[9], V3 a)
+{
+    return v3(M[0] * a.x + M[1] * a.y + M[2] * a.z, M[3] * a.x + M[4] * a.y + M[5] * a.z,
+              M[6] * a.x + M[7] * a.y + M[8] * a.z);
+}
+// homogeneous image K (R X + t)
+V3 image_h(const double K[9], const double R[9], const double t[3], V3 X)
+{
+    const V3 Y = mat_vec(R, X);
+    return mat_vec(K, v3(Y.x + t[0], Y.y + t[1], Y.z + t[2]));
+}
+// sine of the angle between two rays (directions)
+double sin_between(V3 a, V3 b) { return vlen(cross(a, b)) / (vlen(a) * vlen(b)); }
+V3 corner_ray(const double Ki[9], int W, int H, int c)
+{
+    return mat_vec(Ki, v3((c & 1) ? W - 1 : 0, (c & 2) ? H - 1 : 0, 1.0));
+}
+}  // namespace
+
+fassmvs_status fassmvs_plane_bounds(const double K[9], int W, int H, const double n[3], double d_min, double d_max,
+                                    double* delta_min, double* delta_max)
+{
+    if (!K || !n || !delta_min || !delta_max) return fail(nullptr, FASSMVS_EINVAL, "NULL argument");
+    double Ki[9];
+    if (!k_inverse(K, Ki) || W < 1 || H < 1) return fail(nullptr, FASSMVS_EINVAL, "bad K or image size");
+    if (!(d_min > 0.0) || !(d_max > d_min)) return fail(nullptr, FASSMVS_EINVAL, "need 0 < d_min < d_max");
+    const V3 nn = v3(n[0], n[1], n[2]);
+    if (!(std::fabs(vlen(nn) - 1.0) < 1e-9)) return fail(nullptr, FASSMVS_EINVAL, "n must be a unit vector");
+    double lo = HUGE_VAL, hi = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        const V3 r = corner_ray(Ki, W, H, c);
+        if (!(dot(nn, r) < 0.0)) return fail(nullptr, FASSMVS_EINVAL, "a corner ray does not meet the planes");
+        lo = std::min(lo, std::fabs(dot(nn, mul(r, d_min))));
+        hi = std::max(hi, std::fabs(dot(nn, mul(r, d_max))));
+    }
+    *delta_min = lo;
+    *delta_max = hi;
+    return FASSMVS_OK;
+}
+
+fassmvs_status fassmvs_cross_ratio_planes(const double K[9], int W, int H, int n_cams, const double* R,
+                                          const double* t, const double n[3], double delta_min, double delta_max,
+                                          int max_planes, double* deltas, int* count, int* camera,
+                                          fassmvs_planes* uniform)
+{
+    if (!K || !R || !t || !n || !count) return fail(nullptr, FASSMVS_EINVAL, "NULL argument");
+    double Ki[9];
+    if (!k_inverse(K, Ki) || W < 1 || H < 1) return fail(nullptr, FASSMVS_EINVAL, "bad K or image size");
+    if (n_cams < 1) return fail(nullptr, FASSMVS_EINVAL, "need at least one camera");
+    if (!(delta_min > 0.0) || !(delta_max > delta_min))
+        return fail(nullptr, FASSMVS_EINVAL, "need 0 < delta_min < delta_max");
+    if (deltas && max_planes < 2) return fail(nullptr, FASSMVS_EINVAL, "max_planes must be >= 2");
+    const V3 nn = v3(n[0], n[1], n[2]);
+    if (!(std::fabs(vlen(nn) - 1.0) < 1e-9)) return fail(nullptr, FASSMVS_EINVAL, "n must be a unit vector");
+    for (int i = 0; i < n_cams; ++i) {
+        const double* Ri = R + 9 * i;
+        const double* ti = t + 3 * i;
+        // C_i = -R_i^T t_i must lie in front of Pi_min
+        const V3 Ci = v3(-(Ri[0] * ti[0] + Ri[3] * ti[1] + Ri[6] * ti[2]), -(Ri[1] * ti[0] + Ri[4] * ti[1] + Ri[7] * ti[2]),
+                         -(Ri[2] * ti[0] + Ri[5] * ti[1] + Ri[8] * ti[2]));
+        if (!(dot(nn, Ci) + delta_min > 0.0))
+            return fail(nullptr, FASSMVS_EINVAL, "camera %d is not in front of the nearest plane", i);
+    }
+    // p_ref and camera k: the longest image segment between the bounding planes
+    int k = -1, corner = 0;
+    double L = 0.0;
+    for (int i = 0; i < n_cams; ++i)
+        for (int c = 0; c < 4; ++c) {
+            const V3 r = corner_ray(Ki, W, H, c);
+            const double nr = dot(nn, r);
+            if (!(nr < 0.0)) return fail(nullptr, FASSMVS_EINVAL, "a corner ray does not meet the planes");
+            const V3 a = image_h(K, R + 9 * i, t + 3 * i, mul(r, -delta_min / nr));
+            const V3 b = image_h(K, R + 9 * i, t + 3 * i, mul(r, -delta_max / nr));
+            if (!(a.z > 0.0 && b.z > 0.0)) continue;
+            const double len = std::hypot(a.x / a.z - b.x / b.z, a.y / a.z - b.y / b.z);
+            if (len > L) {
+                L = len;
+                k = i;
+                corner = c;
+            }
+        }
+    if (k < 0) return fail(nullptr, FASSMVS_EINVAL, "no corner segment between the planes in any camera");
+    const double* Rk = R + 9 * k;
+    const double* tk = t + 3 * k;
+    const V3 V = corner_ray(Ki, W, H, corner);
+    const double nV = dot(nn, V);
+    const V3 xmin = image_h(K, Rk, tk, mul(V, -delta_min / nV));
+    const V3 xmax = image_h(K, Rk, tk, mul(V, -delta_max / nV));
+    const double pmin[2] = {xmin.x / xmin.z, xmin.y / xmin.z}, pmax[2] = {xmax.x / xmax.z, xmax.y / xmax.z};
+    const double kx = (pmin[0] - pmax[0]) / L, ky = (pmin[1] - pmax[1]) / L;
+    // rays of camera k; the epipole's ray runs from C_k towards C_ref, whose
+    // homogeneous image is K t_k: its direction is t_k whatever side C_ref is on
+    const V3 Ve = v3(tk[0], tk[1], tk[2]);
+    const V3 Vmin = mat_vec(Ki, v3(pmin[0], pmin[1], 1.0)), Vmax = mat_vec(Ki, v3(pmax[0], pmax[1], 1.0));
+    const double s_mm = sin_between(Vmin, Vmax), s_emax = sin_between(Ve, Vmax);
+    // distance of the plane whose image of p_ref is `a` pixels from p_max
+    auto delta_at = [&](double a) {
+        const V3 Vi = mat_vec(Ki, v3(pmax[0] + a * kx, pmax[1] + a * ky, 1.0));
+        const double Q = sin_between(Ve, Vi) * s_mm / (s_emax * sin_between(Vmin, Vi));
+        return Q * delta_max * delta_min / (Q * delta_max - (delta_max - delta_min));
+    };
+    const int steps = (int)std::ceil(L);
+    *count = steps + 1;
+    if (camera) *camera = k;
+    if (deltas && steps + 1 > max_planes)
+        return fail(nullptr, FASSMVS_EINVAL, "%d planes needed, more than max_planes", steps + 1);
+    if (deltas) {
+        for (int i = 0; i < steps; ++i) deltas[i] = delta_at(i);
+        deltas[steps] = delta_min;
+    }
+    if (uniform) {
+        // uniform in inverse distance, covering [delta_min, delta_max]: what
+        // the estimate sweeps.  The image of p_ref moves along the epipolar
+        // line as a projective function of 1/delta, so its speed is monotone
+        // and largest at one end; the step is the smaller of the one-pixel
+        // steps at the two ends, and then no step moves p_ref by more than a
+        // pixel.  The range is then split evenly so that the last plane is
+        // Pi_min itself (past it p_ref would move faster still).  A segment
+        // shorter than a pixel gives the two bounding planes.
+        const double range = 1.0 / delta_min - 1.0 / delta_max;
+        double inv_step = range;
+        if (L > 1.0) {
+            inv_step = std::min(1.0 / delta_at(1.0) - 1.0 / delta_max, 1.0 / delta_min - 1.0 / delta_at(L - 1.0));
+        }
+        const int32_t G0 = (int32_t)std::ceil(range / inv_step - 1e-9) + 1;
+        uniform->n[0] = n[0];
+        uniform->n[1] = n[1];
+        uniform->n[2] = n[2];
+        uniform->rho_far = 1.0 / delta_max;
+        uniform->drho = range / (G0 - 1);
+        uniform->G0 = G0;
+    }
+    return FASSMVS_OK;
 }
 
 fassmvs_status fassmvs_dog_filter(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch, float* depth,

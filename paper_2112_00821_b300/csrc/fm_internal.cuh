@@ -150,7 +150,7 @@ void launch_normals(const float* depth, const uint8_t* img, int img_pitch, int W
                     float rho_deg, float* conf, cudaStream_t st);
 void launch_window(const float* dc, int Wc, int Hc, int W, int H, Intr K, const float n[3],
                    float rho0, float drho, int G, int D, int32_t* lo, cudaStream_t st);
-void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, Intr K,
+void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, Intr K, const float m[3],
                 float drho, int dmax, int8_t* dI, cudaStream_t st);
 
 // Records the thread-local error text returned by fassmvs_last_error(NULL).

@@ -267,8 +267,11 @@ __global__ void window_kernel(const float* __restrict__ dc, int Wc, int Hc, int 
 }
 
 // ---------------------------------------------------------------- surface-normal jumps (FP32)
+// m: the sweep normal; the jump is the change of 1/delta = -1/(m^T X) between
+// P and the point where the predecessor ray meets the tangent plane, in the
+// oracle's FP32 operation order (for m = (0,0,-1) it is -s1 / (d s0 drho))
 __global__ void dsn_kernel(const float* __restrict__ dc, const float* __restrict__ nc, int Wc,
-                           int Hc, int W, int H, Intr K, float drho, int dmax,
+                           int Hc, int W, int H, Intr K, float sw0, float sw1, float sw2, float drho, int dmax,
                            int8_t* __restrict__ dI)
 {
     const int kdx[8] = {1, -1, 0, 0, 1, -1, 1, -1};
@@ -282,6 +285,7 @@ __global__ void dsn_kernel(const float* __restrict__ dc, const float* __restrict
     const float a = __fdiv_rn(__fsub_rn((float)x, K.cx), K.fx);
     const float b = __fdiv_rn(__fsub_rn((float)y, K.cy), K.fy);
     const float s0 = __fadd_rn(__fadd_rn(__fmul_rn(n0, a), __fmul_rn(n1, b)), n2);
+    const float u0 = __fadd_rn(__fadd_rn(__fmul_rn(sw0, a), __fmul_rn(sw1, b)), sw2);
     const bool nz = (n0 != 0.0f || n1 != 0.0f || n2 != 0.0f);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -289,10 +293,13 @@ __global__ void dsn_kernel(const float* __restrict__ dc, const float* __restrict
         const float gy = __fdiv_rn((float)kdy[r], K.fy);
         const float s1 = __fadd_rn(__fmul_rn(n0, gx), __fmul_rn(n1, gy));
         const float sp = __fsub_rn(s0, s1);
+        const float u1 = __fadd_rn(__fmul_rn(sw0, gx), __fmul_rn(sw1, gy));
+        const float uq = __fsub_rn(u0, u1);
         int out = 0;
-        if (nz && s0 < -1e-6f && sp < -1e-6f && d > 0.0f) {
-            const float den = __fmul_rn(__fmul_rn(d, s0), drho);
-            const float c = __fdiv_rn(-s1, den);
+        if (nz && s0 < -1e-6f && sp < -1e-6f && u0 < -1e-6f && uq < -1e-6f && d > 0.0f) {
+            const float den = __fmul_rn(__fmul_rn(__fmul_rn(__fmul_rn(d, s0), u0), uq), drho);
+            const float num = __fsub_rn(__fmul_rn(s1, u0), __fmul_rn(s0, u1));
+            const float c = __fdiv_rn(num, den);
             float rc = c >= 0.0f ? floorf(__fadd_rn(c, 0.5f)) : -floorf(__fadd_rn(-c, 0.5f));
             rc = fminf(fmaxf(rc, (float)-dmax), (float)dmax);
             out = (int)rc;
@@ -385,11 +392,11 @@ void launch_window(const float* dc, int Wc, int Hc, int W, int H, Intr K, const 
     count_launch();
 }
 
-void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, Intr K,
+void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, Intr K, const float m[3],
                 float drho, int dmax, int8_t* dI, cudaStream_t st)
 {
     dim3 b(32, 8);
-    dsn_kernel<<<grid2(W, H, b), b, 0, st>>>(dc, nc, Wc, Hc, W, H, K, drho, dmax, dI);
+    dsn_kernel<<<grid2(W, H, b), b, 0, st>>>(dc, nc, Wc, Hc, W, H, K, m[0], m[1], m[2], drho, dmax, dI);
     count_launch();
 }
 

@@ -102,7 +102,7 @@ _SIGS = {
                         C.c_float, _VP, _VP],
     "fassmvs_window": [_VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double,
                        C.c_double, C.c_int, C.c_int, _VP, _VP],
-    "fassmvs_dsn": [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, C.c_double, C.c_int,
+    "fassmvs_dsn": [_VP, _VP, _VP, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, C.c_double, C.c_int,
                     _VP, _VP],
     "fassmvs_estimate_batch": [_VP, _VP, C.c_int, _VP],
     "fassmvs_set_graph": [_VP, C.c_int],
@@ -117,6 +117,9 @@ _SIGS = {
     "fassmvs_server_poll": [_VP, _VP, C.c_int, _VP, C.c_int],
     "fassmvs_server_get_stats": [_VP, _VP],
     "fassmvs_server_last_error": [_VP],
+    "fassmvs_plane_bounds": [_VP, C.c_int, C.c_int, _VP, C.c_double, C.c_double, _VP, _VP],
+    "fassmvs_cross_ratio_planes": [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
+                                   _VP, _VP, _VP, _VP],
     "fassmvs_dog_filter": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP],
     "fassmvs_geo_filter": [_VP, _VP, _VP, _VP, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, C.c_double, C.c_int,
                            _VP, _VP],
@@ -192,8 +195,9 @@ class Context:
                     ctx=False)
 
     def close(self):
-        if self._h:
-            lib().fassmvs_destroy(self._h)
+        h = getattr(self, "_h", None)
+        if h:
+            lib().fassmvs_destroy(h)
             self._h = C.c_void_p()
 
     __del__ = close
@@ -433,12 +437,13 @@ class Context:
                                          int(D), _ptr(lo), _stream()))
         return lo
 
-    def dsn(self, dc, nc, W, H, K, drho, dmax=8):
+    def dsn(self, dc, nc, W, H, K, drho, dmax=8, n=(0.0, 0.0, -1.0)):
         import torch
         Hc, Wc = dc.shape
         out = torch.empty((8, H, W), dtype=torch.int8, device=dc.device)
         k_, kp = _dbl(K, 9)
-        self._check(lib().fassmvs_dsn(self._h, _ptr(dc), _ptr(nc), Wc, Hc, W, H, kp, drho, int(dmax),
+        n_, np_ = _dbl(n, 3)
+        self._check(lib().fassmvs_dsn(self._h, _ptr(dc), _ptr(nc), Wc, Hc, W, H, kp, np_, drho, int(dmax),
                                       _ptr(out), _stream()))
         return out
 
@@ -476,7 +481,7 @@ class Server:
             raise FassmvsError(st, (msg or b"").decode())
 
     def close(self):
-        if self._h:
+        if getattr(self, "_h", None):
             lib().fassmvs_server_destroy(self._h)
             self._h = C.c_void_p()
             self._keep.clear()
@@ -539,6 +544,40 @@ def wta_refine_noalloc(Sbar, D, K, n, rho0, drho, G, lo=None, depth=None, gwin=N
     if st != OK:
         raise FassmvsError(st, (lib().fassmvs_last_error(None) or b"").decode())
     return depth, gwin
+
+
+def plane_bounds(K, W, H, n, d_min, d_max):
+    """(delta_min, delta_max) of planes with normal n enclosing the reference
+    frustum between depths d_min and d_max (host computation, no device)."""
+    k_, kp = _dbl(K, 9)
+    n_, np_ = _dbl(n, 3)
+    lo, hi = C.c_double(), C.c_double()
+    st = lib().fassmvs_plane_bounds(kp, int(W), int(H), np_, float(d_min), float(d_max), C.byref(lo), C.byref(hi))
+    if st != OK:
+        raise FassmvsError(st, (lib().fassmvs_last_error(None) or b"").decode())
+    return lo.value, hi.value
+
+
+def cross_ratio_planes(K, W, H, R, t, n, delta_min, delta_max, max_planes=4096):
+    """Alg. 2 plane distances (far to near), the index of camera k, and the
+    uniform inverse-distance Planes the estimate takes (host computation, no
+    device).  R: (n, 3, 3), t: (n, 3), reference -> camera."""
+    R = np.ascontiguousarray(np.asarray(R, np.float64).reshape(-1, 9))
+    t = np.ascontiguousarray(np.asarray(t, np.float64).reshape(-1, 3))
+    if R.shape[0] != t.shape[0]:
+        raise ValueError("R and t disagree on the camera count")
+    k_, kp = _dbl(K, 9)
+    n_, np_ = _dbl(n, 3)
+    out = np.zeros(max_planes, np.float64)
+    cnt, cam = C.c_int(), C.c_int(-1)
+    uni = Planes()
+    st = lib().fassmvs_cross_ratio_planes(kp, int(W), int(H), R.shape[0], R.ctypes.data_as(C.c_void_p),
+                                          t.ctypes.data_as(C.c_void_p), np_, float(delta_min), float(delta_max),
+                                          int(max_planes), out.ctypes.data_as(C.c_void_p), C.byref(cnt),
+                                          C.byref(cam), C.byref(uni))
+    if st != OK:
+        raise FassmvsError(st, (lib().fassmvs_last_error(None) or b"").decode())
+    return out[:cnt.value].copy(), cam.value, uni
 
 
 def planes_of(scene):
