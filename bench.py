@@ -46,13 +46,15 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--form", default="frame", choices=["frame", "batch", "serve", "ablation", "filters", "slanted"],
+    p.add_argument("--form", default="frame", choices=["frame", "batch", "serve", "ablation", "filters", "slanted",
+                                                          "sweeps"],
                    help="frame: the 1080p per-frame workload (default line); batch: the mixed "
                         "16-frame batch, batched form against one estimate per frame; serve: two 30 fps "
                         "streams through the server against one estimate per keyframe; ablation: "
                         "8 / 4 paths x plane-wise / surface-normal / path-gradient SGM at 1600x1200; filters: "
                         "the DoG and geometric post-filters on 1920x1080 maps; slanted: fronto against "
-                        "ground-parallel sweeps of the 1080p frame, uniform and cross-ratio plane sets")
+                        "ground-parallel sweeps of the 1080p frame, uniform and cross-ratio plane sets; sweeps: "
+                        "pyramid height n = 1..5 and bundle size 3 / 5 / 7 (Tabs. pyrLvls-runtime, bundlesize)")
     return p.parse_args()
 
 
@@ -717,6 +719,98 @@ def run_slanted(a):
     return 0
 
 
+# ---------------------------------------------------------------- pyramid height / bundle size sweeps
+PAPER_PYR_MS = {"planes_1600x1200": [2365, 1315, 386, 220, 187], "city_1798x1200": [613, 431, 225, 196, 192]}
+PAPER_PYR_PLANES = {"planes_1600x1200": [256, 256, 128, 64, 32], "city_1798x1200": [128, 64, 32, 16, 8]}
+PAPER_BUNDLE_DMS = {"planes_1600x1200": {5: 271, 7: 302}, "city_1798x1200": {5: 360, 7: 410}}
+
+
+def _sweep_frame(name, seed, n_side):
+    from paper_2112_00821_b300 import synth
+    if name == "planes_1600x1200":
+        # wide baselines, so that the finest list is ~570 planes as on the paper's object-scale data
+        return synth.make_frame("planes", seed, W=1600, H=1200, n_left=n_side, n_right=n_side, base_frac=0.12), \
+            (5.4, 31.5)
+    return synth.make_frame("city", seed, W=1798, H=1200, n_left=n_side, n_right=n_side), (20.0, 300.0)
+
+
+def run_sweeps(a):
+    """Run-time (and accuracy against the rendered ground truth) of the whole
+    estimate against the pyramid height n = 1..5 with |Omega| = 3 images, and
+    against the bundle size |Omega| = 3 / 5 / 7 at n = 3 (planes) or n = 2
+    (city), as in Tabs. pyrLvls-runtime and bundlesize: fronto sweep, planes
+    from the cross-ratio list, at most 256 planes at the top level, NCC 5x5,
+    plane-wise SGM, phi1 = 100 with the adaptive phi2, 128-plane windows."""
+    import numpy as np
+    import torch
+    from paper_2112_00821_b300 import fassmvs, metrics
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    n_fronto = np.array([0.0, 0.0, -1.0])
+
+    def timed(sc, levels, drange):
+        H, W = sc.ref.shape
+        lo, hi = fassmvs.plane_bounds(sc.K, W, H, n_fronto, *drange)
+        _, cam, uni = fassmvs.cross_ratio_planes(sc.K, W, H, sc.R, sc.t, n_fronto, lo, hi)
+        G0, drho = uni.G0, uni.drho
+        step = 1 << (levels - 1)
+        if (G0 - 1) // step + 1 > 256:                      # the top-level cap
+            G0 = 255 * step + 1
+            drho = (1.0 / lo - 1.0 / hi) / (G0 - 1)
+        p = fassmvs.Planes()
+        p.n = (ctypes.c_double * 3)(*n_fronto)
+        p.rho_far, p.drho, p.G0 = 1.0 / hi, drho, G0
+        cfg = fassmvs.default_config(levels=levels, D=[128] * levels, paths=8, variant=0, p1=100, p2=0,
+                                     adaptive_p2=1, cost=1)
+        ctx = fassmvs.Context(cfg)
+        ctx.set_cameras(sc.K, sc.R, sc.t, sc.side)
+        ref = torch.from_numpy(sc.ref).cuda()
+        nbrs = [torch.from_numpy(x).cuda() for x in sc.nbrs]
+        for _ in range(max(a.warmup, 3)):
+            ctx.estimate(ref, nbrs, p)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(a.steps):
+            d, _, _ = ctx.estimate(ref, nbrs, p)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.steps
+        d = d.cpu().numpy()
+        ctx.close()
+        rep = metrics.depth_report(d, sc.depth_gt)
+        return {"ms_per_depth_map": round(ms, 3), "finest_planes": int(G0), "top_planes": (G0 - 1) // step + 1,
+                "views": len(sc.nbrs) + 1, **{k: round(v, 5) for k, v in rep.items()}}
+
+    pyramid, bundle = [], []
+    for name in ("planes_1600x1200", "city_1798x1200"):
+        sc, drange = _sweep_frame(name, a.seed, 1)
+        for levels in range(1, 6):
+            r = timed(sc, levels, drange)
+            r.update(scene=name, levels=levels, paper_ms=PAPER_PYR_MS[name][levels - 1],
+                     paper_top_planes=PAPER_PYR_PLANES[name][levels - 1])
+            pyramid.append(r)
+        n_b = 3 if name.startswith("planes") else 2
+        base_ms = None
+        for n_side in (1, 2, 3):
+            scb = sc if n_side == 1 else _sweep_frame(name, a.seed, n_side)[0]
+            r = timed(scb, n_b, drange)
+            base_ms = r["ms_per_depth_map"] if n_side == 1 else base_ms
+            r.update(scene=name, levels=n_b, delta_ms_vs_3=round(r["ms_per_depth_map"] - base_ms, 3),
+                     paper_delta_ms=PAPER_BUNDLE_DMS[name].get(2 * n_side + 1))
+            bundle.append(r)
+    if rank == 0:
+        print(json.dumps({"form": "sweeps", "metric": "ms per depth map (whole estimate)", "unit": "ms",
+                          "higher_is_better": False, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+                          "dtype": "u16", "data": "synthetic",
+                          "config": {"cost": "ncc 5x5", "sgm": "plane-wise, 8 paths", "p1": 100, "window": 128,
+                                     "top_level_plane_cap": 256, "planes": "cross-ratio list, fronto",
+                                     "paper_hardware": "Titan X (context only)"},
+                          "pyramid_height": pyramid, "bundle_size": bundle}), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -731,6 +825,8 @@ def main():
         return run_filters(a)
     if a.form == "slanted":
         return run_slanted(a)
+    if a.form == "sweeps":
+        return run_sweeps(a)
     return run_ours(a)
 
 

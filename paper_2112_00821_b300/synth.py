@@ -492,8 +492,9 @@ WORKLOADS = {
 }
 
 
-def make_frame(kind, seed, W=None, H=None, G0=None, n_left=None, n_right=None, want_gt=True):
-    """Build one reference frame of the given scene kind."""
+def make_frame(kind, seed, W=None, H=None, G0=None, n_left=None, n_right=None, want_gt=True, base_frac=None):
+    """Build one reference frame of the given scene kind (base_frac: the
+    camera spacing as a fraction of the mean scene depth, "planes" only)."""
     if kind == "tiny":
         W = W or 160
         H = H or 120
@@ -516,7 +517,7 @@ def make_frame(kind, seed, W=None, H=None, G0=None, n_left=None, n_right=None, w
         n_planes = int(g.integers(8, 21))
         zmin, zmax = 6.0, 30.0
         quads = _random_plane_quads(seed, f, n_planes, zmin, zmax, W, H)
-        base = 0.03 * 0.5 * (zmin + zmax)
+        base = (0.03 if base_frac is None else base_frac) * 0.5 * (zmin + zmax)
         c, tg, s = _bundle(n_left or 2, n_right or 2, base, 0.5 * (zmin + zmax), seed)
         sc = make_scene(quads, W, H, f, c, tg, s, G0 or 512, 0.9 * zmin, 1.05 * zmax, seed,
                         noise_sigma=2.0, want_gt=want_gt, meta={"n_planes": n_planes})
