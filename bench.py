@@ -777,11 +777,20 @@ def run_sweeps(a):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / a.steps
+        # stage split from a separate profiled pass (the timers add events)
+        ctx.profile(True)
+        for _ in range(a.steps):
+            ctx.estimate(ref, nbrs, p)
+        torch.cuda.synchronize()
+        st = ctx.profile_read()
+        ctx.profile(False)
         d = d.cpu().numpy()
         ctx.close()
         rep = metrics.depth_report(d, sc.depth_gt)
         return {"ms_per_depth_map": round(ms, 3), "finest_planes": int(G0), "top_planes": (G0 - 1) // step + 1,
-                "views": len(sc.nbrs) + 1, **{k: round(v, 5) for k, v in rep.items()}}
+                "views": len(sc.nbrs) + 1,
+                "stage_ms": {k: round(v[0] / a.steps, 3) for k, v in st.items() if v[1]},
+                **{k: round(v, 5) for k, v in rep.items()}}
 
     pyramid, bundle = [], []
     for name in ("planes_1600x1200", "city_1798x1200"):
