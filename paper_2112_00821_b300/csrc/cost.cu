@@ -50,6 +50,7 @@ struct SmemCost {
         } ncc;
     };
     int32_t lo[PH][PW];
+    int32_t rlo[PH], rhi[PH];            // per pixel row: planes its windows need, [rlo, rhi)
     int glo, ghi;
 };
 
@@ -223,6 +224,22 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             sm.ncc.refs[r][c] = make_int2(sa, 25 * saa - sa * sa);
         }
     }
+    // per pixel row, the planes its windows need; empty sample buffers, so
+    // that a row no warp sampled yet holds finite values
+    for (int r = tid; r < PH; r += THREADS) {
+        int l = a.G, h = 0;
+        for (int c = 0; c < PW; ++c) {
+            const int v = sm.lo[r][c];
+            if (v != (1 << 30)) {
+                l = min(l, v);
+                h = max(h, v + a.D);
+            }
+        }
+        sm.rlo[r] = l;
+        sm.rhi[r] = h;
+    }
+    for (int i = tid; i < 2 * SH * SW; i += THREADS) (&sm.pair[0][0][0])[i] = 0u;
+    for (int i = tid; i < 2 * PH * 2; i += THREADS) (&sm.okm[0][0][0])[i] = 0u;
     __syncthreads();
     // planes of this tile (guarded against an out-of-range window map), split
     // into nz consecutive chunks
@@ -238,15 +255,42 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     const int rs = (SH * warp) / NWARP, re = (SH * (warp + 1)) / NWARP;
     const int X0 = min(max(tx0 - 4 + lane, 0), W - 1);
     const int X1 = min(max(tx0 + 28 + lane, 0), W - 1);
+    // Windows differ across the tile (a per-pixel range of D planes), so a
+    // warp skips a plane its rows do not need.  Sample row j feeds the census
+    // of pixel rows j - 6 .. j (NCC: j - 5 .. j - 1, a subset) and the centre
+    // bit of pixel row j - 3; the census chunk needs the planes of its own
+    // pixels.  Only work is skipped, never a barrier, and the flags are
+    // uniform across the warp.  A skipped sample row keeps an older plane's
+    // values: it can only feed pixels whose windows exclude this plane, and
+    // their results are not stored.
+    int splo = a.G, sphi = 0;
+    for (int r = max(rs - 6, 0); r <= min(re - 1, PH - 1); ++r) {
+        splo = min(splo, sm.rlo[r]);
+        sphi = max(sphi, sm.rhi[r]);
+    }
+    int cplo = a.G, cphi = 0;
+    if (cact) {
+        for (int r = 0; r < CH; ++r) {
+            const int v = sm.lo[pr0 + r][pc];
+            if (v != (1 << 30)) {
+                cplo = min(cplo, v);
+                cphi = max(cphi, v + a.D);
+            }
+        }
+    }
+    cplo = __reduce_min_sync(0xFFFFFFFFu, cplo);
+    cphi = __reduce_max_sync(0xFFFFFFFFu, cphi);
 
     int buf = 0;
     for (int g = glo; g < ghi; ++g) {
         uint32_t slr[CH];
 #pragma unroll
         for (int r = 0; r < CH; ++r) slr[r] = 0;
+        const bool do_sample = g >= splo && g < sphi;
+        const bool do_cost = cact && g >= cplo && g < cphi;
         for (int k = 0; k < a.V; ++k) {
             // ---------------------------------------------------------- sampling
-            {
+            if (do_sample) {
                 const float* h = a.htab + ((size_t)g * a.V + k) * 18;
                 const uint8_t* img = a.views.img[k];
                 const df h0 = load_df(h, 0), h1 = load_df(h, 1), h2 = load_df(h, 2);
@@ -311,7 +355,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             __syncthreads();
             // ---------------------------------------------------------- NCC 5x5
             if constexpr (NCC) {
-                if (cact) {
+                if (do_cost) {
                     // window of output row r: sample rows pr0 + r + 1 .. + 5,
                     // columns pc + 2 .. pc + 6; row sums slide down the column
                     const uint32_t* bp = &sm.pair[buf][pr0 + 1][pc + 2];
@@ -361,7 +405,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 }
             } else
             // ---------------------------------------------------------- census
-            if (cact) {
+            if (do_cost) {
                 const uint32_t* base = &sm.pair[buf][pr0][pc];
                 __half2 cen[CH];
                 __half2 acc[CH][4];
@@ -407,7 +451,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             buf ^= 1;
         }
         // -------------------------------------------------------------- store
-        if (cact && tx0 + pc < W) {
+        if (do_cost && tx0 + pc < W) {
 #pragma unroll
             for (int r = 0; r < CH; ++r) {
                 const int py = ty0 + pr0 + r;
