@@ -40,6 +40,9 @@ constexpr int MAGIC_BITS = 0x4B400000;
 constexpr uint32_t LAYOUT_MASK = 0x03FF03FFu;
 
 struct SmemCost {
+    uint64_t mbar[2];                    // staging: completion of the tensor copy into slot 0 / 1
+    int stg_x0[2], stg_y0[2], stg_ok[2]; // staging: box origin in the view image, and whether it was issued
+    int stg_dead;                        // a staged copy missed its bound: no further staging in this CTA
     uint32_t pair[2][SH][SW];            // census: FP16x2 (V(x) - 2040, V(x+1) - 2040); NCC: u16x2 (V(x), V(x+1))
     uint32_t okm[2][PH][2];              // centre-in-image bit per pixel column
     union {
@@ -126,7 +129,7 @@ __device__ __forceinline__ int fix_pos(df N, df Dn, float r)
 // the position lies on the image grid
 template <bool WANT_OK>
 __device__ __forceinline__ int sample(const uint8_t* __restrict__ img, int W, int H, int pitch, df Nu,
-                                      df Nv, df Dn, bool& ok)
+                                      df Nv, df Dn, bool& ok, const uint8_t* stg, int sx0, int sy0)
 {
     int Pu = -PMAX, Pv = -PMAX;
     const bool front = Dn.hi > 0.0f || (Dn.hi == 0.0f && Dn.lo > 0.0f);
@@ -140,9 +143,18 @@ __device__ __forceinline__ int sample(const uint8_t* __restrict__ img, int W, in
     const int cu = min(max(Pu, 0), wmax), cv = min(max(Pv, 0), hmax);
     const int iu = min(cu >> 8, W - 2), iv = min(cv >> 8, H - 2);
     const int A = cu - 256 * iu, B = cv - 256 * iv;
-    const uint8_t* r0 = img + (size_t)iv * pitch + iu;
-    const int i00 = __ldg(r0), i01 = __ldg(r0 + 1);
-    const int i10 = __ldg(r0 + pitch), i11 = __ldg(r0 + pitch + 1);
+    int i00, i01, i10, i11;
+    const int ru = iu - sx0, rv = iv - sy0;
+    if (stg && (unsigned)ru <= (unsigned)(kStageBX - 2) && (unsigned)rv <= (unsigned)(kStageBY - 2)) {
+        // the 2x2 taps from the staged box of the view image
+        const uint8_t* r0 = stg + rv * kStageBX + ru;
+        i00 = r0[0]; i01 = r0[1];
+        i10 = r0[kStageBX]; i11 = r0[kStageBX + 1];
+    } else {
+        const uint8_t* r0 = img + (size_t)iv * pitch + iu;
+        i00 = __ldg(r0); i01 = __ldg(r0 + 1);
+        i10 = __ldg(r0 + pitch); i11 = __ldg(r0 + pitch + 1);
+    }
     const int top = (i00 << 8) + A * (i01 - i00);
     const int bot = (i10 << 8) + A * (i11 - i10);
     return ((top << 8) + B * (bot - top) + 2048) >> 12;     // [0, 4080]
@@ -176,11 +188,118 @@ __device__ __forceinline__ uint4 to_layout(uint64_t c)
 __device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
 __device__ __forceinline__ uint32_t as_u32(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
+// ---------------------------------------------------------------- staging
+// For each (plane, view) pair one elected thread copies a kStageBX x kStageBY
+// box of the view image that holds the warped sample tile into shared memory
+// with a TMA tensor copy, one pair ahead of the sampling (two slots, the same
+// parity as the sample-tile double buffer, so the loop's one barrier orders
+// every reuse).  Samples whose 2x2 taps lie outside the box read global memory
+// as before, so results never depend on the box.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void stage_init(SmemCost& sm)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&sm.mbar[i])), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sm.stg_dead = 0;
+        sm.stg_ok[0] = sm.stg_ok[1] = 0;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void stage_issue(uint64_t* mbar, uint8_t* dst, const void* tmap, int x0, int y0)
+{
+    uint64_t state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state)
+                 : "r"(smem_u32(mbar)), "r"(kStageBX * kStageBY)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)tmap), "r"(x0), "r"(y0), "r"(smem_u32(mbar))
+        : "memory");
+    (void)state;
+}
+
+// waits for the phase of the given parity, at most ~2^31 clocks (about a
+// second); false when the bound is reached
+__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
+    }
+}
+
+// warp 0: the box for pair (g, k) into `slot`.  Lanes 0-3 warp the four
+// corners of the (clamped) sample tile in FP32 (the box gets two pixels of
+// margin, more than the FP32 error of a corner); all four must lie in front of
+// the view.  The box origin's x is a multiple of 16 (TMA alignment).
+__device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint8_t* stg, int tx0, int ty0, int g,
+                                           int k, int slot, int lane)
+{
+    float u = 0.0f, v = 0.0f;
+    bool front = true;
+    if (lane < 4) {
+        const float* h = a.htab + ((size_t)g * a.V + k) * 18;
+        float hh[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hh[i] = __ldg(h + i) + __ldg(h + 9 + i);
+        const float x = (float)((lane & 1) ? min(max(tx0 + 59, 0), a.W - 1) : min(max(tx0 - 4, 0), a.W - 1));
+        const float y = (float)((lane & 2) ? min(max(ty0 + 54, 0), a.H - 1) : min(max(ty0 - 3, 0), a.H - 1));
+        const float nu = hh[0] * x + hh[1] * y + hh[2];
+        const float nv = hh[3] * x + hh[4] * y + hh[5];
+        const float dn = hh[6] * x + hh[7] * y + hh[8];
+        front = dn > 0.0f;
+        if (front) {
+            u = nu / dn;
+            v = nv / dn;
+        }
+    }
+    const bool all_front = __all_sync(0xFFFFFFFFu, front);
+    float umin = lane < 4 ? u : 3.0e38f, umax = lane < 4 ? u : -3.0e38f;
+    float vmin = lane < 4 ? v : 3.0e38f, vmax = lane < 4 ? v : -3.0e38f;
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        umin = fminf(umin, __shfl_xor_sync(0xFFFFFFFFu, umin, o));
+        umax = fmaxf(umax, __shfl_xor_sync(0xFFFFFFFFu, umax, o));
+        vmin = fminf(vmin, __shfl_xor_sync(0xFFFFFFFFu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
+    }
+    if (lane == 0) {
+        int ok = 0, x0 = 0, y0 = 0;
+        if (all_front && !sm.stg_dead) {
+            const float wm = (float)(a.W - 1), hm = (float)(a.H - 1);
+            const float ulo = fminf(fmaxf(umin, 0.0f), wm), uhi = fminf(fmaxf(umax, 0.0f), wm);
+            const float vlo = fminf(fmaxf(vmin, 0.0f), hm), vhi = fminf(fmaxf(vmax, 0.0f), hm);
+            x0 = max((int)floorf(ulo) - 2, 0) & ~15;
+            y0 = max((int)floorf(vlo) - 2, 0);
+            ok = (int)floorf(uhi) + 3 <= x0 + kStageBX - 1 && (int)floorf(vhi) + 3 <= y0 + kStageBY - 1;
+        }
+        sm.stg_x0[slot] = x0;
+        sm.stg_y0[slot] = y0;
+        sm.stg_ok[slot] = ok;
+        if (ok)
+            stage_issue(&sm.mbar[slot], stg + slot * kStageBX * kStageBY,
+                        static_cast<const char*>(a.tmaps) + (size_t)k * 128, x0, y0);
+    }
+}
+
 // One tile (bx, by) of one frame, plane chunk bz of nz, with the census (NCC
 // false) or NCC 5x5 cost.  Called by the single-frame grid kernel and by the
 // multi-frame kernel.
 template <bool NCC>
-__device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int bz, int nz, SmemCost& sm)
+__device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int bz, int nz, SmemCost& sm,
+                                          uint8_t* stg, uint32_t& phase)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tx0 = bx * PW, ty0 = by * PH;
@@ -200,6 +319,8 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         }
         if constexpr (!NCC) sm.refl[r][c] = to_layout(in ? a.cref[(size_t)py * W + px] : 0ull);
     }
+    // the window map and the tile's plane range are read below by every thread
+    __syncthreads();
     if constexpr (NCC) {
         // reference values on the sample grid (clamp-to-edge), then each pixel's
         // 5x5 window sums
@@ -240,12 +361,24 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     }
     for (int i = tid; i < 2 * SH * SW; i += THREADS) (&sm.pair[0][0][0])[i] = 0u;
     for (int i = tid; i < 2 * PH * 2; i += THREADS) (&sm.okm[0][0][0])[i] = 0u;
-    __syncthreads();
     // planes of this tile (guarded against an out-of-range window map), split
     // into nz consecutive chunks
     const int tlo = max(sm.glo, 0), thi = min(sm.ghi, a.G);
     const int chunk = (thi - tlo + nz - 1) / nz;
     const int glo = tlo + bz * chunk, ghi = min(thi, glo + chunk);
+    const bool use_stage = a.tmaps != nullptr && stg != nullptr;
+    if (use_stage && warp == 0 && ghi > glo) {
+        // the tensor maps were written to global memory by a host copy: the
+        // issuing thread orders the tensor-map proxy's reads after it
+        if (lane == 0)
+            for (int k = 0; k < a.V; ++k)
+                asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;"
+                             ::"l"((uint64_t)(static_cast<const char*>(a.tmaps) + (size_t)k * 128))
+                             : "memory");
+        __syncwarp();
+        stage_plan(a, sm, stg, tx0, ty0, glo, 0, 0, lane);
+    }
+    __syncthreads();
 
     // census role: columns cp*32 + lane, rows rc*13 .. rc*13 + 12
     const int pc = (warp & 1) * 32 + lane;
@@ -289,8 +422,27 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         const bool do_sample = g >= splo && g < sphi;
         const bool do_cost = cact && g >= cplo && g < cphi;
         for (int k = 0; k < a.V; ++k) {
+            // ---------------------------------------------------------- staging of the next pair
+            if (use_stage && warp == 0) {
+                const int gn = k + 1 < a.V ? g : g + 1, kn = k + 1 < a.V ? k + 1 : 0;
+                if (gn < ghi) stage_plan(a, sm, stg, tx0, ty0, gn, kn, buf ^ 1, lane);
+            }
+            const bool staged = use_stage && sm.stg_ok[buf];
+            // every issued copy completes before the barrier below: warp 0 waits
+            // for it even when it samples nothing of this plane (a plane in a gap
+            // between the tile's windows is needed by no warp)
+            bool ready = false;
+            if (staged && (do_sample || warp == 0)) {
+                ready = stage_wait(&sm.mbar[buf], (phase >> buf) & 1u);
+                if (!ready && lane == 0) {
+                    if (a.err) atomicOr(a.err, 1);
+                    sm.stg_dead = 1;
+                }
+            }
             // ---------------------------------------------------------- sampling
             if (do_sample) {
+                const uint8_t* sp = ready ? stg + buf * kStageBX * kStageBY : nullptr;
+                const int sx0 = ready ? sm.stg_x0[buf] : 0, sy0 = ready ? sm.stg_y0[buf] : 0;
                 const float* h = a.htab + ((size_t)g * a.V + k) * 18;
                 const uint8_t* img = a.views.img[k];
                 const df h0 = load_df(h, 0), h1 = load_df(h, 1), h2 = load_df(h, 2);
@@ -320,11 +472,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     const bool centre_row = j >= 3 && j < 3 + PH;
                     int i0, i1;
                     if (centre_row) {
-                        i0 = sample<true>(img, W, H, a.pitch, u0, v0, d0, ok0);
-                        i1 = sample<true>(img, W, H, a.pitch, u1, v1, d1, ok1);
+                        i0 = sample<true>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
+                        i1 = sample<true>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
                     } else {
-                        i0 = sample<false>(img, W, H, a.pitch, u0, v0, d0, ok0);
-                        i1 = sample<false>(img, W, H, a.pitch, u1, v1, d1, ok1);
+                        i0 = sample<false>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
+                        i1 = sample<false>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
                     }
                     if constexpr (NCC) {
                         int n0 = __shfl_sync(0xFFFFFFFFu, i0, (lane + 1) & 31);
@@ -352,6 +504,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     }
                 }
             }
+            if (staged) phase ^= 1u << buf;
             __syncthreads();
             // ---------------------------------------------------------- NCC 5x5
             if constexpr (NCC) {
@@ -475,7 +628,9 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
-    cost_tile<NCC>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm);
+    stage_init(sm);
+    uint32_t phase = 0;
+    cost_tile<NCC>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm, nullptr, phase);
 }
 
 // Batched form: work items (frame, tile x, tile y, chunk | chunks << 16) of
@@ -491,6 +646,11 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
     SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
     __shared__ CostArgs sa;
     __shared__ int s_item;
+    // the staging slots follow SmemCost, 128-byte aligned in the shared window
+    const uint32_t base = smem_u32(smraw);
+    uint8_t* stg = smraw + (((base + (uint32_t)sizeof(SmemCost) + 127u) & ~127u) - base);
+    stage_init(sm);
+    uint32_t phase = 0;
     int it = blockIdx.x;
     for (;;) {
         if (counter) {
@@ -506,7 +666,7 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
             for (int i = threadIdx.x; i < (int)(sizeof(CostArgs) / sizeof(int)); i += THREADS) dst[i] = src[i];
         }
         __syncthreads();
-        cost_tile<NCC>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm);
+        cost_tile<NCC>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm, stg, phase);
         __syncthreads();
         if (!counter) break;
     }
@@ -518,6 +678,8 @@ int cost_tiles_x(int W) { return (W + PW - 1) / PW; }
 int cost_tiles_y(int H) { return (H + PH - 1) / PH; }
 
 namespace {
+// SmemCost, alignment slack and the two staging slots
+constexpr int kBatchSmem = (int)sizeof(SmemCost) + 128 + 2 * kStageBX * kStageBY;
 // the shared-memory opt-in is a per-device function attribute
 void cost_smem_optin()
 {
@@ -528,8 +690,8 @@ void cost_smem_optin()
     const int smem = (int)sizeof(SmemCost);
     cudaFuncSetAttribute(cost_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(cost_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(cost_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(cost_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(cost_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    cudaFuncSetAttribute(cost_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
     done[dev] = true;
 }
 }  // namespace
@@ -554,9 +716,9 @@ void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int
     auto kern = ncc ? cost_batch_kernel<true> : cost_batch_kernel<false>;
     if (ctas > 0) {
         cudaMemsetAsync(counter, 0, sizeof(int), st);
-        kern<<<ctas, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, counter);
+        kern<<<ctas, THREADS, kBatchSmem, st>>>(args, items, n_items, counter);
     } else {
-        kern<<<n_items, THREADS, sizeof(SmemCost), st>>>(args, items, n_items, nullptr);
+        kern<<<n_items, THREADS, kBatchSmem, st>>>(args, items, n_items, nullptr);
     }
     count_launch();
 }

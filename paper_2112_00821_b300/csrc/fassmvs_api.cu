@@ -12,6 +12,8 @@
 #include <vector>
 #include <atomic>
 
+#include <cuda.h>   // CUtensorMap and its enums; the encoder is resolved through the runtime
+
 #include "../../include/fassmvs.h"
 #include "fm_internal.cuh"
 #include "host.h"
@@ -58,6 +60,41 @@ fassmvs_status cuda_check(fassmvs_ctx* c, cudaError_t e, const char* what)
         fassmvs_status _s = (expr);           \
         if (_s != FASSMVS_OK) return _s;      \
     } while (0)
+
+// cuTensorMapEncodeTiled, resolved once through the runtime (no link against
+// the driver library); null when the driver does not offer it
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// the tensor map of a uint8 view image for the cost kernel's staging box;
+// false when the image cannot be staged (row pitch or base not 16-byte
+// aligned, image smaller than the box, or no encoder)
+bool encode_view(void* out, const uint8_t* img, int W, int H, int pitch)
+{
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn || ((uintptr_t)img & 15) || (pitch & 15) || W < fm::kStageBX || H < fm::kStageBY) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+    const cuuint32_t box[2] = {(cuuint32_t)fm::kStageBX, (cuuint32_t)fm::kStageBY};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(img), dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // device scratch kept by name; grows within the budget
 fassmvs_status ensure(fassmvs_ctx* c, const char* name, size_t bytes, void** out)
@@ -346,6 +383,7 @@ fassmvs_status fassmvs_create(const fassmvs_config* cfg, int device, size_t mem_
     }
     s = set_device(c);
     if (s != FASSMVS_OK) { delete c; return s; }
+    encode_tiled();                        // resolved outside any stream capture
     *out = c;
     return FASSMVS_OK;
 }
@@ -654,7 +692,8 @@ fassmvs_status stage_prepare(fassmvs_ctx* c, const fassmvs_frame* frames, int n,
             items += (size_t)fm::cost_tiles_x(w) * fm::cost_tiles_y(h) *
                      ((fm::kMaxSlots + cmin - 1) / cmin + 1);
         }
-        need += 2 * 256 + n * sizeof(fm::CostArgs) + items * sizeof(int4);
+        need += 2 * 256 + n * sizeof(fm::CostArgs) + items * sizeof(int4) +
+                n * (256 + sizeof(CUtensorMap) * (size_t)fm::kMaxViews);
     }
     FM_TRY(stage_reserve(c, need));
     const int half = c->arena_half;
@@ -699,7 +738,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
         for (int l = 1; l < L; ++l) {
             F.Ws[l] = (F.Ws[l - 1] + 1) / 2;
             F.Hs[l] = (F.Hs[l - 1] + 1) / 2;
-            F.Ps[l] = F.Ws[l];
+            F.Ps[l] = (F.Ws[l] + 15) & ~15;    // 16-byte rows: the cost kernel stages them by TMA
         }
         if (pyrs) {
             // resident pyramids (serving form): level l of view k, pitch W_l
@@ -711,6 +750,11 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
     }
     void* counter;
     FM_TRY(ensure(c, "counter", 256, &counter));
+    // raised by the cost kernel when a staged copy misses its bound (read by fassmvs_sync)
+    void* cost_err;
+    const bool fresh_err = !c->bufs.count("cost_err");
+    FM_TRY(ensure(c, "cost_err", sizeof(int), &cost_err));
+    if (fresh_err) FM_TRY(cuda_check(c, cudaMemsetAsync(cost_err, 0, sizeof(int), st), "memset"));
     Stage sg = stage;
     std::vector<fm::SgmArgs> sargs;
     static thread_local fm::SgmBatch sb;       // 20 KB: kept off the stack
@@ -722,9 +766,9 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             FrameRun& F = fr[f];
             for (int l = 1; l < L; ++l) {
                 void* p;
-                FM_TRY(fscratch(c, f, ("pyr" + std::to_string(l)).c_str(), (size_t)(F.V + 1) * F.Ws[l] * F.Hs[l], &p));
+                FM_TRY(fscratch(c, f, ("pyr" + std::to_string(l)).c_str(), (size_t)(F.V + 1) * F.Ps[l] * F.Hs[l], &p));
                 for (int k = 0; k <= F.V; ++k) {
-                    uint8_t* o = (uint8_t*)p + (size_t)k * F.Ws[l] * F.Hs[l];
+                    uint8_t* o = (uint8_t*)p + (size_t)k * F.Ps[l] * F.Hs[l];
                     fm::launch_pyramid_down(F.img[l - 1][k], F.Ws[l - 1], F.Hs[l - 1], F.Ps[l - 1], o, F.Ps[l], st);
                     F.img[l][k] = o;
                 }
@@ -825,6 +869,17 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             a.bstride = 16 * np;
             a.bshift = 4;
             a.S = (uint16_t*)F.pSblk;
+            // tensor maps of the views for the kernel's staging (all views or none)
+            {
+                size_t at_tm;
+                unsigned char* tm = (unsigned char*)sg.take(sizeof(CUtensorMap) * (size_t)F.V, at_tm);
+                if (!tm) return fail(c, FASSMVS_EINTERNAL, "staging overflow");
+                bool all = true;
+                for (int k = 0; k < F.V && all; ++k)
+                    all = encode_view(tm + sizeof(CUtensorMap) * k, F.img[l][k + 1], F.w, F.h, F.Ps[l]);
+                a.tmaps = all ? (const void*)(sg.dev + at_tm) : nullptr;
+            }
+            a.err = (int*)cost_err;
             // aggregation arguments
             fm::SgmArgs& g = sargs[f];
             memset(&g, 0, sizeof g);
@@ -1157,14 +1212,20 @@ fassmvs_status fassmvs_sync(fassmvs_ctx* c)
     cudaError_t e = c->last ? cudaStreamSynchronize(c->last) : cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     FM_TRY(cuda_check(c, e, "device error"));
-    // deferred device-side flags: a connected-component walk that hit its cap
-    auto it = c->bufs.find("ccl_err");
-    if (it != c->bufs.end() && it->second.p) {
+    // deferred device-side flags: a connected-component walk that hit its cap;
+    // a staged copy of the cost kernel that missed its bound (the kernel then
+    // read global memory, so the volume is still right)
+    const std::pair<const char*, const char*> flags[2] = {
+        {"ccl_err", "a connected-component walk reached its bound (DoG filter)"},
+        {"cost_err", "a staged copy of the cost kernel did not complete within its bound"}};
+    for (const auto& fl : flags) {
+        auto it = c->bufs.find(fl.first);
+        if (it == c->bufs.end() || !it->second.p) continue;
         int flag = 0;
         FM_TRY(cuda_check(c, cudaMemcpy(&flag, it->second.p, sizeof flag, cudaMemcpyDeviceToHost), "flag read"));
         if (flag) {
             cudaMemset(it->second.p, 0, sizeof flag);
-            return fail(c, FASSMVS_EINTERNAL, "a connected-component walk reached its bound (DoG filter)");
+            return fail(c, FASSMVS_EINTERNAL, "%s", fl.second);
         }
     }
     return FASSMVS_OK;

@@ -59,7 +59,15 @@ struct CostArgs {
     size_t pstride, bstride;
     int bshift;
     uint16_t* S;
+    // staging of the neighbour images (may be null): V tensor maps (CUtensorMap,
+    // 128 B each, 64-byte aligned, global memory) of the views' uint8 images
+    // with a kStageBX x kStageBY box; and an error word raised when a staged
+    // copy does not complete within its bound (the kernel then reads global
+    // memory, so results are unchanged)
+    const void* tmaps;
+    int* err;
 };
+constexpr int kStageBX = 128, kStageBY = 80;
 void launch_cost(const CostArgs& a, cudaStream_t st);
 // multi-frame form: items[i] = (frame, tile x, tile y, chunk | chunks << 16);
 // ctas > 0 persistent CTAs pulling items from *counter, else one CTA per item;

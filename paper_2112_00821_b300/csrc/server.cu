@@ -464,8 +464,10 @@ fassmvs_status fassmvs_server_push_frame(fassmvs_server* s, int64_t id, const ui
     for (int l = 0; l < L; ++l) {
         if (l > 0) { w = (w + 1) / 2; h = (h + 1) / 2; }
         offs[l] = total;
-        F->pitch[l] = w;
-        total += align_up((size_t)w * h);
+        // levels >= 1 in 16-byte rows (the cost kernel stages them by TMA);
+        // level 0 keeps the pushed frame's layout
+        F->pitch[l] = l ? (w + 15) & ~15 : w;
+        total += align_up((size_t)F->pitch[l] * h);
     }
     {
         std::lock_guard<std::mutex> g(s->mu);
