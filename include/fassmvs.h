@@ -59,7 +59,8 @@ typedef enum {
     FASSMVS_EBUSY = 3,     /* no room for the request right now (serving) */
     FASSMVS_ETIMEOUT = 4,  /* a bounded device wait gave up */
     FASSMVS_ECUDA = 5,     /* a CUDA runtime call failed */
-    FASSMVS_EINTERNAL = 6  /* a kernel reported an inconsistency */
+    FASSMVS_EINTERNAL = 6, /* a kernel reported an inconsistency */
+    FASSMVS_ECANCELED = 7  /* a queued request was withdrawn (serving) */
 } fassmvs_status;
 
 /* Sweep planes (Sec. 2.2): normal n (unit, reference frame) and the inverse
@@ -183,9 +184,12 @@ FASSMVS_API fassmvs_status fassmvs_set_graph(fassmvs_ctx* ctx, int on);
  *                 CTA per work item (lets stream priorities act per CTA)
  *   sgm_parts     partial sums of the aggregation, 1, 2, 4 or 8 (at most the
  *                 path count), or 0: one per path.  With P parts, P
- *                 directions run concurrently in each of paths/P launches. */
+ *                 directions run concurrently in each of paths/P launches.
+ *   no_staging    0: the cost kernel stages the view images in shared memory
+ *                 by TMA where their rows are 16-byte aligned (default);
+ *                 1: it reads them from global memory. */
 typedef struct {
-    int32_t chunk_planes, ctas_per_sm, sgm_parts;
+    int32_t chunk_planes, ctas_per_sm, sgm_parts, no_staging;
 } fassmvs_tuning;
 
 /* fassmvs_autotune times a set of candidate tunings on the given batch
@@ -276,6 +280,12 @@ FASSMVS_API fassmvs_status fassmvs_server_release_frame(fassmvs_server* srv, int
  * size and intrinsics.  FASSMVS_ENOMEM when its scratch exceeds the whole
  * budget (it could never be admitted). */
 FASSMVS_API fassmvs_status fassmvs_server_submit(fassmvs_server* srv, const fassmvs_request* req);
+/* Withdraws a request that has not been launched yet (waiting for memory or
+ * for a lane): it completes at once with status FASSMVS_ECANCELED and its
+ * reserved memory and frame references are given back.  FASSMVS_EBUSY when it
+ * is already running (it then completes normally); FASSMVS_EINVAL when no
+ * queued or running request has that id. */
+FASSMVS_API fassmvs_status fassmvs_server_cancel(fassmvs_server* srv, int64_t id);
 /* Takes up to max completed results (waiting up to timeout_ms for the first);
  * *n_out receives the count.  Outputs of a completed request are in place. */
 FASSMVS_API fassmvs_status fassmvs_server_poll(fassmvs_server* srv, fassmvs_result* out, int max, int* n_out,

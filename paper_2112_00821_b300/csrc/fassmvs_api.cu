@@ -13,6 +13,7 @@
 #include <atomic>
 
 #include <cuda.h>   // CUtensorMap and its enums; the encoder is resolved through the runtime
+#include <nvtx3/nvToolsExt.h>   // header-only ranges for profilers (no-ops without one)
 
 #include "../../include/fassmvs.h"
 #include "fm_internal.cuh"
@@ -133,7 +134,18 @@ cudaEvent_t take_event(fassmvs_ctx* c)
     return e;
 }
 
-// Brackets the launches of one stage with events when profiling is on.
+// an NVTX range for a scope (levels of the coarse-to-fine loop)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Brackets the launches of one stage with events when profiling is on, and
+// with an NVTX range named after the stage (seen by nsys / ncu when attached).
+const char* const kStageNames[8] = {"fassmvs pyramid", "fassmvs census", "fassmvs cost",    "fassmvs sgm",
+                                    "fassmvs wta",     "fassmvs median", "fassmvs normals", "fassmvs window"};
 struct StageTimer {
     fassmvs_ctx* c;
     int stage;
@@ -141,10 +153,12 @@ struct StageTimer {
     cudaEvent_t a = nullptr;
     StageTimer(fassmvs_ctx* c_, int s, cudaStream_t st_) : c(c_), stage(s), st(st_)
     {
+        nvtxRangePushA(s >= 0 && s < 8 ? kStageNames[s] : "fassmvs stage");
         if (c && c->prof && (a = take_event(c))) cudaEventRecord(a, st);
     }
     ~StageTimer()
     {
+        nvtxRangePop();
         if (!a) return;
         cudaEvent_t b = take_event(c);
         if (!b) { c->pool.push_back(a); return; }
@@ -785,6 +799,9 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
         wave = nsm * (ctas_per_sm ? ctas_per_sm : 2);
     }
     for (int l = L - 1; l >= 0; --l) {
+        char level_name[32];
+        snprintf(level_name, sizeof level_name, "fassmvs level %d", l);
+        NvtxRange level_range(level_name);
         const size_t block0 = (sg.off + 255) & ~(size_t)255;
         size_t at_cargs, at_items;
         fm::CostArgs* cargs = (fm::CostArgs*)sg.take(sizeof(fm::CostArgs) * n, at_cargs);
@@ -877,7 +894,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 bool all = true;
                 for (int k = 0; k < F.V && all; ++k)
                     all = encode_view(tm + sizeof(CUtensorMap) * k, F.img[l][k + 1], F.w, F.h, F.Ps[l]);
-                a.tmaps = all ? (const void*)(sg.dev + at_tm) : nullptr;
+                a.tmaps = (all && !tn.no_staging) ? (const void*)(sg.dev + at_tm) : nullptr;
             }
             a.err = (int*)cost_err;
             // aggregation arguments
@@ -1027,6 +1044,7 @@ fassmvs_status check_tuning(fassmvs_ctx* c, const fassmvs_tuning& t)
         return fail(c, FASSMVS_EINVAL, "chunk_planes 0 (automatic) or 1..256, ctas_per_sm 0 (one CTA per item), 1 or 2");
     if (t.sgm_parts != 0 && t.sgm_parts != 1 && t.sgm_parts != 2 && t.sgm_parts != 4 && t.sgm_parts != 8)
         return fail(c, FASSMVS_EINVAL, "sgm_parts 0 (automatic), 1, 2, 4 or 8");
+    if (t.no_staging != 0 && t.no_staging != 1) return fail(c, FASSMVS_EINVAL, "no_staging 0 or 1");
     return FASSMVS_OK;
 }
 

@@ -633,6 +633,26 @@ fassmvs_status fassmvs_server_submit(fassmvs_server* s, const fassmvs_request* r
     return FASSMVS_OK;
 }
 
+fassmvs_status fassmvs_server_cancel(fassmvs_server* s, int64_t id)
+{
+    if (!s) return sfail(nullptr, FASSMVS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (std::deque<SReq*>* dq : {&s->pending, &s->admitted})
+        for (auto it = dq->begin(); it != dq->end(); ++it)
+            if ((*it)->r.id == id) {
+                SReq* q = *it;
+                dq->erase(it);
+                complete(s, q, FASSMVS_ECANCELED, 0);
+                s->cv.notify_all();        // memory may have come free for the next in line
+                s->cv_done.notify_all();
+                return FASSMVS_OK;
+            }
+    for (Lane& ln : s->lanes)
+        for (SReq* q : ln.batch)
+            if (q->r.id == id) return sfail(s, FASSMVS_EBUSY, "request %lld is running", (long long)id);
+    return sfail(s, FASSMVS_EINVAL, "no queued or running request %lld", (long long)id);
+}
+
 fassmvs_status fassmvs_server_poll(fassmvs_server* s, fassmvs_result* out, int max, int* n_out, int timeout_ms)
 {
     if (!s) return sfail(nullptr, FASSMVS_EINVAL, "server is NULL");

@@ -16,8 +16,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfassmvs.so")
 _lib = None
 
-OK, EINVAL, ENOMEM, EBUSY, ETIMEOUT, ECUDA, EINTERNAL = range(7)
-_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ETIMEOUT", 5: "ECUDA", 6: "EINTERNAL"}
+OK, EINVAL, ENOMEM, EBUSY, ETIMEOUT, ECUDA, EINTERNAL, ECANCELED = range(8)
+_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "EBUSY", 4: "ETIMEOUT", 5: "ECUDA", 6: "EINTERNAL",
+          7: "ECANCELED"}
 
 
 class FassmvsError(RuntimeError):
@@ -47,7 +48,8 @@ class Frame(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("chunk_planes", C.c_int32), ("ctas_per_sm", C.c_int32), ("sgm_parts", C.c_int32)]
+    _fields_ = [("chunk_planes", C.c_int32), ("ctas_per_sm", C.c_int32), ("sgm_parts", C.c_int32),
+                ("no_staging", C.c_int32)]
 
 
 class ServerConfig(C.Structure):
@@ -114,6 +116,7 @@ _SIGS = {
     "fassmvs_server_push_frame": [_VP, C.c_int64, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP],
     "fassmvs_server_release_frame": [_VP, C.c_int64],
     "fassmvs_server_submit": [_VP, _VP],
+    "fassmvs_server_cancel": [_VP, C.c_int64],
     "fassmvs_server_poll": [_VP, _VP, C.c_int, _VP, C.c_int],
     "fassmvs_server_get_stats": [_VP, _VP],
     "fassmvs_server_last_error": [_VP],
@@ -289,8 +292,8 @@ class Context:
     def set_graph(self, on=True):
         self._check(lib().fassmvs_set_graph(self._h, 1 if on else 0))
 
-    def set_tuning(self, chunk_planes=0, ctas_per_sm=2, sgm_parts=0):
-        t = Tuning(int(chunk_planes), int(ctas_per_sm), int(sgm_parts))
+    def set_tuning(self, chunk_planes=0, ctas_per_sm=2, sgm_parts=0, no_staging=0):
+        t = Tuning(int(chunk_planes), int(ctas_per_sm), int(sgm_parts), int(no_staging))
         self._check(lib().fassmvs_set_tuning(self._h, C.byref(t)))
 
     def autotune(self, items):
@@ -509,6 +512,15 @@ class Server:
                      normal.data_ptr(), conf.data_ptr(), 1 if host else 0)
         self._check(lib().fassmvs_server_submit(self._h, C.byref(rq)))
         self._keep[int(rid)] = (depth, normal, conf)
+
+    def cancel(self, rid):
+        """Withdraws a request not launched yet (its result comes with status
+        ECANCELED); False when it is already running (it completes normally)."""
+        st = lib().fassmvs_server_cancel(self._h, int(rid))
+        if st == EBUSY:
+            return False
+        self._check(st)
+        return True
 
     def poll(self, max_results=64, timeout_ms=0):
         """Completed results: list of dicts (id, status, batch_size, times in ns)."""

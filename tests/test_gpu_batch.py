@@ -162,3 +162,25 @@ def test_batch_rejects_bad_frames_by_index():
     ctx.estimate_batch(items)
     ctx.sync()
     ctx.close()
+
+
+@pytest.mark.parametrize("cost", [0, 1])
+def test_staging_of_the_view_images_changes_no_result(cost):
+    """The cost kernel's TMA staging of the view images (levels whose rows
+    are 16-byte aligned: 640x480 at every level, 240x136 and 160x120 at the
+    finest) gives the volume of the global reads, bit for bit."""
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs, synth
+    scs = _frames() + [synth.make_frame("planes", 47, W=640, H=480, G0=128, n_left=2, n_right=2, want_gt=False)]
+    items = [_item(sc) for sc in scs]
+    cfg = fassmvs.default_config(levels=3, D=[32, 32, 32], paths=8, variant=2, p1=100 if cost else 24, p2=0,
+                                 adaptive_p2=1, cost=cost)
+    ctx = fassmvs.Context(cfg)
+    ctx.set_tuning(no_staging=0)
+    staged = ctx.estimate_batch(items)
+    ctx.sync()
+    ctx.set_tuning(no_staging=1)
+    plain = ctx.estimate_batch(items)
+    ctx.sync()
+    _same(staged, plain)
+    ctx.close()

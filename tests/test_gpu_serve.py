@@ -1,8 +1,8 @@
 """Serving form (fassmvs_server_*): continuous batching must not change any
 result, admission must keep the device memory within the budget, and the
 host-side failure modes (a request that can never fit, a request not admitted
-before its deadline, a frame that does not fit, an unknown frame) must be
-reported as statuses without disturbing the other requests."""
+before its deadline, a cancelled request, a frame that does not fit, an unknown
+frame) must be reported as statuses without disturbing the other requests."""
 import numpy as np
 import pytest
 
@@ -195,4 +195,44 @@ def test_unknown_frames_are_rejected(streams):
     assert ei.value.status == fassmvs.EINVAL and "not resident" in str(ei.value)
     with pytest.raises(fassmvs.FassmvsError):
         srv.release_frame(s.fid(9))
+    srv.close()
+
+
+def test_cancelled_request_completes_at_once_and_the_others_are_unchanged():
+    import time
+    from paper_2112_00821_b300 import fassmvs, serve
+    s = serve.make_streams(sizes=((1920, 1080),), n_frames=5, seed=5, device="cuda")[0]
+    r, idx, _ = s.reqs[0]
+    cfg = fassmvs.default_config(levels=3, D=[256, 256, 256], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1)
+    srv = fassmvs.Server(cfg, fassmvs.server_config(lanes=1, max_batch=1, mem_budget=40 << 30))
+    _push(srv, s, sorted(idx + [r]))
+    outs = {q: _outs(s) for q in (1, 2, 3)}
+    srv.submit(1, s.fid(r), [s.fid(k) for k in idx], serve._planes(256), *outs[1])
+    t0 = time.monotonic()
+    while srv.stats()["batches"] < 1 and time.monotonic() - t0 < 30:
+        time.sleep(0.0005)
+    for q in (2, 3):
+        srv.submit(q, s.fid(r), [s.fid(k) for k in idx], serve._planes(256), *outs[q])
+    assert srv.cancel(2) is True
+    try:
+        running = srv.cancel(1)                 # the blocker is on the device: it cannot be withdrawn
+        assert running is False
+    except fassmvs.FassmvsError as e:           # unless it already finished
+        assert e.status == fassmvs.EINVAL
+    with pytest.raises(fassmvs.FassmvsError) as ei:
+        srv.cancel(99)
+    assert ei.value.status == fassmvs.EINVAL
+    got = {}
+    t0 = time.monotonic()
+    while len(got) < 3 and time.monotonic() - t0 < 60:
+        for x in srv.poll(4, 1000):
+            got[x["id"]] = x
+    assert got[2]["status"] == fassmvs.ECANCELED and got[2]["batch_size"] == 0
+    assert got[2]["t_done_ns"] < got[1]["t_done_ns"]
+    assert got[1]["status"] == fassmvs.OK and got[3]["status"] == fassmvs.OK
+    torch.cuda.synchronize()
+    for x, y in zip(outs[1], outs[3]):
+        assert torch.equal(x, y)
+    st = srv.stats()
+    assert st["completed"] == 2 and st["failed"] == 1 and st["queued"] == 0
     srv.close()
