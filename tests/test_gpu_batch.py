@@ -184,3 +184,23 @@ def test_staging_of_the_view_images_changes_no_result(cost):
     ctx.sync()
     _same(staged, plain)
     ctx.close()
+
+
+def test_staging_changes_no_result_at_full_size():
+    """The benchmark's frame and configuration (1920x1080, 5 views, 256
+    planes, 4 levels, path-gradient SGM): staged and global reads agree bit
+    for bit; the unstaged volume itself is checked against the oracle on
+    sampled voxels at this size in test_gpu_parity.py."""
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs, synth
+    sc, base = synth.workload("fhd_1920x1080_g256_l4", 0, want_gt=False)
+    items = [_item(sc)]
+    ctx = fassmvs.Context(fassmvs.default_config(**base))
+    ctx.set_tuning(no_staging=0)
+    staged = ctx.estimate_batch(items)
+    ctx.sync()
+    ctx.set_tuning(no_staging=1)
+    plain = ctx.estimate_batch(items)
+    ctx.sync()
+    _same(staged, plain)
+    ctx.close()
