@@ -24,6 +24,8 @@
 // its sign and its >= 1 test, so the census comparisons are exact.
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "fm_internal.cuh"
 
 namespace fm {
@@ -127,7 +129,7 @@ __device__ __forceinline__ int fix_pos(df N, df Dn, float r)
 
 // one warped sample: its value V = 16 x grey level in [0, 4080] and whether
 // the position lies on the image grid
-template <bool WANT_OK>
+template <bool WANT_OK, bool STAGED>
 __device__ __forceinline__ int sample(const uint8_t* __restrict__ img, int W, int H, int pitch, df Nu,
                                       df Nv, df Dn, bool& ok, const uint8_t* stg, int sx0, int sy0)
 {
@@ -144,13 +146,18 @@ __device__ __forceinline__ int sample(const uint8_t* __restrict__ img, int W, in
     const int iu = min(cu >> 8, W - 2), iv = min(cv >> 8, H - 2);
     const int A = cu - 256 * iu, B = cv - 256 * iv;
     int i00, i01, i10, i11;
-    const int ru = iu - sx0, rv = iv - sy0;
-    if (stg && (unsigned)ru <= (unsigned)(kStageBX - 2) && (unsigned)rv <= (unsigned)(kStageBY - 2)) {
-        // the 2x2 taps from the staged box of the view image
-        const uint8_t* r0 = stg + rv * kStageBX + ru;
-        i00 = r0[0]; i01 = r0[1];
-        i10 = r0[kStageBX]; i11 = r0[kStageBX + 1];
-    } else {
+    bool in_box = false;
+    if constexpr (STAGED) {
+        const int ru = iu - sx0, rv = iv - sy0;
+        in_box = (unsigned)ru <= (unsigned)(kStageBX - 2) && (unsigned)rv <= (unsigned)(kStageBY - 2);
+        if (in_box) {
+            // the 2x2 taps from the staged box of the view image
+            const uint8_t* r0 = stg + rv * kStageBX + ru;
+            i00 = r0[0]; i01 = r0[1];
+            i10 = r0[kStageBX]; i11 = r0[kStageBX + 1];
+        }
+    }
+    if (!in_box) {
         const uint8_t* r0 = img + (size_t)iv * pitch + iu;
         i00 = __ldg(r0); i01 = __ldg(r0 + 1);
         i10 = __ldg(r0 + pitch); i11 = __ldg(r0 + pitch + 1);
@@ -459,6 +466,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 df d1 = to_grid(df_add(df_mul_int(h6, fx1), by_d));
                 const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
                 uint32_t(*prow)[SW] = sm.pair[buf];
+                // the row loop in two variants, chosen once per (plane, view):
+                // taps from the staged box (global memory outside it), or from
+                // global memory only
+                auto rows = [&](auto staged_tag) {
+                constexpr bool ST = decltype(staged_tag)::value;
 #pragma unroll 2
                 for (int jj = 0; jj < 8; ++jj) {
                     const int j = rs + jj;
@@ -472,11 +484,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     const bool centre_row = j >= 3 && j < 3 + PH;
                     int i0, i1;
                     if (centre_row) {
-                        i0 = sample<true>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
-                        i1 = sample<true>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
+                        i0 = sample<true, ST>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
+                        i1 = sample<true, ST>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
                     } else {
-                        i0 = sample<false>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
-                        i1 = sample<false>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
+                        i0 = sample<false, ST>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
+                        i1 = sample<false, ST>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
                     }
                     if constexpr (NCC) {
                         int n0 = __shfl_sync(0xFFFFFFFFu, i0, (lane + 1) & 31);
@@ -503,6 +515,9 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                         }
                     }
                 }
+                };
+                if (sp) rows(std::true_type{});
+                else rows(std::false_type{});
             }
             if (staged) phase ^= 1u << buf;
             __syncthreads();
