@@ -293,6 +293,13 @@ FASSMVS_API fassmvs_status fassmvs_server_poll(fassmvs_server* srv, fassmvs_resu
 FASSMVS_API fassmvs_status fassmvs_server_get_stats(fassmvs_server* srv, fassmvs_server_stats* stats);
 FASSMVS_API const char* fassmvs_server_last_error(const fassmvs_server* srv);
 
+/* Test hook for failure detection, no fault involved.  mode 1: the cost
+ * kernel plans its staging boxes but issues no copies and bounds its waits at
+ * about a millisecond, so every staged wait gives up.  The kernel then reads
+ * global memory, so results are unchanged, and the next fassmvs_sync reports
+ * FASSMVS_ETIMEOUT.  mode 0: off (default). */
+FASSMVS_API fassmvs_status fassmvs_debug_inject(fassmvs_ctx* ctx, int mode);
+
 /* ---- plane selection (Sec. 2.2.2, Alg. 2; host-side, no device work) ------- */
 
 /* Distances of the bounding planes n^T X + delta = 0 (n unit, reference

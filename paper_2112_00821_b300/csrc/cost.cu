@@ -230,9 +230,9 @@ __device__ __forceinline__ void stage_issue(uint64_t* mbar, uint8_t* dst, const 
     (void)state;
 }
 
-// waits for the phase of the given parity, at most ~2^31 clocks (about a
-// second); false when the bound is reached
-__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity)
+// waits for the phase of the given parity, at most `bound` clocks (2^31,
+// about a second; 2^21 under the test hook); false when the bound is reached
+__device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity, long long bound)
 {
     const long long t0 = clock64();
     for (;;) {
@@ -243,7 +243,7 @@ __device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity)
             : "r"(smem_u32(mbar)), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > bound) return false;
     }
 }
 
@@ -295,7 +295,7 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
         sm.stg_x0[slot] = x0;
         sm.stg_y0[slot] = y0;
         sm.stg_ok[slot] = ok;
-        if (ok)
+        if (ok && !a.stage_test)
             stage_issue(&sm.mbar[slot], stg + slot * kStageBX * kStageBY,
                         static_cast<const char*>(a.tmaps) + (size_t)k * 128, x0, y0);
     }
@@ -440,7 +440,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             // between the tile's windows is needed by no warp)
             bool ready = false;
             if (staged && (do_sample || warp == 0)) {
-                ready = stage_wait(&sm.mbar[buf], (phase >> buf) & 1u);
+                ready = stage_wait(&sm.mbar[buf], (phase >> buf) & 1u, a.stage_test ? (1LL << 21) : (1LL << 31));
                 if (!ready && lane == 0) {
                     if (a.err) atomicOr(a.err, 1);
                     sm.stg_dead = 1;

@@ -897,6 +897,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 a.tmaps = (all && !tn.no_staging) ? (const void*)(sg.dev + at_tm) : nullptr;
             }
             a.err = (int*)cost_err;
+            a.stage_test = c->inject == 1;
             // aggregation arguments
             fm::SgmArgs& g = sargs[f];
             memset(&g, 0, sizeof g);
@@ -1233,17 +1234,24 @@ fassmvs_status fassmvs_sync(fassmvs_ctx* c)
     // deferred device-side flags: a connected-component walk that hit its cap;
     // a staged copy of the cost kernel that missed its bound (the kernel then
     // read global memory, so the volume is still right)
-    const std::pair<const char*, const char*> flags[2] = {
-        {"ccl_err", "a connected-component walk reached its bound (DoG filter)"},
-        {"cost_err", "a staged copy of the cost kernel did not complete within its bound"}};
-    for (const auto& fl : flags) {
-        auto it = c->bufs.find(fl.first);
+    struct Flag {
+        const char* buf;
+        fassmvs_status status;
+        const char* msg;
+    };
+    const Flag flags[2] = {
+        {"ccl_err", FASSMVS_EINTERNAL, "a connected-component walk reached its bound (DoG filter)"},
+        {"cost_err", FASSMVS_ETIMEOUT,
+         "a staged copy of the cost kernel did not complete within its bound (the volume was read from global "
+         "memory)"}};
+    for (const Flag& fl : flags) {
+        auto it = c->bufs.find(fl.buf);
         if (it == c->bufs.end() || !it->second.p) continue;
         int flag = 0;
         FM_TRY(cuda_check(c, cudaMemcpy(&flag, it->second.p, sizeof flag, cudaMemcpyDeviceToHost), "flag read"));
         if (flag) {
             cudaMemset(it->second.p, 0, sizeof flag);
-            return fail(c, FASSMVS_EINTERNAL, "%s", fl.second);
+            return fail(c, fl.status, "%s", fl.msg);
         }
     }
     return FASSMVS_OK;
@@ -1300,6 +1308,14 @@ V3 corner_ray(const double Ki[9], int W, int H, int c)
     return mat_vec(Ki, v3((c & 1) ? W - 1 : 0, (c & 2) ? H - 1 : 0, 1.0));
 }
 }  // namespace
+
+fassmvs_status fassmvs_debug_inject(fassmvs_ctx* c, int mode)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (mode != 0 && mode != 1) return fail(c, FASSMVS_EINVAL, "mode 0 (off) or 1 (staging waits give up)");
+    c->inject = mode;
+    return FASSMVS_OK;
+}
 
 fassmvs_status fassmvs_plane_bounds(const double K[9], int W, int H, const double n[3], double d_min, double d_max,
                                     double* delta_min, double* delta_max)

@@ -66,6 +66,9 @@ struct CostArgs {
     // memory, so results are unchanged)
     const void* tmaps;
     int* err;
+    // test hook: plan the staging boxes but issue no copies, with a wait
+    // bound of about a millisecond, so that every staged wait gives up
+    int stage_test;
 };
 constexpr int kStageBX = 128, kStageBY = 80;
 void launch_cost(const CostArgs& a, cudaStream_t st);

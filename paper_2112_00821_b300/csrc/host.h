@@ -29,6 +29,7 @@ struct fassmvs_ctx {
     cudaStream_t last = nullptr;
     // stage timers
     bool prof = false;
+    int inject = 0;                      // test hook (fassmvs_debug_inject)
     struct Rec { cudaEvent_t a, b; int stage; };
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> pending;

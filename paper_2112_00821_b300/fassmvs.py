@@ -120,6 +120,7 @@ _SIGS = {
     "fassmvs_server_poll": [_VP, _VP, C.c_int, _VP, C.c_int],
     "fassmvs_server_get_stats": [_VP, _VP],
     "fassmvs_server_last_error": [_VP],
+    "fassmvs_debug_inject": [_VP, C.c_int],
     "fassmvs_plane_bounds": [_VP, C.c_int, C.c_int, _VP, C.c_double, C.c_double, _VP, _VP],
     "fassmvs_cross_ratio_planes": [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
                                    _VP, _VP, _VP, _VP],
@@ -334,6 +335,11 @@ class Context:
         return hits
 
     STAGES = ("pyramid", "census", "cost", "sgm", "wta", "median", "normals", "window")
+
+    def debug_inject(self, mode):
+        """Test hook: 1 makes the cost kernel's staged waits give up (results
+        unchanged, the next sync reports ETIMEOUT); 0 turns it off."""
+        self._check(lib().fassmvs_debug_inject(self._h, int(mode)))
 
     def profile(self, on=True):
         self._check(lib().fassmvs_profile_enable(self._h, 1 if on else 0))

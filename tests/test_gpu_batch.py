@@ -204,3 +204,27 @@ def test_staging_changes_no_result_at_full_size():
     ctx.sync()
     _same(staged, plain)
     ctx.close()
+
+
+def test_a_staged_wait_that_gives_up_is_reported_and_changes_no_result():
+    """Failure detection without a fault: under the test hook the cost
+    kernel's staging waits find nothing to wait for and give up at their
+    bound; the kernel reads global memory instead, the outputs are those of
+    a normal run, sync reports ETIMEOUT once, and the context stays usable."""
+    _need_gpu()
+    from paper_2112_00821_b300 import fassmvs
+    items = [_item(sc) for sc in _frames()]
+    ctx = fassmvs.Context(_cfg(2))
+    ref = ctx.estimate_batch(items)
+    ctx.sync()
+    ctx.debug_inject(1)
+    got = ctx.estimate_batch(items)
+    with pytest.raises(fassmvs.FassmvsError) as ei:
+        ctx.sync()
+    assert ei.value.status == fassmvs.ETIMEOUT and "staged copy" in str(ei.value)
+    _same(got, ref)
+    ctx.debug_inject(0)
+    again = ctx.estimate_batch(items)
+    ctx.sync()
+    _same(again, ref)
+    ctx.close()
