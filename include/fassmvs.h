@@ -242,7 +242,24 @@ typedef struct {
     float* normal;            /* pinned host memory when host_outputs (copied */
     float* conf;              /* back by the server), else device memory */
     int32_t host_outputs;
+    /* post-filters of Sec. 2.6, run on the device before the outputs are
+     * returned (0: none); FASSMVS_POST_* flags: */
+    int32_t postfilter;
+    int32_t geo_n;            /* FASSMVS_POST_GEO: 1..4 earlier requests ... */
+    int64_t geo_ids[4];       /* ... whose estimated depth maps were kept */
+    double geo_eta_r;         /* reprojection threshold in pixels (Alg. 4) */
+    int32_t geo_eta_h;        /* minimum number of consistent maps (Alg. 4) */
 } fassmvs_request;
+
+/* DoG texture mask (Alg. 3) of the reference image applied to the outputs */
+#define FASSMVS_POST_DOG 1
+/* geometric consistency (Alg. 4) against the kept depth maps geo_ids (same
+ * size and intrinsics; their reference poses give the relative poses) */
+#define FASSMVS_POST_GEO 2
+/* keep this request's estimated depth map (before any post-filter) on the
+ * device, inside the memory budget, for later requests' consistency checks,
+ * until fassmvs_server_release_depth */
+#define FASSMVS_POST_KEEP 4
 
 typedef struct {
     int64_t id;
@@ -286,6 +303,9 @@ FASSMVS_API fassmvs_status fassmvs_server_submit(fassmvs_server* srv, const fass
  * is already running (it then completes normally); FASSMVS_EINVAL when no
  * queued or running request has that id. */
 FASSMVS_API fassmvs_status fassmvs_server_cancel(fassmvs_server* srv, int64_t id);
+/* Gives back the depth map kept for request id (FASSMVS_POST_KEEP) once no
+ * queued or running request names it; FASSMVS_EINVAL when none is kept. */
+FASSMVS_API fassmvs_status fassmvs_server_release_depth(fassmvs_server* srv, int64_t id);
 /* Takes up to max completed results (waiting up to timeout_ms for the first);
  * *n_out receives the count.  Outputs of a completed request are in place. */
 FASSMVS_API fassmvs_status fassmvs_server_poll(fassmvs_server* srv, fassmvs_result* out, int max, int* n_out,

@@ -674,7 +674,11 @@ fassmvs_status ctx_reserve(fassmvs_ctx* c, size_t bytes)
     FM_TRY(stage_reserve(c, bytes));
     FM_TRY(ensure(c, "stageA", bytes, &p));
     FM_TRY(ensure(c, "stageB", bytes, &p));
-    return ensure(c, "counter", 256, &p);
+    FM_TRY(ensure(c, "counter", 256, &p));
+    const bool fresh = !c->bufs.count("cost_err");
+    FM_TRY(ensure(c, "cost_err", sizeof(int), &p));
+    if (fresh) FM_TRY(cuda_check(c, cudaMemset(p, 0, sizeof(int)), "memset"));
+    return FASSMVS_OK;
 }
 
 // scratch buffer `name` of frame f of the batch
@@ -1091,6 +1095,25 @@ fassmvs_status estimate_batch_impl(fassmvs_ctx* c, const fassmvs_frame* frames, 
     return cuda_check(c, cudaGraphLaunch(ex, st), "graph launch");
 }
 
+// Alg. 3 weights: a 7-tap Gaussian of sigma 1.4, quantised to integers that
+// sum to 256 (the rounding remainder goes to the centre tap)
+fm::DogWeights dog_weights()
+{
+    fm::DogWeights w;
+    double g[7], sum = 0.0;
+    for (int i = 0; i < 7; ++i) {
+        g[i] = std::exp(-(double)((i - 3) * (i - 3)) / (2.0 * 1.4 * 1.4));
+        sum += g[i];
+    }
+    int tot = 0;
+    for (int i = 0; i < 7; ++i) {
+        w.w[i] = (int32_t)std::floor(256.0 * g[i] / sum + 0.5);
+        tot += w.w[i];
+    }
+    w.w[3] += 256 - tot;
+    return w;
+}
+
 }  // namespace fmh
 
 extern "C" {
@@ -1257,24 +1280,6 @@ fassmvs_status fassmvs_sync(fassmvs_ctx* c)
     return FASSMVS_OK;
 }
 
-// Alg. 3 weights: a 7-tap Gaussian of sigma 1.4, quantised to integers that
-// sum to 256 (the rounding remainder goes to the centre tap)
-static fm::DogWeights dog_weights()
-{
-    fm::DogWeights w;
-    double g[7], sum = 0.0;
-    for (int i = 0; i < 7; ++i) {
-        g[i] = std::exp(-(double)((i - 3) * (i - 3)) / (2.0 * 1.4 * 1.4));
-        sum += g[i];
-    }
-    int tot = 0;
-    for (int i = 0; i < 7; ++i) {
-        w.w[i] = (int32_t)std::floor(256.0 * g[i] / sum + 0.5);
-        tot += w.w[i];
-    }
-    w.w[3] += 256 - tot;
-    return w;
-}
 
 // ---------------------------------------------------------------- plane selection
 // Sec. 2.2.2 and Alg. 2: host-side FP64 geometry, no device work.  Planes are

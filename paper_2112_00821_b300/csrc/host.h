@@ -88,6 +88,9 @@ int sgm_parts(const fassmvs_tuning& t, int paths);
 fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cudaStream_t st,
                          const fassmvs_tuning& tn, const Stage& stage, const fm::PyrSet* pyrs);
 
+// Alg. 3 smoothing weights (a 7-tap Gaussian quantised to a unit sum of 256)
+fm::DogWeights dog_weights();
+
 // Largest size over the levels of every per-frame scratch buffer run_batch
 // asks for (by name) when the pyramids are resident.
 void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0, int parts,

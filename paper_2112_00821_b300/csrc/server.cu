@@ -55,6 +55,22 @@ struct SReq {
     size_t bytes = 0, off = SIZE_MAX;
     float *d_depth = nullptr, *d_normal = nullptr, *d_conf = nullptr;
     int64_t t_submit = 0, t_admit = 0, t_launch = 0, deadline = 0;
+    // post-filters: the kept-depth block (its own arena block, handed to the
+    // server's kept maps when the request succeeds), the consistency partners
+    // and the relative poses reference -> partner
+    size_t keep_bytes = 0, keep_off = SIZE_MAX;
+    std::vector<int64_t> geo;
+    std::vector<size_t> geo_off;               // arena offsets of the partners' maps (fixed while named)
+    std::vector<double> geo_R, geo_t;
+};
+
+// a depth map kept for later consistency checks (FASSMVS_POST_KEEP)
+struct Kept {
+    size_t off = SIZE_MAX;
+    int W = 0, H = 0;
+    double K[9], R[9], t[3];   // intrinsics and world -> camera pose of its reference
+    int refs = 0;              // queued or running requests that name it
+    bool released = false;
 };
 
 struct Lane {
@@ -65,6 +81,7 @@ struct Lane {
     bool busy = false;
     std::vector<SReq*> batch;
     int64_t t_launch = 0;
+    int* h_err = nullptr;                      // pinned: per batch entry, the DoG filter's error word
 };
 
 }  // namespace
@@ -81,6 +98,7 @@ struct fassmvs_server {
     std::deque<SReq*> pending;    // submitted, waiting for memory
     std::deque<SReq*> admitted;   // scratch reserved, waiting for a lane
     std::deque<fassmvs_result> results;
+    std::unordered_map<int64_t, Kept> kept;
     std::vector<Lane> lanes;
     // uploads: host rows -> pinned slot (CPU copy) -> device on copy_st, then
     // the pyramid on pyr_st (highest priority); copies never queue behind
@@ -152,6 +170,28 @@ void complete(fassmvs_server* s, SReq* q, fassmvs_status st, int batch_size)
     r.t_done_ns = now_ns();
     s->results.push_back(r);
     if (q->off != SIZE_MAX) s->arena.release(q->off);
+    if (q->keep_off != SIZE_MAX) {
+        if (st == FASSMVS_OK) {
+            Kept& k = s->kept[q->r.id];
+            const SFrame* F0 = q->frames[0];
+            k.off = q->keep_off;
+            k.W = F0->W;
+            k.H = F0->H;
+            memcpy(k.K, F0->K, sizeof k.K);
+            memcpy(k.R, F0->R, sizeof k.R);
+            memcpy(k.t, F0->t, sizeof k.t);
+        } else {
+            s->arena.release(q->keep_off);
+        }
+    }
+    for (int64_t id : q->geo) {
+        auto it = s->kept.find(id);
+        if (it == s->kept.end()) continue;
+        if (--it->second.refs == 0 && it->second.released) {
+            s->arena.release(it->second.off);
+            s->kept.erase(it);
+        }
+    }
     for (SFrame* F : q->frames) {
         if (--F->refs == 0 && F->released) {
             s->arena.release(F->off);
@@ -204,6 +244,44 @@ fassmvs_status launch_batch(fassmvs_server* s, Lane& ln, const fassmvs_tuning& t
     ln.ctx->scratch_fn = nullptr;
     ln.ctx->scratch_user = nullptr;
     if (st != FASSMVS_OK) return sfail(s, st, "%s", ln.ctx->err.c_str());
+    // post-filters (Sec. 2.6) on the outputs, before they are returned
+    for (int i = 0; i < n; ++i) {
+        SReq* q = ln.batch[i];
+        const int pf = q->r.postfilter;
+        ln.h_err[i] = 0;
+        if (!pf) continue;
+        const SFrame* F0 = q->frames[0];
+        const int W = F0->W, H = F0->H;
+        const size_t np = (size_t)W * H;
+        if (pf & FASSMVS_POST_KEEP)
+            cudaMemcpyAsync(s->arena.at(q->keep_off), q->d_depth, 4 * np, cudaMemcpyDeviceToDevice, ln.st);
+        if (pf & FASSMVS_POST_DOG) {
+            auto at = [&](const char* name) -> void* {
+                for (auto& kv : q->layout)
+                    if (kv.first == name) return s->arena.at(q->off + kv.second);
+                return nullptr;
+            };
+            int* err = (int*)at("dog:err");
+            cudaMemsetAsync(err, 0, sizeof(int), ln.st);
+            fm::launch_dog_mask(F0->lvl[0], W, H, F0->pitch[0], dog_weights(), (uint8_t*)at("dog:mask"),
+                                (uint8_t*)at("dog:tmp"), (int*)at("dog:parent"), (int*)at("dog:size"), err, ln.st);
+            fm::launch_apply_mask((const uint8_t*)at("dog:mask"), W, H, q->d_depth, q->d_normal, q->d_conf, ln.st);
+            cudaMemcpyAsync(&ln.h_err[i], err, sizeof(int), cudaMemcpyDeviceToHost, ln.st);
+        }
+        if (pf & FASSMVS_POST_GEO) {
+            fm::GeoArgs g;
+            memset(&g, 0, sizeof g);
+            g.W = W; g.H = H; g.n = (int)q->geo.size(); g.eta_h = q->r.geo_eta_h; g.eta_r = q->r.geo_eta_r;
+            g.fx = F0->K[0]; g.fy = F0->K[4]; g.cx = F0->K[2]; g.cy = F0->K[5];
+            for (int k = 0; k < g.n; ++k) {
+                g.dk[k] = (const float*)s->arena.at(q->geo_off[k]);
+                for (int j = 0; j < 9; ++j) g.R[k][j] = q->geo_R[9 * k + j];
+                for (int j = 0; j < 3; ++j) g.t[k][j] = q->geo_t[3 * k + j];
+            }
+            fm::launch_geo_filter(g, q->d_depth, q->d_normal, q->d_conf, nullptr, ln.st);
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return sfail(s, FASSMVS_ECUDA, "post-filter launch");
     for (int i = 0; i < n; ++i) {
         SReq* q = ln.batch[i];
         if (!q->r.host_outputs) continue;
@@ -228,7 +306,13 @@ void worker(fassmvs_server* s)
             if (q == cudaErrorNotReady) continue;
             const fassmvs_status st = q == cudaSuccess ? FASSMVS_OK : FASSMVS_ECUDA;
             if (st != FASSMVS_OK) s->err = std::string("batch: ") + cudaGetErrorString(q);
-            for (SReq* r : ln.batch) complete(s, r, st, (int)ln.batch.size());
+            for (size_t i = 0; i < ln.batch.size(); ++i) {
+                SReq* r = ln.batch[i];
+                // a union-find walk of the DoG filter that reached its bound
+                const bool dog_err = st == FASSMVS_OK && (r->r.postfilter & FASSMVS_POST_DOG) && ln.h_err[i];
+                if (dog_err) s->err = "request " + std::to_string((long long)r->r.id) + ": DoG filter walk bound";
+                complete(s, r, dog_err ? FASSMVS_EINTERNAL : st, (int)ln.batch.size());
+            }
             ln.batch.clear();
             ln.busy = false;
             s->cv_done.notify_all();
@@ -244,7 +328,16 @@ void worker(fassmvs_server* s)
                 s->cv_done.notify_all();
                 continue;
             }
-            const size_t off = s->arena.alloc(q->bytes);
+            size_t off = s->arena.alloc(q->bytes);
+            size_t koff = SIZE_MAX;
+            if (off != SIZE_MAX && q->keep_bytes) {
+                // the kept map outlives the request: from the top, like frames
+                koff = s->arena.alloc(q->keep_bytes, true);
+                if (koff == SIZE_MAX) {
+                    s->arena.release(off);
+                    off = SIZE_MAX;
+                }
+            }
             if (off == SIZE_MAX) {
                 // with nothing admitted or running, no completion can free
                 // memory for it (the resident frames it needs stay): refuse it
@@ -260,6 +353,7 @@ void worker(fassmvs_server* s)
                 continue;
             }
             q->off = off;
+            q->keep_off = koff;
             q->t_admit = t;
             if (q->r.host_outputs) {
                 for (auto& kv : q->layout) {
@@ -380,6 +474,9 @@ fassmvs_status fassmvs_server_create(const fassmvs_config* cfg, const fassmvs_se
         ln.st = ln.prio[0];
         if (st == FASSMVS_OK && cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) != cudaSuccess)
             st = sfail(s, FASSMVS_ECUDA, "event");
+        if (st == FASSMVS_OK &&
+            cudaHostAlloc((void**)&ln.h_err, sizeof(int) * fm::kSgmBatch, cudaHostAllocDefault) != cudaSuccess)
+            st = sfail(s, FASSMVS_ECUDA, "pinned error words");
         s->lanes.push_back(ln);
         if (st != FASSMVS_OK) return bail(st);
     }
@@ -423,6 +520,7 @@ void fassmvs_server_destroy(fassmvs_server* s)
             if (q) cudaStreamSynchronize(q);
         if (ln.ctx) fassmvs_destroy(ln.ctx);
         if (ln.done) cudaEventDestroy(ln.done);
+        if (ln.h_err) cudaFreeHost(ln.h_err);
         for (cudaStream_t q : ln.prio)
             if (q) cudaStreamDestroy(q);
     }
@@ -557,6 +655,11 @@ fassmvs_status fassmvs_server_submit(fassmvs_server* s, const fassmvs_request* r
             return sfail(s, FASSMVS_EINVAL, "request %lld: outputs must be %s memory", (long long)r->id,
                          r->host_outputs ? "pinned host" : "device");
     }
+    const int pf = r->postfilter;
+    if (pf & ~(FASSMVS_POST_DOG | FASSMVS_POST_GEO | FASSMVS_POST_KEEP))
+        return sfail(s, FASSMVS_EINVAL, "request %lld: unknown post-filter flags", (long long)r->id);
+    if ((pf & FASSMVS_POST_GEO) && (r->geo_n < 1 || r->geo_n > 4 || !(r->geo_eta_r > 0.0) || r->geo_eta_h < 0))
+        return sfail(s, FASSMVS_EINVAL, "request %lld: geo_n 1..4, geo_eta_r > 0, geo_eta_h >= 0", (long long)r->id);
     auto q = std::make_unique<SReq>();
     q->r = *r;
     q->nb.assign(r->nbrs, r->nbrs + r->n_nb);
@@ -601,6 +704,32 @@ fassmvs_status fassmvs_server_submit(fassmvs_server* s, const fassmvs_request* r
         }
         q->side.push_back(q->nb[k] < r->ref ? -1 : 1);
     }
+    // consistency partners: kept depth maps of the same size and intrinsics;
+    // X_k = R_k R_ref^T X_ref + (t_k - R_k R_ref^T t_ref) as for the views
+    if (pf & FASSMVS_POST_GEO) {
+        for (int i = 0; i < r->geo_n; ++i) {
+            auto it = s->kept.find(r->geo_ids[i]);
+            if (it == s->kept.end() || it->second.released)
+                return sfail(s, FASSMVS_EINVAL, "request %lld: no depth map of request %lld is kept", (long long)r->id,
+                             (long long)r->geo_ids[i]);
+            const Kept& k = it->second;
+            if (k.W != F0->W || k.H != F0->H || memcmp(k.K, F0->K, sizeof k.K) != 0)
+                return sfail(s, FASSMVS_EINVAL, "request %lld: kept map %lld differs in size or intrinsics",
+                             (long long)r->id, (long long)r->geo_ids[i]);
+            double Rk[9];
+            mat3_mul(k.R, RrT, Rk);
+            for (int j = 0; j < 9; ++j) q->geo_R.push_back(Rk[j]);
+            for (int a = 0; a < 3; ++a) {
+                double v = k.t[a];
+                for (int m = 0; m < 3; ++m) v -= Rk[3 * a + m] * F0->t[m];
+                q->geo_t.push_back(v);
+            }
+            q->geo.push_back(r->geo_ids[i]);
+            q->geo_off.push_back(k.off);
+        }
+    }
+    if ((pf & FASSMVS_POST_KEEP) && s->kept.count(r->id))
+        return sfail(s, FASSMVS_EINVAL, "request %lld: a depth map of that id is already kept", (long long)r->id);
     // scratch layout of the request
     std::vector<std::pair<std::string, size_t>> sizes;
     frame_scratch_layout(s->cfg, F0->W, F0->H, (int)q->nb.size(), pl.G0, sgm_parts(s->scfg.tuning, s->cfg.paths), sizes);
@@ -614,6 +743,15 @@ fassmvs_status fassmvs_server_submit(fassmvs_server* s, const fassmvs_request* r
         q->d_normal = r->normal;
         q->d_conf = r->conf;
     }
+    const size_t np0 = (size_t)F0->W * F0->H;
+    if (pf & FASSMVS_POST_DOG) {
+        sizes.push_back({"dog:mask", np0});
+        sizes.push_back({"dog:tmp", np0});
+        sizes.push_back({"dog:parent", 4 * np0});
+        sizes.push_back({"dog:size", 4 * np0});
+        sizes.push_back({"dog:err", sizeof(int)});
+    }
+    if (pf & FASSMVS_POST_KEEP) q->keep_bytes = 4 * np0;
     size_t off = 0;
     for (auto& kv : sizes) {
         q->layout.push_back({kv.first, off});
@@ -621,10 +759,11 @@ fassmvs_status fassmvs_server_submit(fassmvs_server* s, const fassmvs_request* r
         off += align_up(kv.second);
     }
     q->bytes = off;
-    if (q->bytes > s->arena.capacity())
+    if (q->bytes + align_up(q->keep_bytes) > s->arena.capacity())
         return sfail(s, FASSMVS_ENOMEM, "request %lld needs %zu bytes, more than the %zu-byte budget", (long long)r->id,
-                     q->bytes, s->arena.capacity());
+                     q->bytes + align_up(q->keep_bytes), s->arena.capacity());
     for (SFrame* F : q->frames) ++F->refs;
+    for (int64_t id : q->geo) ++s->kept[id].refs;
     q->t_submit = now_ns();
     q->deadline = s->scfg.deadline_ms ? q->t_submit + (int64_t)s->scfg.deadline_ms * 1000000 : 0;
     s->pending.push_back(q.release());
@@ -651,6 +790,23 @@ fassmvs_status fassmvs_server_cancel(fassmvs_server* s, int64_t id)
         for (SReq* q : ln.batch)
             if (q->r.id == id) return sfail(s, FASSMVS_EBUSY, "request %lld is running", (long long)id);
     return sfail(s, FASSMVS_EINVAL, "no queued or running request %lld", (long long)id);
+}
+
+fassmvs_status fassmvs_server_release_depth(fassmvs_server* s, int64_t id)
+{
+    if (!s) return sfail(nullptr, FASSMVS_EINVAL, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->kept.find(id);
+    if (it == s->kept.end() || it->second.released)
+        return sfail(s, FASSMVS_EINVAL, "no depth map of request %lld is kept", (long long)id);
+    if (it->second.refs == 0) {
+        s->arena.release(it->second.off);
+        s->kept.erase(it);
+        s->cv.notify_all();                    // memory may have come free for the next in line
+    } else {
+        it->second.released = true;
+    }
+    return FASSMVS_OK;
 }
 
 fassmvs_status fassmvs_server_poll(fassmvs_server* s, fassmvs_result* out, int max, int* n_out, int timeout_ms)

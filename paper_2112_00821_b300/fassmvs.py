@@ -58,10 +58,14 @@ class ServerConfig(C.Structure):
                 ("tuning_overlap", Tuning)]
 
 
+POST_DOG, POST_GEO, POST_KEEP = 1, 2, 4
+
+
 class Request(C.Structure):
     _fields_ = [("id", C.c_int64), ("ref", C.c_int64), ("nbrs", C.c_void_p), ("n_nb", C.c_int32),
                 ("planes", Planes), ("depth", C.c_void_p), ("normal", C.c_void_p), ("conf", C.c_void_p),
-                ("host_outputs", C.c_int32)]
+                ("host_outputs", C.c_int32), ("postfilter", C.c_int32), ("geo_n", C.c_int32),
+                ("geo_ids", C.c_int64 * 4), ("geo_eta_r", C.c_double), ("geo_eta_h", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -117,6 +121,7 @@ _SIGS = {
     "fassmvs_server_release_frame": [_VP, C.c_int64],
     "fassmvs_server_submit": [_VP, _VP],
     "fassmvs_server_cancel": [_VP, C.c_int64],
+    "fassmvs_server_release_depth": [_VP, C.c_int64],
     "fassmvs_server_poll": [_VP, _VP, C.c_int, _VP, C.c_int],
     "fassmvs_server_get_stats": [_VP, _VP],
     "fassmvs_server_last_error": [_VP],
@@ -510,14 +515,25 @@ class Server:
     def release_frame(self, fid):
         self._check(lib().fassmvs_server_release_frame(self._h, int(fid)))
 
-    def submit(self, rid, ref, nbrs, planes, depth, normal, conf):
-        """Outputs: pinned host tensors (copied back) or CUDA tensors."""
+    def submit(self, rid, ref, nbrs, planes, depth, normal, conf, postfilter=0, geo_ids=(), geo_eta_r=10.0,
+               geo_eta_h=3):
+        """Outputs: pinned host tensors (copied back) or CUDA tensors.
+        postfilter: POST_DOG | POST_GEO | POST_KEEP; geo_ids: earlier requests
+        with kept depth maps (POST_GEO)."""
         host = not depth.is_cuda
         nb = (C.c_int64 * len(nbrs))(*[int(x) for x in nbrs])
+        gi = list(geo_ids)
+        if len(gi) > 4:
+            raise ValueError("at most 4 consistency partners")
         rq = Request(int(rid), int(ref), C.cast(nb, C.c_void_p), len(nbrs), planes, depth.data_ptr(),
-                     normal.data_ptr(), conf.data_ptr(), 1 if host else 0)
+                     normal.data_ptr(), conf.data_ptr(), 1 if host else 0, int(postfilter), len(gi),
+                     (C.c_int64 * 4)(*(gi + [0] * (4 - len(gi)))), float(geo_eta_r), int(geo_eta_h))
         self._check(lib().fassmvs_server_submit(self._h, C.byref(rq)))
         self._keep[int(rid)] = (depth, normal, conf)
+
+    def release_depth(self, rid):
+        """Gives back the depth map kept for request rid (POST_KEEP)."""
+        self._check(lib().fassmvs_server_release_depth(self._h, int(rid)))
 
     def cancel(self, rid):
         """Withdraws a request not launched yet (its result comes with status

@@ -2,7 +2,8 @@
 result, admission must keep the device memory within the budget, and the
 host-side failure modes (a request that can never fit, a request not admitted
 before its deadline, a cancelled request, a frame that does not fit, an unknown
-frame) must be reported as statuses without disturbing the other requests."""
+frame) must be reported as statuses without disturbing the other requests.
+The post-filters of Sec. 2.6 run in the server equal the standalone ones."""
 import numpy as np
 import pytest
 
@@ -235,4 +236,85 @@ def test_cancelled_request_completes_at_once_and_the_others_are_unchanged():
         assert torch.equal(x, y)
     st = srv.stats()
     assert st["completed"] == 2 and st["failed"] == 1 and st["queued"] == 0
+    srv.close()
+
+
+def _rel_pose(Rr, tr, Rk, tk):
+    """Reference -> k from world -> camera poses, in the server's order of
+    operations (so that the FP64 consistency test sees identical inputs)."""
+    RrT = [[float(Rr[j][i]) for j in range(3)] for i in range(3)]
+    R = [[0.0] * 3 for _ in range(3)]
+    for i in range(3):
+        for j in range(3):
+            v = 0.0
+            for m in range(3):
+                v += float(Rk[i][m]) * RrT[m][j]
+            R[i][j] = v
+    t = []
+    for i in range(3):
+        v = float(tk[i])
+        for m in range(3):
+            v -= R[i][m] * float(tr[m])
+        t.append(v)
+    return np.array(R), np.array(t)
+
+
+def test_post_filters_in_the_server_equal_the_standalone_filters(streams):
+    """DoG mask (Alg. 3) and geometric consistency (Alg. 4) run by the server
+    on a request's outputs equal the standalone filters applied to the same
+    request served unfiltered, the partner being an earlier request's kept
+    depth map; kept maps are given back by release_depth."""
+    import time
+    from paper_2112_00821_b300 import fassmvs, serve
+    s = streams[0]
+    (r1, idx1, G1), (r2, idx2, G2) = s.reqs[0], s.reqs[1]
+    srv = fassmvs.Server(_cfg(), fassmvs.server_config(lanes=1, max_batch=1, mem_budget=2 << 30))
+    _push(srv, s, sorted(set(idx1 + idx2 + [r1, r2])))
+    flat = s.frames[r1].copy()
+    flat[40:120, 100:220] = 128                          # an untextured patch for the DoG mask
+    R1, t1 = s.poses[r1]
+    srv.push_frame(9001, flat, s.K, R1, t1)
+    o = {q: _outs(s) for q in (1, 2, 3, 4)}
+    got = {}
+
+    def run(q, ref, idx, G, **kw):
+        srv.submit(q, ref, [s.fid(k) for k in idx], serve._planes(G), *o[q], **kw)
+        t0 = time.monotonic()
+        while q not in got and time.monotonic() - t0 < 60:
+            for x in srv.poll(4, 1000):
+                got[x["id"]] = x
+        assert got[q]["status"] == fassmvs.OK, got[q]
+
+    run(1, 9001, idx1, G1, postfilter=fassmvs.POST_KEEP)
+    run(2, s.fid(r2), idx2, G2, postfilter=fassmvs.POST_KEEP)
+    run(3, 9001, idx1, G1, postfilter=fassmvs.POST_DOG)
+    run(4, s.fid(r2), idx2, G2, postfilter=fassmvs.POST_DOG | fassmvs.POST_GEO, geo_ids=[1], geo_eta_r=1.0,
+        geo_eta_h=1)
+    torch.cuda.synchronize()
+    ctx = fassmvs.Context(_cfg())
+    e3 = [x.clone() for x in o[1]]
+    mask = ctx.dog_filter(torch.from_numpy(flat).cuda(), *e3)
+    e4 = [x.clone() for x in o[2]]
+    ctx.dog_filter(torch.from_numpy(s.frames[r2]).cuda(), *e4)
+    R21, t21 = _rel_pose(*s.poses[r2], R1, t1)          # request 2's reference -> request 1's
+    hits = ctx.geo_filter(e4[0], s.K, [o[1][0]], R21[None], t21[None], normal=e4[1], conf=e4[2], eta_r=1.0,
+                          eta_h=1)
+    ctx.sync()
+    for x, y in zip(o[3], e3):
+        assert torch.equal(x, y)
+    for x, y in zip(o[4], e4):
+        assert torch.equal(x, y)
+    assert not mask[60:100, 120:200].any()                # the filters did act
+    assert (hits == 0).any() and (o[4][0] == 0).sum() > (o[2][0] == 0).sum()
+    ctx.close()
+    with pytest.raises(fassmvs.FassmvsError) as ei:      # only kept maps can be partners
+        srv.submit(5, s.fid(r2), [s.fid(k) for k in idx2], serve._planes(G2), *_outs(s),
+                   postfilter=fassmvs.POST_GEO, geo_ids=[3])
+    assert ei.value.status == fassmvs.EINVAL
+    before = srv.stats()["bytes_in_use"]
+    srv.release_depth(1)
+    srv.release_depth(2)
+    assert srv.stats()["bytes_in_use"] < before
+    with pytest.raises(fassmvs.FassmvsError):
+        srv.release_depth(1)
     srv.close()
