@@ -524,6 +524,10 @@ def run_serve_form(a):
                    "all_available": serve.run_server(streams, cfg, scfg, fps=None)},
         "plain_per_frame": {"paced_30fps": serve.run_plain(streams, cfg, fps=30.0),
                             "all_available": serve.run_plain(streams, cfg, fps=None)},
+        # with the post-filters of Sec. 2.6: DoG mask, and geometric consistency
+        # against the last two completed keyframes of the stream (kept maps)
+        "server_postfilter": {"paced_30fps": serve.run_server(streams, cfg, scfg, fps=30.0, post=2),
+                              "all_available": serve.run_server(streams, cfg, scfg, fps=None, post=2)},
     }
     ck = clocks.stop()
     if rank != 0:
@@ -538,6 +542,8 @@ def run_serve_form(a):
                    "levels": 4, "variant": "path-gradient", "paths": 8, "mem_budget_gb": 120,
                    "lanes": scfg.lanes, "max_batch": scfg.max_batch, "overlap_queue": scfg.overlap_queue,
                    "tuning": {"alone": [0, 2, 0], "next_to_running": [32, 0, 0]},
+                   "postfilter": "DoG mask + geometric consistency vs the last 2 completed keyframes of the "
+                                 "stream, eta_r 10 px, eta_h 1",
                    "render_s": round(t_render, 1)},
         "forms": res,
         "p99_plain_over_server": round(pp["latency_ms"]["p99"] / sp["latency_ms"]["p99"], 3),

@@ -97,14 +97,18 @@ def _pinned(shape):
     return torch.empty(shape, dtype=torch.float32, pin_memory=True)
 
 
-def run_server(streams, cfg, scfg, fps=30.0, keep=False, wait_s=300.0):
+def run_server(streams, cfg, scfg, fps=30.0, keep=False, wait_s=300.0, post=0, eta_r=10.0, eta_h=1):
     """Serves the streams through one fassmvs.Server.  fps=None: every frame
-    is available at once (throughput).  Returns a summary dict and, with keep,
-    the outputs per (stream, request).  Raises if a frame stays refused or
-    results stay out for longer than the bounds."""
+    is available at once (throughput).  post > 0: every keyframe also gets the
+    DoG mask and the geometric consistency check against the kept depth maps
+    of the last `post` completed keyframes of its stream (a sliding window;
+    older maps are given back).  Returns a summary dict and, with keep, the
+    outputs per (stream, request).  Raises if a frame stays refused or results
+    stay out for longer than the bounds."""
     srv = fassmvs.Server(cfg, scfg)
     lat, outs, pend = [], {}, {}
     last_use = [_last_use(s) for s in streams]
+    window = [[] for _ in streams]          # completed keyframes with kept depth maps, oldest first
     n_req = sum(len(s.reqs) for s in streams)
     t0 = time.monotonic_ns()
 
@@ -114,6 +118,11 @@ def run_server(streams, cfg, scfg, fps=30.0, keep=False, wait_s=300.0):
             if r["status"] != fassmvs.OK:
                 raise fassmvs.FassmvsError(r["status"], "request %d failed" % r["id"])
             lat.append((r["t_done_ns"] - t_ready) * 1e-9)
+            if post:
+                w = window[key[0]]
+                w.append(r["id"])
+                while len(w) > post:
+                    srv.release_depth(w.pop(0))
 
     rid = 0
     for t, si, i, ready in _events(streams, fps):
@@ -133,7 +142,12 @@ def run_server(streams, cfg, scfg, fps=30.0, keep=False, wait_s=300.0):
         for j in ready:
             r, idx, G0 = s.reqs[j]
             o = (_pinned((s.H, s.W)), _pinned((s.H, s.W, 3)), _pinned((s.H, s.W)))
-            srv.submit(rid, s.fid(r), [s.fid(k) for k in idx], _planes(G0), *o)
+            kw = {}
+            if post:
+                part = window[si][-post:]
+                kw = dict(postfilter=fassmvs.POST_KEEP | fassmvs.POST_DOG | (fassmvs.POST_GEO if part else 0),
+                          geo_ids=part, geo_eta_r=eta_r, geo_eta_h=min(eta_h, len(part)))
+            srv.submit(rid, s.fid(r), [s.fid(k) for k in idx], _planes(G0), *o, **kw)
             pend[rid] = ((si, j), t0 + int(t * 1e9))
             if keep:
                 outs[(si, j)] = o
