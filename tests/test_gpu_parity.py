@@ -304,3 +304,32 @@ def test_estimate_end_to_end(orc, variant, levels):
     valid = (np.linalg.norm(n_e, axis=-1) > 0) & (rel < 1e-4)
     assert np.median(_angle_deg(n[valid], n_e[valid])) <= 0.5
     assert np.mean(np.abs(conf - c_e)) < 2e-3
+
+
+def test_estimate_equals_the_stage_entry_points_at_full_size(ctx):
+    """The benchmark's frame at one level (1920x1080, 5 views, 256 planes,
+    path-gradient SGM with the adaptive P2): the estimate, i.e. the batched
+    cost kernel with TMA-staged view images, the 16-plane blocked volume and
+    its relayout, and the aggregation's partial sums, equals the chain of stage
+    entry points bit for bit.  Each stage entry point is checked against the
+    oracle above."""
+    import math
+    from paper_2112_00821_b300 import fassmvs, synth
+    sc, base = synth.workload("fhd_1920x1080_g256_l4", 0, want_gt=False)
+    c = fassmvs.Context(fassmvs.default_config(**dict(base, levels=1, D=[256])))
+    c.set_cameras(sc.K, sc.R, sc.t, sc.side)
+    ref = dev(sc.ref)
+    nbrs = [dev(x) for x in sc.nbrs]
+    d, n, conf = c.estimate(ref, nbrs, fassmvs.planes_of(sc))
+    nmax = max(sum(1 for s in sc.side if s < 0), sum(1 for s in sc.side if s > 0))
+    p1 = base["p1"] * nmax
+    lut = [min(65535, math.floor(p1 * (1.0 + 8.0 * math.exp(-i / 10.0)) + 0.5)) for i in range(256)]
+    S = c.cost_volume(ref, nbrs, sc.side, sc.K, sc.R, sc.t, sc.plane_n, sc.rho_far, sc.drho, 256)
+    Sb = c.sgm_aggregate(S, 256, p1, lut=lut, img=ref, paths=8, variant=2)
+    dr, _ = c.wta_refine(Sb, 256, sc.K, sc.plane_n, sc.rho_far, sc.drho, 256)
+    dm = c.median5(dr)
+    nn, _, cc = c.normals(dm, ref, sc.K, n_plane=sc.plane_n)
+    c.sync()
+    assert torch.equal(d, dm)
+    assert torch.equal(n, nn) and torch.equal(conf, cc)
+    c.close()
