@@ -13,8 +13,8 @@ step, in millions (Mpix*planes/s).
 
 Under torchrun (N > 1) every rank estimates its own frames (weak scaling, no
 data-path collective); rank 0 prints one JSON line.  `--impl reference` times
-the CPU oracle (the reference of this build) on the host cores on a bounded
-sample of the same workload.
+the CPU oracle (the reference arm) on the host cores on a bounded sample of
+the same workload.
 """
 from __future__ import annotations
 
@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -87,7 +88,8 @@ class Clocks:
     def __init__(self, gpu):
         self.gpu = gpu
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+        # the raw samples go to FASSMVS_CLOCKS_DIR (default: the temporary directory)
+        self.path = os.path.join(os.environ.get("FASSMVS_CLOCKS_DIR") or tempfile.gettempdir(),
                                  "clocks_rank%d.csv" % gpu)
 
     def start(self):

@@ -526,7 +526,7 @@ def test_fronto_plane_scene_recovers_plane_index(orc):
 
 def test_tiny_estimate_close_to_ground_truth(orc):
     # 64 planes span only ~7 px of disparity here (0.12 px per plane), so the
-    # error is judged in plane indices rather than in relative depth
+    # error is measured in plane indices rather than in relative depth
     from paper_2112_00821_b300 import synth
     sc, cfg = synth.workload("tiny_160x120_g64", 0)
     c = orc.make_config(levels=1, D=[64], p1=10, p2=120)
