@@ -320,6 +320,25 @@ FASSMVS_API const char* fassmvs_server_last_error(const fassmvs_server* srv);
  * FASSMVS_ETIMEOUT.  mode 0: off (default). */
 FASSMVS_API fassmvs_status fassmvs_debug_inject(fassmvs_ctx* ctx, int mode);
 
+/* Intermediates of one pyramid level of the next estimates (frame 0 of a
+ * batch), for parity tests and debugging.  fassmvs_debug_capture(ctx, level)
+ * selects the level (-1: off; while on, estimates run eagerly, never from a
+ * CUDA graph).  fassmvs_debug_dump copies one intermediate of the last
+ * capture into dst (device or host memory, cap bytes; dst NULL: only *bytes
+ * and dims) after waiting for the context's last stream; dims (may be NULL)
+ * receives W, H, D, Ds, G of the level.  what (layouts row-major): */
+#define FASSMVS_DUMP_COST 0       /* uint16 [H][W][Ds]: cost volume, slot s = plane lo_p + s */
+#define FASSMVS_DUMP_WINDOW 1     /* int32 [H][W]: window start lo_p (0 at the top level) */
+#define FASSMVS_DUMP_DSN 2        /* int8 [8][H][W]: surface-normal index jumps (0 unless sn) */
+#define FASSMVS_DUMP_AGG 3        /* uint16 [H][W][Ds]: aggregated costs, all paths summed */
+#define FASSMVS_DUMP_ARGMIN 4     /* int32 [H][W]: winning plane of the winner-takes-all */
+#define FASSMVS_DUMP_DEPTH_RAW 5  /* float [H][W]: refined depth before the median */
+#define FASSMVS_DUMP_DEPTH 6      /* float [H][W]: depth after the 5x5 median */
+#define FASSMVS_DUMP_NORMAL 7     /* float [H][W][3]: smoothed unit normals */
+FASSMVS_API fassmvs_status fassmvs_debug_capture(fassmvs_ctx* ctx, int level);
+FASSMVS_API fassmvs_status fassmvs_debug_dump(fassmvs_ctx* ctx, int level, int what, void* dst, size_t cap,
+                                              size_t* bytes, int32_t dims[5]);
+
 /* ---- plane selection (Sec. 2.2.2, Alg. 2; host-side, no device work) ------- */
 
 /* Distances of the bounding planes n^T X + delta = 0 (n unit, reference

@@ -958,6 +958,24 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 fm::launch_relayout16((const uint16_t*)fr[f].pSblk, (uint16_t*)fr[f].pS, (size_t)fr[f].w * fr[f].h,
                                       fr[f].Ds, st);
         }
+        // debug capture of frame 0 at the selected level: the cost volume,
+        // the window starts and the surface-normal jumps
+        const bool dbg = l == c->dbg_level;
+        if (dbg) {
+            const FrameRun& F = fr[0];
+            const size_t np = (size_t)F.w * F.h;
+            const int dims[5] = {F.w, F.h, F.D, F.Ds, F.Gl};
+            memcpy(c->dbg_dims, dims, sizeof dims);
+            void* p;
+            FM_TRY(ensure(c, "dbg:S", 2 * np * F.Ds, &p));
+            FM_TRY(cuda_check(c, cudaMemcpyAsync(p, F.pS, 2 * np * F.Ds, cudaMemcpyDeviceToDevice, st), "capture"));
+            FM_TRY(ensure(c, "dbg:lo", 4 * np, &p));
+            FM_TRY(cuda_check(c, F.plo ? cudaMemcpyAsync(p, F.plo, 4 * np, cudaMemcpyDeviceToDevice, st)
+                                       : cudaMemsetAsync(p, 0, 4 * np, st), "capture"));
+            FM_TRY(ensure(c, "dbg:dI", 8 * np, &p));
+            FM_TRY(cuda_check(c, F.pdI ? cudaMemcpyAsync(p, F.pdI, 8 * np, cudaMemcpyDeviceToDevice, st)
+                                       : cudaMemsetAsync(p, 0, 8 * np, st), "capture"));
+        }
         {
             StageTimer tm(c, FASSMVS_STAGE_SGM, st);
             // `parts` partial sums: launch g runs, for every part k, direction
@@ -997,6 +1015,15 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 }
             }
         }
+        void* dbg_gwin = nullptr;
+        if (dbg) {
+            const FrameRun& F = fr[0];
+            const size_t nv = (size_t)F.w * F.h * F.Ds;
+            void* p;
+            FM_TRY(ensure(c, "dbg:agg", 2 * nv, &p));
+            fm::launch_sum_parts((const uint16_t*)F.pSb, parts, nv, nv, (uint16_t*)p, st);
+            FM_TRY(ensure(c, "dbg:gwin", 4 * (size_t)F.w * F.h, &dbg_gwin));
+        }
         for (int f = 0; f < n; ++f) {
             FrameRun& F = fr[f];
             const fassmvs_frame& X = *F.fr;
@@ -1005,18 +1032,34 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 StageTimer tm(c, FASSMVS_STAGE_WTA, st);
                 fm::launch_wta_refine((const uint16_t*)F.pSb, (const int32_t*)F.plo, F.w, F.h, F.D, F.Ds,
                                       (const float*)F.delta, intr(F.Kl), nf,
-                                      cfg.median5 ? (float*)F.pdraw : (float*)F.pdmed, nullptr, st, parts,
+                                      cfg.median5 ? (float*)F.pdraw : (float*)F.pdmed,
+                                      dbg && f == 0 ? (int32_t*)dbg_gwin : nullptr, st, parts,
                                       (size_t)F.w * F.h * F.Ds);
             }
             if (cfg.median5) {
                 StageTimer tm(c, FASSMVS_STAGE_MEDIAN, st);
                 fm::launch_median5((const float*)F.pdraw, F.w, F.h, (float*)F.pdmed, st);
             }
+            if (dbg && f == 0) {
+                const size_t np = (size_t)F.w * F.h;
+                void* p;
+                FM_TRY(ensure(c, "dbg:draw", 4 * np, &p));
+                FM_TRY(cuda_check(c, cudaMemcpyAsync(p, cfg.median5 ? F.pdraw : F.pdmed, 4 * np,
+                                                     cudaMemcpyDeviceToDevice, st), "capture"));
+                FM_TRY(ensure(c, "dbg:dmed", 4 * np, &p));
+                FM_TRY(cuda_check(c, cudaMemcpyAsync(p, F.pdmed, 4 * np, cudaMemcpyDeviceToDevice, st), "capture"));
+            }
             {
                 StageTimer tm(c, FASSMVS_STAGE_NORMALS, st);
                 fm::launch_normals((const float*)F.pdmed, F.img[l][0], F.Ps[l], F.w, F.h, intr(F.Kl), cfg.normal_radius,
                                    cfg.normal_beta, (float*)F.pnraw, (float*)F.pnrm, nf, cfg.rho_deg,
                                    l == 0 ? X.conf : nullptr, st);
+            }
+            if (dbg && f == 0) {
+                void* p;
+                FM_TRY(ensure(c, "dbg:nrm", 12 * (size_t)F.w * F.h, &p));
+                FM_TRY(cuda_check(c, cudaMemcpyAsync(p, F.pnrm, 12 * (size_t)F.w * F.h, cudaMemcpyDeviceToDevice, st),
+                                  "capture"));
             }
             F.dprev = (float*)F.pdmed;
             F.nprev = (float*)F.pnrm;
@@ -1033,7 +1076,10 @@ uint64_t batch_signature(const fassmvs_ctx* c, const fassmvs_frame* fr, int n, c
     uint64_t h = 1469598103934665603ull;
     auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
     mix((uint64_t)n);
-    if (tn) { mix((uint64_t)tn->chunk_planes); mix((uint64_t)tn->ctas_per_sm); mix((uint64_t)tn->sgm_parts); }
+    if (tn) {
+        mix((uint64_t)tn->chunk_planes); mix((uint64_t)tn->ctas_per_sm); mix((uint64_t)tn->sgm_parts);
+        mix((uint64_t)tn->no_staging);
+    }
     const unsigned char* cb = reinterpret_cast<const unsigned char*>(&c->cfg);
     for (size_t i = 0; i < sizeof(c->cfg); ++i) mix(cb[i]);
     for (int f = 0; f < n; ++f) {
@@ -1066,7 +1112,7 @@ fassmvs_status estimate_batch_impl(fassmvs_ctx* c, const fassmvs_frame* frames, 
     const uint64_t sig = batch_signature(c, frames, n, &tn);
     Stage sg;
     FM_TRY(stage_prepare(c, frames, n, tn.chunk_planes, &sg));
-    if (!c->graph || st == nullptr || !c->seen.count(sig)) {
+    if (!c->graph || st == nullptr || !c->seen.count(sig) || c->dbg_level >= 0) {
         // eager (and the first run of a shape: allocates all scratch)
         FM_TRY(run_batch(c, frames, n, st, tn, sg, nullptr));
         c->seen[sig] = 1;
@@ -1313,6 +1359,37 @@ V3 corner_ray(const double Ki[9], int W, int H, int c)
     return mat_vec(Ki, v3((c & 1) ? W - 1 : 0, (c & 2) ? H - 1 : 0, 1.0));
 }
 }  // namespace
+
+fassmvs_status fassmvs_debug_capture(fassmvs_ctx* c, int level)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (level < -1 || level >= c->cfg.levels) return fail(c, FASSMVS_EINVAL, "level -1 (off) or 0..levels-1");
+    c->dbg_level = level;
+    memset(c->dbg_dims, 0, sizeof c->dbg_dims);
+    return FASSMVS_OK;
+}
+
+fassmvs_status fassmvs_debug_dump(fassmvs_ctx* c, int level, int what, void* dst, size_t cap, size_t* bytes,
+                                  int32_t dims[5])
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (level != c->dbg_level || c->dbg_dims[0] == 0)
+        return fail(c, FASSMVS_EINVAL, "level %d was not captured by the last estimate", level);
+    static const char* const names[8] = {"dbg:S",    "dbg:lo",   "dbg:dI",   "dbg:agg",
+                                         "dbg:gwin", "dbg:draw", "dbg:dmed", "dbg:nrm"};
+    if (what < 0 || what > 7) return fail(c, FASSMVS_EINVAL, "what 0..7");
+    const size_t np = (size_t)c->dbg_dims[0] * c->dbg_dims[1], nv = np * c->dbg_dims[3];
+    const size_t need[8] = {2 * nv, 4 * np, 8 * np, 2 * nv, 4 * np, 4 * np, 4 * np, 12 * np};
+    if (bytes) *bytes = need[what];
+    if (dims) memcpy(dims, c->dbg_dims, sizeof c->dbg_dims);
+    if (!dst) return FASSMVS_OK;
+    if (cap < need[what]) return fail(c, FASSMVS_EINVAL, "%zu bytes needed", need[what]);
+    auto it = c->bufs.find(names[what]);
+    if (it == c->bufs.end() || !it->second.p) return fail(c, FASSMVS_EINVAL, "nothing captured");
+    FM_TRY(set_device(c));
+    FM_TRY(cuda_check(c, cudaStreamSynchronize(c->last), "sync"));
+    return cuda_check(c, cudaMemcpy(dst, it->second.p, need[what], cudaMemcpyDefault), "dump copy");
+}
 
 fassmvs_status fassmvs_debug_inject(fassmvs_ctx* c, int mode)
 {

@@ -155,6 +155,8 @@ void launch_delta_table(double rho0, double drho, int G, float* delta, cudaStrea
 // cost volume [Ds / 16][np][16] (as the batched cost kernel writes it) ->
 // [np][Ds] (as the aggregation reads it); Ds a multiple of 16
 void launch_relayout16(const uint16_t* src, uint16_t* dst, size_t np, int Ds, cudaStream_t st);
+// out[i] = sum over p < parts of Sbar[p * stride + i] (the aggregate of a debug capture)
+void launch_sum_parts(const uint16_t* Sbar, int parts, size_t stride, size_t n, uint16_t* out, cudaStream_t st);
 void launch_median5(const float* in, int W, int H, float* out, cudaStream_t st);
 void launch_normals(const float* depth, const uint8_t* img, int img_pitch, int W, int H, Intr K,
                     int radius, float beta, float* raw, float* normal, const float npl[3],

@@ -30,6 +30,8 @@ struct fassmvs_ctx {
     // stage timers
     bool prof = false;
     int inject = 0;                      // test hook (fassmvs_debug_inject)
+    int dbg_level = -1;                  // level captured by the next estimate (fassmvs_debug_capture)
+    int dbg_dims[5] = {0, 0, 0, 0, 0};  // W, H, D, Ds, G of the captured level
     struct Rec { cudaEvent_t a, b; int stage; };
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> pending;

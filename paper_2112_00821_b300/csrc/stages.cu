@@ -127,6 +127,17 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
 // [Ds / 16][np][16] -> [np][Ds]: warp w moves pixels 32 w .. 32 w + 31, lane l
 // pixel 32 w + l; per 16-plane block the warp reads 1 KB contiguous and every
 // lane writes one whole 32-byte sector of its pixel's row.
+// sum of the aggregation's partial sums (debug capture): out[i] = sum_p Sbar[p * stride + i]
+__global__ void sum_parts_kernel(const uint16_t* __restrict__ Sbar, int parts, size_t stride, size_t n,
+                                 uint16_t* __restrict__ out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t v = 0;
+    for (int p = 0; p < parts; ++p) v += Sbar[(size_t)p * stride + i];
+    out[i] = (uint16_t)v;
+}
+
 __global__ void relayout16_kernel(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst, size_t np,
                                   int Ds)
 {
@@ -355,6 +366,13 @@ void launch_relayout16(const uint16_t* src, uint16_t* dst, size_t np, int Ds, cu
 {
     if (np == 0) return;
     relayout16_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(src, dst, np, Ds);
+    count_launch();
+}
+
+void launch_sum_parts(const uint16_t* Sbar, int parts, size_t stride, size_t n, uint16_t* out, cudaStream_t st)
+{
+    if (n == 0) return;
+    sum_parts_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Sbar, parts, stride, n, out);
     count_launch();
 }
 

@@ -126,6 +126,8 @@ _SIGS = {
     "fassmvs_server_get_stats": [_VP, _VP],
     "fassmvs_server_last_error": [_VP],
     "fassmvs_debug_inject": [_VP, C.c_int],
+    "fassmvs_debug_capture": [_VP, C.c_int],
+    "fassmvs_debug_dump": [_VP, C.c_int, C.c_int, _VP, C.c_size_t, _VP, _VP],
     "fassmvs_plane_bounds": [_VP, C.c_int, C.c_int, _VP, C.c_double, C.c_double, _VP, _VP],
     "fassmvs_cross_ratio_planes": [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
                                    _VP, _VP, _VP, _VP],
@@ -340,6 +342,31 @@ class Context:
         return hits
 
     STAGES = ("pyramid", "census", "cost", "sgm", "wta", "median", "normals", "window")
+
+    DUMPS = ("cost", "window", "dsn", "agg", "argmin", "depth_raw", "depth", "normal")
+
+    def debug_capture(self, level):
+        """The next estimates keep the intermediates of pyramid level `level`
+        (frame 0); -1 turns capturing off."""
+        self._check(lib().fassmvs_debug_capture(self._h, int(level)))
+
+    def debug_dump(self, level, what):
+        """One captured intermediate (a name of DUMPS) as a CUDA tensor:
+        cost / agg uint16 (H, W, Ds) viewed as int16, window / argmin int32
+        (H, W), dsn int8 (8, H, W), depth_raw / depth float32 (H, W), normal
+        float32 (H, W, 3)."""
+        import torch
+        w = self.DUMPS.index(what)
+        dims = (C.c_int32 * 5)()
+        nb = C.c_size_t()
+        self._check(lib().fassmvs_debug_dump(self._h, int(level), w, None, 0, C.byref(nb), dims))
+        W, H, D, Ds, G = list(dims)
+        shape, dt = {0: ((H, W, Ds), torch.int16), 1: ((H, W), torch.int32), 2: ((8, H, W), torch.int8),
+                     3: ((H, W, Ds), torch.int16), 4: ((H, W), torch.int32), 5: ((H, W), torch.float32),
+                     6: ((H, W), torch.float32), 7: ((H, W, 3), torch.float32)}[w]
+        out = torch.empty(shape, dtype=dt, device="cuda")
+        self._check(lib().fassmvs_debug_dump(self._h, int(level), w, _ptr(out), nb.value, None, None))
+        return out, dict(W=W, H=H, D=D, Ds=Ds, G=G)
 
     def debug_inject(self, mode):
         """Test hook: 1 makes the cost kernel's staged waits give up (results
