@@ -318,3 +318,28 @@ def test_post_filters_in_the_server_equal_the_standalone_filters(streams):
     with pytest.raises(fassmvs.FassmvsError):
         srv.release_depth(1)
     srv.close()
+
+
+def test_post_filters_with_host_outputs(streams):
+    """With pinned host outputs the filters act on the server's device copy
+    before it is copied back: the result equals the device-output request's."""
+    import time
+    from paper_2112_00821_b300 import fassmvs, serve
+    s = streams[1]
+    r, idx, G0 = s.reqs[2]
+    srv = fassmvs.Server(_cfg(), fassmvs.server_config(lanes=1, max_batch=1, mem_budget=2 << 30))
+    _push(srv, s, sorted(idx + [r]))
+    dev_o = _outs(s)
+    host_o = tuple(torch.empty_like(x, device="cpu").pin_memory() for x in dev_o)
+    got = {}
+    for q, o in ((1, dev_o), (2, host_o)):
+        srv.submit(q, s.fid(r), [s.fid(k) for k in idx], serve._planes(G0), *o, postfilter=fassmvs.POST_DOG)
+        t0 = time.monotonic()
+        while q not in got and time.monotonic() - t0 < 60:
+            for x in srv.poll(4, 1000):
+                got[x["id"]] = x
+        assert got[q]["status"] == fassmvs.OK
+    torch.cuda.synchronize()
+    for x, y in zip(dev_o, host_o):
+        assert torch.equal(x.cpu(), y)
+    srv.close()
