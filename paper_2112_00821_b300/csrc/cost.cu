@@ -3,12 +3,16 @@
 // A CTA of 8 warps owns a 56 x 52 tile of reference pixels and walks every
 // plane its windows need, one (plane, view) pair per iteration:
 //   1. sampling: the 64 x 58 warped sample tile (tile + 9x7 census halo) is
-//      produced cooperatively -- each warp owns ~7 sample rows, each lane two
-//      sample columns (coalesced neighbour-image reads), the homography is
-//      stepped down the column in double-float arithmetic; samples are stored
-//      as FP16 pairs (V(x), V(x+1)) so the census can load two at a time;
+//      produced cooperatively -- each warp owns 7 or 8 sample rows, each
+//      lane two sample columns (coalesced
+//      neighbour-image reads), the homography is stepped down the column in
+//      double-float arithmetic; samples are stored as FP16 pairs (V(x),
+//      V(x+1)) so the census can load two at a time;
 //   2. one __syncthreads (the sample tile is double-buffered);
-//   3. census: warp w takes a 32-column x 13-row chunk of the tile; for every
+//   3. census: warp w < 7 takes columns 8w .. 8w + 7 of the tile, lane l
+//      column 8w + l % 8 and rows 13 (l / 8) .. + 12 (every lane of the seven
+//      warps busy; rows 72 words apart so the four row chunks fall in
+//      different shared-memory banks); for every
 //      window row, five packed FP16 saturating subtractions give ten
 //      comparison bits [V(q) < V(p)] which five packed FMAs add, with
 //      power-of-two weights, into four FP16x2 accumulators (10 bits per half,
@@ -33,9 +37,15 @@ namespace fm {
 namespace {
 
 constexpr int PW = 56, PH = 52;          // pixel tile
-constexpr int SW = 64, SH = PH + 6;      // sample tile (PW + 8 <= SW)
+constexpr int SW = 72, SH = PH + 6;      // sample tile rows: 64 samples (PW + 8) in a 72-word stride
 constexpr int NWARP = 8, THREADS = 256;
 constexpr int CH = 13;                   // pixel rows per census chunk (PH / 4)
+constexpr int kCensusWarps = PW / 8;     // 7 warps x (8 columns x 4 chunks of 13 rows)
+constexpr int kPlanWarp = NWARP - 1;     // plans and issues the staging copies
+// first sample row of warp w's share (7 or 8 rows each)
+__host__ __device__ constexpr int row_start(int w) { return (SH * w) / NWARP; }
+constexpr int kMaxRows = 8;              // the largest share
+static_assert(row_start(NWARP) - row_start(NWARP - 1) <= kMaxRows, "row shares");
 constexpr int PMAX = 1 << 24;
 constexpr float MAGIC = 12582912.0f;     // 1.5 * 2^23: adding it leaves an integer in the mantissa
 constexpr int MAGIC_BITS = 0x4B400000;
@@ -247,7 +257,7 @@ __device__ __forceinline__ bool stage_wait(uint64_t* mbar, uint32_t parity, long
     }
 }
 
-// warp 0: the box for pair (g, k) into `slot`.  Lanes 0-3 warp the four
+// the planning warp: the box for pair (g, k) into `slot`.  Lanes 0-3 warp the four
 // corners of the (clamped) sample tile in FP32 (the box gets two pixels of
 // margin, more than the FP32 error of a corner); all four must lie in front of
 // the view.  The box origin's x is a multiple of 16 (TMA alignment).
@@ -374,7 +384,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     const int chunk = (thi - tlo + nz - 1) / nz;
     const int glo = tlo + bz * chunk, ghi = min(thi, glo + chunk);
     const bool use_stage = a.tmaps != nullptr && stg != nullptr;
-    if (use_stage && warp == 0 && ghi > glo) {
+    if (use_stage && warp == kPlanWarp && ghi > glo) {
         // the tensor maps were written to global memory by a host copy: the
         // issuing thread orders the tensor-map proxy's reads after it
         if (lane == 0)
@@ -387,12 +397,13 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     }
     __syncthreads();
 
-    // census role: columns cp*32 + lane, rows rc*13 .. rc*13 + 12
-    const int pc = (warp & 1) * 32 + lane;
-    const int pr0 = (warp >> 1) * CH;
-    const bool cact = pc < PW;
+    // census role (warps 0-6): column 8 * warp + lane % 8, rows
+    // 13 * (lane / 8) .. + 12; warp 7 has none
+    const int pc = warp * 8 + (lane & 7);
+    const int pr0 = (lane >> 3) * CH;
+    const bool cact = warp < kCensusWarps;
     // sampling role: sample rows [rs, re), sample columns lane and 32 + lane
-    const int rs = (SH * warp) / NWARP, re = (SH * (warp + 1)) / NWARP;
+    const int rs = row_start(warp), re = row_start(warp + 1);
     const int X0 = min(max(tx0 - 4 + lane, 0), W - 1);
     const int X1 = min(max(tx0 + 28 + lane, 0), W - 1);
     // Windows differ across the tile (a per-pixel range of D planes), so a
@@ -430,16 +441,16 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         const bool do_cost = cact && g >= cplo && g < cphi;
         for (int k = 0; k < a.V; ++k) {
             // ---------------------------------------------------------- staging of the next pair
-            if (use_stage && warp == 0) {
+            if (use_stage && warp == kPlanWarp) {
                 const int gn = k + 1 < a.V ? g : g + 1, kn = k + 1 < a.V ? k + 1 : 0;
                 if (gn < ghi) stage_plan(a, sm, stg, tx0, ty0, gn, kn, buf ^ 1, lane);
             }
             const bool staged = use_stage && sm.stg_ok[buf];
-            // every issued copy completes before the barrier below: warp 0 waits
-            // for it even when it samples nothing of this plane (a plane in a gap
-            // between the tile's windows is needed by no warp)
+            // every issued copy completes before the barrier below: the planning
+            // warp waits for it even when it samples nothing of this plane (a
+            // plane in a gap between the tile's windows is needed by no warp)
             bool ready = false;
-            if (staged && (do_sample || warp == 0)) {
+            if (staged && (do_sample || warp == kPlanWarp)) {
                 ready = stage_wait(&sm.mbar[buf], (phase >> buf) & 1u, a.stage_test ? (1LL << 21) : (1LL << 31));
                 if (!ready && lane == 0) {
                     if (a.err) atomicOr(a.err, 1);
@@ -472,7 +483,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 auto rows = [&](auto staged_tag) {
                 constexpr bool ST = decltype(staged_tag)::value;
 #pragma unroll 2
-                for (int jj = 0; jj < 8; ++jj) {
+                for (int jj = 0; jj < kMaxRows; ++jj) {
                     const int j = rs + jj;
                     if (j >= re) break;
                     const int Y = ty0 - 3 + j;
