@@ -171,7 +171,9 @@ void complete(fassmvs_server* s, SReq* q, fassmvs_status st, int batch_size)
     s->results.push_back(r);
     if (q->off != SIZE_MAX) s->arena.release(q->off);
     if (q->keep_off != SIZE_MAX) {
-        if (st == FASSMVS_OK) {
+        // (a second request with the same id in flight keeps nothing: the
+        // first map stays, the block is given back)
+        if (st == FASSMVS_OK && !s->kept.count(q->r.id)) {
             Kept& k = s->kept[q->r.id];
             const SFrame* F0 = q->frames[0];
             k.off = q->keep_off;
