@@ -98,6 +98,16 @@ __device__ __forceinline__ df to_grid(df a)
     return {h, __fadd_rn(a.lo, __fsub_rn(a.hi, h))};
 }
 __device__ __forceinline__ df grid_add(df a, df b) { return {__fadd_rn(a.hi, b.hi), __fadd_rn(a.lo, b.lo)}; }
+// The denominator D is carried divided by 256 (exact: a power of two), which
+// puts its high words on the 2^-18 grid with |D / 256| < 2^4 and lets the
+// reciprocal give 256 / D directly.
+constexpr float DGRID_MAGIC = 48.0f;     // 1.5 * 2^5: rounds |x| < 2^4 to the 2^-18 grid
+__device__ __forceinline__ df to_dgrid(df a)
+{
+    float h = __fsub_rn(__fadd_rn(a.hi, DGRID_MAGIC), DGRID_MAGIC);
+    return {h, __fadd_rn(a.lo, __fsub_rn(a.hi, h))};
+}
+__device__ __forceinline__ df df_scale(df a, float s) { return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)}; }
 
 // a * b for an integer-valued b (|b| < 2^24)
 __device__ __forceinline__ df df_mul_int(df a, float b)
@@ -118,35 +128,39 @@ __device__ __forceinline__ float rcp_approx(float x)
 
 __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h + i), __ldg(h + 9 + i)}; }
 
-// floor(256 N / D) for D > 0 (r ~ 1/(D.hi + D.lo)), for |N / D| < 16000:
-// q = N/D to a few ulps, the double-float residual N - q D gives the
-// correction, and the floors come from adding 1.5 * 2^23 with round-down.
-// The words of N and D are split on the 2^-10 grid, so the low words are not
-// small: q and r are formed from the summed words.
+// floor(256 N / D) for D > 0, given Dn = D / 256 and r ~ 256 / D, for
+// |N / D| < 16000: q = 256 N / D to a few ulps, the double-float residual
+// N - (q / 256) D = N - q Dn gives the correction, and the floors come from
+// adding 1.5 * 2^23 with round-down.  The words of N and D are split on a
+// grid, so the low words are not small: q and r are formed from the summed
+// words.
 __device__ __forceinline__ int fix_pos(df N, df Dn, float r)
 {
     float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
     float e1 = __fmaf_rn(-q, Dn.hi, N.hi);
     float e2 = __fmaf_rn(-q, Dn.lo, N.lo);
     float corr = __fmul_rn(__fadd_rn(e1, e2), r);
-    float a = fminf(fmaxf(__fmul_rn(q, 256.0f), -4194000.0f), 4194000.0f);
+    float a = fminf(fmaxf(q, -4194000.0f), 4194000.0f);
     float t1 = __fadd_rd(a, MAGIC);
     float fa = __fsub_rn(t1, MAGIC);
-    float rem = __fmaf_rn(corr, 256.0f, __fsub_rn(a, fa));
+    float rem = __fadd_rn(corr, __fsub_rn(a, fa));
     float t2 = __fadd_rd(rem, MAGIC);
-    return __float_as_int(t1) + __float_as_int(t2) - 2 * MAGIC_BITS;
+    return (__float_as_int(t1) - MAGIC_BITS) + (__float_as_int(t2) - MAGIC_BITS);
 }
 
-// one warped sample: its value V = 16 x grey level in [0, 4080] and whether
-// the position lies on the image grid
-template <bool WANT_OK, bool STAGED>
-__device__ __forceinline__ int sample(const uint8_t* __restrict__ img, int W, int H, int pitch, df Nu,
-                                      df Nv, df Dn, bool& ok, const uint8_t* stg, int sx0, int sy0)
+// The clamped tap position of one warped sample and whether the position
+// lies on the image grid.  Dn is the denominator divided by 256; its sign is
+// that of the exact sum of its words (rounding keeps the sign).
+struct SPos { int iu, iv, A, B; };
+
+template <bool WANT_OK>
+__device__ __forceinline__ SPos sample_pos(int W, int H, df Nu, df Nv, df Dn, bool& ok)
 {
     int Pu = -PMAX, Pv = -PMAX;
-    const bool front = Dn.hi > 0.0f || (Dn.hi == 0.0f && Dn.lo > 0.0f);
+    const float dsum = __fadd_rn(Dn.hi, Dn.lo);
+    const bool front = dsum > 0.0f;
     if (front) {
-        float r = rcp_approx(__fadd_rn(Dn.hi, Dn.lo));
+        const float r = rcp_approx(dsum);
         Pu = fix_pos(Nu, Dn, r);
         Pv = fix_pos(Nv, Dn, r);
     }
@@ -154,27 +168,34 @@ __device__ __forceinline__ int sample(const uint8_t* __restrict__ img, int W, in
     if (WANT_OK) ok = front && Pu >= 0 && Pu <= wmax && Pv >= 0 && Pv <= hmax;
     const int cu = min(max(Pu, 0), wmax), cv = min(max(Pv, 0), hmax);
     const int iu = min(cu >> 8, W - 2), iv = min(cv >> 8, H - 2);
-    const int A = cu - 256 * iu, B = cv - 256 * iv;
-    int i00, i01, i10, i11;
-    bool in_box = false;
-    if constexpr (STAGED) {
-        const int ru = iu - sx0, rv = iv - sy0;
-        in_box = (unsigned)ru <= (unsigned)(kStageBX - 2) && (unsigned)rv <= (unsigned)(kStageBY - 2);
-        if (in_box) {
-            // the 2x2 taps from the staged box of the view image
-            const uint8_t* r0 = stg + rv * kStageBX + ru;
-            i00 = r0[0]; i01 = r0[1];
-            i10 = r0[kStageBX]; i11 = r0[kStageBX + 1];
-        }
-    }
-    if (!in_box) {
-        const uint8_t* r0 = img + (size_t)iv * pitch + iu;
-        i00 = __ldg(r0); i01 = __ldg(r0 + 1);
-        i10 = __ldg(r0 + pitch); i11 = __ldg(r0 + pitch + 1);
-    }
+    return {iu, iv, cu - 256 * iu, cv - 256 * iv};
+}
+
+// exact integer bilinear blend with 8-bit weights: V = 16 x grey level in [0, 4080]
+__device__ __forceinline__ int blend(int i00, int i01, int i10, int i11, int A, int B)
+{
     const int top = (i00 << 8) + A * (i01 - i00);
     const int bot = (i10 << 8) + A * (i11 - i10);
-    return ((top << 8) + B * (bot - top) + 2048) >> 12;     // [0, 4080]
+    return ((top << 8) + B * (bot - top) + 2048) >> 12;
+}
+
+// the 2x2 taps from global memory
+__device__ __forceinline__ int taps_global(const uint8_t* __restrict__ img, int pitch, SPos p)
+{
+    const uint8_t* r0 = img + (size_t)p.iv * pitch + p.iu;
+    return blend(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + pitch), __ldg(r0 + pitch + 1), p.A, p.B);
+}
+
+// the 2x2 taps from the staged box whose origin is (sx0, sy0) (in_box true)
+__device__ __forceinline__ int taps_staged(const uint8_t* stg, int sx0, int sy0, SPos p)
+{
+    const uint8_t* r0 = stg + (p.iv - sy0) * kStageBX + (p.iu - sx0);
+    return blend(r0[0], r0[1], r0[kStageBX], r0[kStageBX + 1], p.A, p.B);
+}
+
+__device__ __forceinline__ bool in_box(int sx0, int sy0, SPos p)
+{
+    return (unsigned)(p.iu - sx0) <= (unsigned)(kStageBX - 2) && (unsigned)(p.iv - sy0) <= (unsigned)(kStageBY - 2);
 }
 
 // V - 2040 as a float (exact), ready for FP16
@@ -465,17 +486,18 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 const uint8_t* img = a.views.img[k];
                 const df h0 = load_df(h, 0), h1 = load_df(h, 1), h2 = load_df(h, 2);
                 const df h3 = load_df(h, 3), h4 = load_df(h, 4), h5 = load_df(h, 5);
-                const df h6 = load_df(h, 6), h7 = load_df(h, 7), h8 = load_df(h, 8);
+                const df h6 = df_scale(load_df(h, 6), 0.00390625f), h7 = df_scale(load_df(h, 7), 0.00390625f);
+                const df h8 = df_scale(load_df(h, 8), 0.00390625f);     // the denominator row / 256
                 const float fy = (float)min(max(ty0 - 3 + rs, 0), H - 1);
                 const float fx0 = (float)X0, fx1 = (float)X1;
                 const df by_u = df_add(df_mul_int(h1, fy), h2);
                 const df by_v = df_add(df_mul_int(h4, fy), h5);
                 const df by_d = df_add(df_mul_int(h7, fy), h8);
                 df u0 = to_grid(df_add(df_mul_int(h0, fx0), by_u)), v0 = to_grid(df_add(df_mul_int(h3, fx0), by_v));
-                df d0 = to_grid(df_add(df_mul_int(h6, fx0), by_d));
+                df d0 = to_dgrid(df_add(df_mul_int(h6, fx0), by_d));
                 df u1 = to_grid(df_add(df_mul_int(h0, fx1), by_u)), v1 = to_grid(df_add(df_mul_int(h3, fx1), by_v));
-                df d1 = to_grid(df_add(df_mul_int(h6, fx1), by_d));
-                const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
+                df d1 = to_dgrid(df_add(df_mul_int(h6, fx1), by_d));
+                const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_dgrid(h7);
                 uint32_t(*prow)[SW] = sm.pair[buf];
                 // the row loop in two variants, chosen once per (plane, view):
                 // taps from the staged box (global memory outside it), or from
@@ -494,12 +516,28 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     bool ok0 = false, ok1 = false;
                     const bool centre_row = j >= 3 && j < 3 + PH;
                     int i0, i1;
+                    SPos p0, p1;
                     if (centre_row) {
-                        i0 = sample<true, ST>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
-                        i1 = sample<true, ST>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
+                        p0 = sample_pos<true>(W, H, u0, v0, d0, ok0);
+                        p1 = sample_pos<true>(W, H, u1, v1, d1, ok1);
                     } else {
-                        i0 = sample<false, ST>(img, W, H, a.pitch, u0, v0, d0, ok0, sp, sx0, sy0);
-                        i1 = sample<false, ST>(img, W, H, a.pitch, u1, v1, d1, ok1, sp, sx0, sy0);
+                        p0 = sample_pos<false>(W, H, u0, v0, d0, ok0);
+                        p1 = sample_pos<false>(W, H, u1, v1, d1, ok1);
+                    }
+                    if constexpr (ST) {
+                        // a row whose taps all lie in the box (the usual case)
+                        // takes one straight shared-memory path
+                        const bool b0 = in_box(sx0, sy0, p0), b1 = in_box(sx0, sy0, p1);
+                        if (__all_sync(0xFFFFFFFFu, b0 && b1)) {
+                            i0 = taps_staged(sp, sx0, sy0, p0);
+                            i1 = taps_staged(sp, sx0, sy0, p1);
+                        } else {
+                            i0 = b0 ? taps_staged(sp, sx0, sy0, p0) : taps_global(img, a.pitch, p0);
+                            i1 = b1 ? taps_staged(sp, sx0, sy0, p1) : taps_global(img, a.pitch, p1);
+                        }
+                    } else {
+                        i0 = taps_global(img, a.pitch, p0);
+                        i1 = taps_global(img, a.pitch, p1);
                     }
                     if constexpr (NCC) {
                         int n0 = __shfl_sync(0xFFFFFFFFu, i0, (lane + 1) & 31);
