@@ -249,16 +249,13 @@ __device__ __forceinline__ void stage_init(SmemCost& sm)
 
 __device__ __forceinline__ void stage_issue(uint64_t* mbar, uint8_t* dst, const void* tmap, int x0, int y0)
 {
-    uint64_t state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state)
-                 : "r"(smem_u32(mbar)), "r"(kStageBX * kStageBY)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_u32(mbar)), "r"(kStageBX * kStageBY)
                  : "memory");
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(smem_u32(dst)), "l"((uint64_t)tmap), "r"(x0), "r"(y0), "r"(smem_u32(mbar))
         : "memory");
-    (void)state;
 }
 
 // waits for the phase of the given parity, at most `bound` clocks (2^31,

@@ -1,14 +1,18 @@
 // Surface-aware semi-global matching (Sec. 2.3 of FaSS-MVS) for sm_103a.
 //
 // One warp walks one path line; lane l holds hypotheses 8l .. 8l+7 of the
-// current pixel, so the previous path line stays in registers.  Per step:
-// the transition minimum T(s') = min(L'(s'), L'(s' +- 1) + P1, M' + P2) is
-// formed on the predecessor's slots (two neighbour shuffles), shifted by the
-// warp-uniform sigma = lo_p - lo_{p-r} + di through a per-warp shared buffer
-// when sigma != 0, added to the data cost, and the new minimum (and, for the
-// path-gradient variant, its slot) comes from a 5-step shuffle reduction.
-// Each direction is one launch; the first writes the aggregate, the others
-// add to it (stream order keeps them apart).
+// current pixel, two per register, so the previous step stays in registers.
+// Per step: the transition minimum T(s') = min(L'(s'), L'(s' +- 1) + P1,
+// M' + P2) is formed on the predecessor's slots with the packed 16x2 min and
+// add-min instructions (the neighbour pairs across lanes come from two
+// shuffles of the previous step), shifted by the warp-uniform
+// sigma = lo_p - lo_{p-r} + di through a per-warp shared buffer when
+// sigma != 0, and added to the data cost; the new minimum (and, for the
+// path-gradient variant, its slot) comes from one warp min-reduction.
+// The stage entry point runs one launch per direction, the first writing the
+// aggregate and the others adding to it (stream order keeps them apart); the
+// estimate runs several directions of several frames in one launch, each
+// direction into its own partial sum, which the winner-takes-all step adds.
 #include "fm_internal.cuh"
 
 namespace fm {
@@ -16,22 +20,7 @@ namespace fm {
 namespace {
 
 constexpr int WARPS = 4;
-constexpr uint32_t INF = 0x3FFFFFFFu;
 constexpr unsigned FULL = 0xFFFFFFFFu;
-
-__device__ __forceinline__ void unpack8(uint4 v, uint32_t (&o)[8])
-{
-    o[0] = v.x & 0xFFFFu; o[1] = v.x >> 16;
-    o[2] = v.y & 0xFFFFu; o[3] = v.y >> 16;
-    o[4] = v.z & 0xFFFFu; o[5] = v.z >> 16;
-    o[6] = v.w & 0xFFFFu; o[7] = v.w >> 16;
-}
-
-__device__ __forceinline__ uint4 pack8(const uint32_t (&o)[8])
-{
-    return make_uint4(o[0] | (o[1] << 16), o[2] | (o[3] << 16), o[4] | (o[5] << 16),
-                      o[6] | (o[7] << 16));
-}
 
 // The data costs and running aggregate of the pixel PF steps down the line
 // are copied into a per-warp shared ring with cp.async (each lane its own 16
