@@ -208,11 +208,14 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
             if (lane == 0) left = INF2;
             if (lane == 31) right = INF2;
             if (a.variant == 2) {
+                // key = cost << 8 | slot: one byte permutation per slot takes
+                // the slot number (byte 0) and the 16-bit cost (bytes 1, 2) with
+                // a zero top byte
                 uint32_t key = 0xFFFFFFFFu;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    key = min(key, ((L[j] & 0xFFFFu) << 8) | (uint32_t)(s0 + 2 * j));
-                    key = min(key, ((L[j] >> 16) << 8) | (uint32_t)(s0 + 2 * j + 1));
+                    key = min(key, __byte_perm(L[j], (uint32_t)(s0 + 2 * j), 0x5104));
+                    key = min(key, __byte_perm(L[j], (uint32_t)(s0 + 2 * j + 1), 0x5324));
                 }
                 key = __reduce_min_sync(FULL, key);
                 M = key >> 8;
