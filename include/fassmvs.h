@@ -136,6 +136,22 @@ FASSMVS_API fassmvs_status fassmvs_estimate(fassmvs_ctx* ctx, const uint8_t* ref
                                 const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* planes,
                                 float* depth, float* normal, float* conf, void* stream);
 
+/* The same estimate from HOST images to HOST maps: ref and nbrs[k] (a HOST
+ * array of n_nb HOST pointers) are W x H uint8 images in host memory with row
+ * pitch `pitch` bytes (>= W); depth (W*H floats), normal (W*H*3) and conf
+ * (W*H) are host buffers.  The call copies the images into device buffers
+ * that the context owns (rows padded to 16 bytes, so that the cost kernel can
+ * stage them; allocated on the first call of a size, within the context
+ * budget: FASSMVS_ENOMEM beyond it), runs fassmvs_estimate on `stream`,
+ * copies the maps back on the same stream and returns once they are in the
+ * host buffers.  Page-locked host memory makes the copies DMA transfers;
+ * pageable memory works and is staged by the driver.  Results equal those of
+ * fassmvs_estimate on device copies of the same images, bit for bit. */
+FASSMVS_API fassmvs_status fassmvs_estimate_host(fassmvs_ctx* ctx, const uint8_t* ref, int W, int H, int pitch,
+                                                 const uint8_t* const* nbrs, int n_nb,
+                                                 const fassmvs_planes* planes, float* depth, float* normal,
+                                                 float* conf, void* stream);
+
 /* ---- batched form ------------------------------------------------------- */
 
 /* One reference frame of a batch (all pointers as for fassmvs_estimate; the

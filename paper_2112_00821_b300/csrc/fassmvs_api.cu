@@ -1260,6 +1260,49 @@ fassmvs_status fassmvs_estimate(fassmvs_ctx* c, const uint8_t* ref, int W, int H
     return estimate_batch_impl(c, &f, 1, S(stream));
 }
 
+fassmvs_status fassmvs_estimate_host(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch,
+                                     const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* pl, float* depth,
+                                     float* normal, float* conf, void* stream)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (!ref || !nbrs || !pl || !depth || !normal || !conf) return fail(c, FASSMVS_EINVAL, "NULL argument");
+    if (W < 2 || H < 2 || pitch < W) return fail(c, FASSMVS_EINVAL, "image %dx%d with pitch %d", W, H, pitch);
+    if (n_nb != c->V) return fail(c, FASSMVS_EINVAL, "n_nb %d differs from the %d cameras set", n_nb, c->V);
+    for (int k = 0; k < n_nb; ++k)
+        if (!nbrs[k]) return fail(c, FASSMVS_EINVAL, "neighbour %d is NULL", k);
+    FM_TRY(set_device(c));
+    cudaStream_t st = S(stream);
+    // device rows padded to 16 bytes: the cost kernel's TMA staging of level 0
+    // needs 16-byte aligned rows
+    const size_t dp = ((size_t)W + 15) & ~(size_t)15, img = dp * (size_t)H, npix = (size_t)W * H;
+    void* din = nullptr;
+    void* dout = nullptr;
+    FM_TRY(ensure(c, "host_images", img * (size_t)(1 + n_nb), &din));
+    FM_TRY(ensure(c, "host_maps", sizeof(float) * npix * 5, &dout));
+    uint8_t* dimg = static_cast<uint8_t*>(din);
+    const uint8_t* dn[fm::kMaxViews];
+    if (n_nb > fm::kMaxViews) return fail(c, FASSMVS_EINVAL, "at most %d neighbours", fm::kMaxViews);
+    FM_TRY(cuda_check(c, cudaMemcpy2DAsync(dimg, dp, ref, (size_t)pitch, (size_t)W, (size_t)H,
+                                           cudaMemcpyHostToDevice, st), "host to device copy"));
+    for (int k = 0; k < n_nb; ++k) {
+        uint8_t* d = dimg + img * (size_t)(1 + k);
+        FM_TRY(cuda_check(c, cudaMemcpy2DAsync(d, dp, nbrs[k], (size_t)pitch, (size_t)W, (size_t)H,
+                                               cudaMemcpyHostToDevice, st), "host to device copy"));
+        dn[k] = d;
+    }
+    float* dd = static_cast<float*>(dout);
+    float* dnrm = dd + npix;
+    float* dc = dnrm + 3 * npix;
+    FM_TRY(fassmvs_estimate(c, dimg, W, H, (int)dp, dn, n_nb, pl, dd, dnrm, dc, stream));
+    FM_TRY(cuda_check(c, cudaMemcpyAsync(depth, dd, sizeof(float) * npix, cudaMemcpyDeviceToHost, st),
+                      "device to host copy"));
+    FM_TRY(cuda_check(c, cudaMemcpyAsync(normal, dnrm, sizeof(float) * 3 * npix, cudaMemcpyDeviceToHost, st),
+                      "device to host copy"));
+    FM_TRY(cuda_check(c, cudaMemcpyAsync(conf, dc, sizeof(float) * npix, cudaMemcpyDeviceToHost, st),
+                      "device to host copy"));
+    return cuda_check(c, cudaStreamSynchronize(st), "estimate_host");
+}
+
 fassmvs_status fassmvs_profile_enable(fassmvs_ctx* c, int on)
 {
     if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");

@@ -93,6 +93,7 @@ _SIGS = {
     "fassmvs_set_config": [_VP, _VP],
     "fassmvs_set_cameras": [_VP, _VP, C.c_int, _VP, _VP, _VP],
     "fassmvs_estimate": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP],
+    "fassmvs_estimate_host": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP],
     "fassmvs_pyramid_down": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
     "fassmvs_census": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
     "fassmvs_cost_volume": [_VP, _VP, _VP, C.c_int, _VP, C.c_int, C.c_int, _VP, _VP, _VP, _VP,
@@ -246,6 +247,31 @@ class Context:
         self._check(lib().fassmvs_estimate(self._h, _ptr(ref), W, H, pitch, arr, len(nbrs),
                                            C.byref(planes), _ptr(depth), _ptr(normal), _ptr(conf),
                                            _stream()))
+        return depth, normal, conf
+
+    def estimate_host(self, ref, nbrs, planes, depth=None, normal=None, conf=None):
+        """The estimate from host images to host maps (fassmvs_estimate_host):
+        ref and nbrs are CPU uint8 tensors (page-locked or not) of one layout;
+        depth / normal / conf are CPU float32 tensors (allocated here when
+        absent).  Returns once the maps are in them."""
+        import torch
+        H, W = ref.shape
+        pitch = ref.stride(0)
+        for x in [ref] + list(nbrs):
+            if x.device.type != "cpu" or x.dtype != torch.uint8 or x.shape != ref.shape or x.stride(0) != pitch \
+                    or x.stride(1) != 1:
+                raise ValueError("images must be CPU uint8 tensors of one row layout")
+        depth = depth if depth is not None else torch.empty((H, W), dtype=torch.float32)
+        normal = normal if normal is not None else torch.empty((H, W, 3), dtype=torch.float32)
+        conf = conf if conf is not None else torch.empty((H, W), dtype=torch.float32)
+        for t, shp in ((depth, (H, W)), (normal, (H, W, 3)), (conf, (H, W))):
+            if t.device.type != "cpu" or t.dtype != torch.float32 or tuple(t.shape) != shp or not t.is_contiguous():
+                raise ValueError("outputs must be contiguous CPU float32 tensors of the map shapes")
+        arr = (C.c_void_p * len(nbrs))(*[x.data_ptr() for x in nbrs])
+        self._check(lib().fassmvs_estimate_host(self._h, C.c_void_p(ref.data_ptr()), W, H, pitch, arr, len(nbrs),
+                                                C.byref(planes), C.c_void_p(depth.data_ptr()),
+                                                C.c_void_p(normal.data_ptr()), C.c_void_p(conf.data_ptr()),
+                                                _stream()))
         return depth, normal, conf
 
     # ------------------------------------------------------------ batched form
