@@ -139,18 +139,32 @@ FASSMVS_API fassmvs_status fassmvs_estimate(fassmvs_ctx* ctx, const uint8_t* ref
 /* The same estimate from HOST images to HOST maps: ref and nbrs[k] (a HOST
  * array of n_nb HOST pointers) are W x H uint8 images in host memory with row
  * pitch `pitch` bytes (>= W); depth (W*H floats), normal (W*H*3) and conf
- * (W*H) are host buffers.  The call copies the images into device buffers
- * that the context owns (rows padded to 16 bytes, so that the cost kernel can
- * stage them; allocated on the first call of a size, within the context
- * budget: FASSMVS_ENOMEM beyond it), runs fassmvs_estimate on `stream`,
- * copies the maps back on the same stream and returns once they are in the
- * host buffers.  Page-locked host memory makes the copies DMA transfers;
- * pageable memory works and is staged by the driver.  Results equal those of
- * fassmvs_estimate on device copies of the same images, bit for bit. */
+ * (W*H) are host buffers.  The call copies the images into one of two device
+ * slots that the context owns (rows padded to 16 bytes, so that the cost
+ * kernel can stage them; allocated on the first call of a size, within the
+ * context budget: FASSMVS_ENOMEM beyond it) on a copy stream, runs
+ * fassmvs_estimate on `stream` and copies the maps back on a second copy
+ * stream; it returns once the maps are in the host buffers.  Page-locked
+ * host memory makes the copies DMA transfers; pageable memory works and is
+ * staged by the driver.  Results equal those of fassmvs_estimate on device
+ * copies of the same images, bit for bit. */
 FASSMVS_API fassmvs_status fassmvs_estimate_host(fassmvs_ctx* ctx, const uint8_t* ref, int W, int H, int pitch,
                                                  const uint8_t* const* nbrs, int n_nb,
                                                  const fassmvs_planes* planes, float* depth, float* normal,
                                                  float* conf, void* stream);
+
+/* The same call for a sequence of frames: it returns once the images have
+ * been copied to the device (the host image buffers may then be reused), with
+ * the estimate and the copy of the maps still running, so that one frame's
+ * copies overlap the kernels of the frames next to it (two slots: a call
+ * waits, on the device, for the slot's use two calls before).  The maps of a
+ * call are in its host buffers, which must stay valid until then, once
+ * fassmvs_sync or a later fassmvs_estimate_host returns.  A call whose image
+ * size differs from the previous call's first waits for every earlier call. */
+FASSMVS_API fassmvs_status fassmvs_estimate_host_async(fassmvs_ctx* ctx, const uint8_t* ref, int W, int H,
+                                                       int pitch, const uint8_t* const* nbrs, int n_nb,
+                                                       const fassmvs_planes* planes, float* depth, float* normal,
+                                                       float* conf, void* stream);
 
 /* ---- batched form ------------------------------------------------------- */
 

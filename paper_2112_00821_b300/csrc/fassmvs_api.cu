@@ -415,7 +415,12 @@ void fassmvs_destroy(fassmvs_ctx* c)
     for (int i = 0; i < 2; ++i) {
         if (c->host_arena[i]) cudaFreeHost(c->host_arena[i]);
         if (c->arena_ev[i]) cudaEventDestroy(c->arena_ev[i]);
+        if (c->hp_in[i]) cudaEventDestroy(c->hp_in[i]);
+        if (c->hp_comp[i]) cudaEventDestroy(c->hp_comp[i]);
+        if (c->hp_out[i]) cudaEventDestroy(c->hp_out[i]);
     }
+    if (c->hp_h2d) cudaStreamDestroy(c->hp_h2d);
+    if (c->hp_d2h) cudaStreamDestroy(c->hp_d2h);
     delete c;
 }
 
@@ -1260,47 +1265,100 @@ fassmvs_status fassmvs_estimate(fassmvs_ctx* c, const uint8_t* ref, int W, int H
     return estimate_batch_impl(c, &f, 1, S(stream));
 }
 
-fassmvs_status fassmvs_estimate_host(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch,
+namespace {
+// Enqueues one host-buffer estimate (fassmvs_estimate_host_async); *slot
+// receives the device slot it used.
+fassmvs_status estimate_host_enqueue(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch,
                                      const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* pl, float* depth,
-                                     float* normal, float* conf, void* stream)
+                                     float* normal, float* conf, void* stream, int* slot)
 {
     if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
     if (!ref || !nbrs || !pl || !depth || !normal || !conf) return fail(c, FASSMVS_EINVAL, "NULL argument");
     if (W < 2 || H < 2 || pitch < W) return fail(c, FASSMVS_EINVAL, "image %dx%d with pitch %d", W, H, pitch);
     if (n_nb != c->V) return fail(c, FASSMVS_EINVAL, "n_nb %d differs from the %d cameras set", n_nb, c->V);
+    if (n_nb > fm::kMaxViews) return fail(c, FASSMVS_EINVAL, "at most %d neighbours", fm::kMaxViews);
     for (int k = 0; k < n_nb; ++k)
         if (!nbrs[k]) return fail(c, FASSMVS_EINVAL, "neighbour %d is NULL", k);
     FM_TRY(set_device(c));
     cudaStream_t st = S(stream);
-    // device rows padded to 16 bytes: the cost kernel's TMA staging of level 0
-    // needs 16-byte aligned rows
+    if (!c->hp_h2d) {
+        FM_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->hp_h2d, cudaStreamNonBlocking), "copy stream"));
+        FM_TRY(cuda_check(c, cudaStreamCreateWithFlags(&c->hp_d2h, cudaStreamNonBlocking), "copy stream"));
+        for (int i = 0; i < 2; ++i) {
+            FM_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->hp_in[i], cudaEventDisableTiming), "event"));
+            FM_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->hp_comp[i], cudaEventDisableTiming), "event"));
+            FM_TRY(cuda_check(c, cudaEventCreateWithFlags(&c->hp_out[i], cudaEventDisableTiming), "event"));
+        }
+    }
+    // per slot: the images with rows padded to 16 bytes (the cost kernel's
+    // TMA staging of level 0 needs 16-byte aligned rows), then the maps
     const size_t dp = ((size_t)W + 15) & ~(size_t)15, img = dp * (size_t)H, npix = (size_t)W * H;
-    void* din = nullptr;
-    void* dout = nullptr;
-    FM_TRY(ensure(c, "host_images", img * (size_t)(1 + n_nb), &din));
-    FM_TRY(ensure(c, "host_maps", sizeof(float) * npix * 5, &dout));
-    uint8_t* dimg = static_cast<uint8_t*>(din);
+    const size_t img_bytes = (img * (size_t)(1 + n_nb) + 255) & ~(size_t)255;
+    const size_t slot_bytes = img_bytes + sizeof(float) * npix * 5;
+    if (slot_bytes != c->hp_slot_bytes) {
+        // a new layout of the slots: every earlier call has finished with them
+        for (int i = 0; i < 2; ++i)
+            FM_TRY(cuda_check(c, cudaEventSynchronize(c->hp_out[i]), "earlier host estimate"));
+        c->hp_slot_bytes = slot_bytes;
+        c->hp_slot = 0;
+    }
+    void* base = nullptr;
+    FM_TRY(ensure(c, "host_slots", 2 * slot_bytes, &base));
+    const int s = c->hp_slot;
+    unsigned char* sb = static_cast<unsigned char*>(base) + (size_t)s * slot_bytes;
+    uint8_t* dimg = sb;
+    float* dd = reinterpret_cast<float*>(sb + img_bytes);
+    float* dnrm = dd + npix;
+    float* dc = dnrm + 3 * npix;
     const uint8_t* dn[fm::kMaxViews];
-    if (n_nb > fm::kMaxViews) return fail(c, FASSMVS_EINVAL, "at most %d neighbours", fm::kMaxViews);
+    // images: once the estimate of this slot's previous use has read them
+    FM_TRY(cuda_check(c, cudaStreamWaitEvent(c->hp_h2d, c->hp_comp[s], 0), "wait"));
     FM_TRY(cuda_check(c, cudaMemcpy2DAsync(dimg, dp, ref, (size_t)pitch, (size_t)W, (size_t)H,
-                                           cudaMemcpyHostToDevice, st), "host to device copy"));
+                                           cudaMemcpyHostToDevice, c->hp_h2d), "host to device copy"));
     for (int k = 0; k < n_nb; ++k) {
         uint8_t* d = dimg + img * (size_t)(1 + k);
         FM_TRY(cuda_check(c, cudaMemcpy2DAsync(d, dp, nbrs[k], (size_t)pitch, (size_t)W, (size_t)H,
-                                               cudaMemcpyHostToDevice, st), "host to device copy"));
+                                               cudaMemcpyHostToDevice, c->hp_h2d), "host to device copy"));
         dn[k] = d;
     }
-    float* dd = static_cast<float*>(dout);
-    float* dnrm = dd + npix;
-    float* dc = dnrm + 3 * npix;
+    FM_TRY(cuda_check(c, cudaEventRecord(c->hp_in[s], c->hp_h2d), "event"));
+    // the estimate: once the images are in and the previous use's maps are out
+    FM_TRY(cuda_check(c, cudaStreamWaitEvent(st, c->hp_in[s], 0), "wait"));
+    FM_TRY(cuda_check(c, cudaStreamWaitEvent(st, c->hp_out[s], 0), "wait"));
     FM_TRY(fassmvs_estimate(c, dimg, W, H, (int)dp, dn, n_nb, pl, dd, dnrm, dc, stream));
-    FM_TRY(cuda_check(c, cudaMemcpyAsync(depth, dd, sizeof(float) * npix, cudaMemcpyDeviceToHost, st),
+    FM_TRY(cuda_check(c, cudaEventRecord(c->hp_comp[s], st), "event"));
+    // the maps
+    FM_TRY(cuda_check(c, cudaStreamWaitEvent(c->hp_d2h, c->hp_comp[s], 0), "wait"));
+    FM_TRY(cuda_check(c, cudaMemcpyAsync(depth, dd, sizeof(float) * npix, cudaMemcpyDeviceToHost, c->hp_d2h),
                       "device to host copy"));
-    FM_TRY(cuda_check(c, cudaMemcpyAsync(normal, dnrm, sizeof(float) * 3 * npix, cudaMemcpyDeviceToHost, st),
+    FM_TRY(cuda_check(c, cudaMemcpyAsync(normal, dnrm, sizeof(float) * 3 * npix, cudaMemcpyDeviceToHost,
+                                         c->hp_d2h), "device to host copy"));
+    FM_TRY(cuda_check(c, cudaMemcpyAsync(conf, dc, sizeof(float) * npix, cudaMemcpyDeviceToHost, c->hp_d2h),
                       "device to host copy"));
-    FM_TRY(cuda_check(c, cudaMemcpyAsync(conf, dc, sizeof(float) * npix, cudaMemcpyDeviceToHost, st),
-                      "device to host copy"));
-    return cuda_check(c, cudaStreamSynchronize(st), "estimate_host");
+    FM_TRY(cuda_check(c, cudaEventRecord(c->hp_out[s], c->hp_d2h), "event"));
+    c->hp_slot = s ^ 1;
+    *slot = s;
+    // the host images have been read
+    return cuda_check(c, cudaEventSynchronize(c->hp_in[s]), "host to device copy");
+}
+}  // namespace
+
+fassmvs_status fassmvs_estimate_host_async(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch,
+                                           const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* pl,
+                                           float* depth, float* normal, float* conf, void* stream)
+{
+    int slot = 0;
+    return estimate_host_enqueue(c, ref, W, H, pitch, nbrs, n_nb, pl, depth, normal, conf, stream, &slot);
+}
+
+fassmvs_status fassmvs_estimate_host(fassmvs_ctx* c, const uint8_t* ref, int W, int H, int pitch,
+                                     const uint8_t* const* nbrs, int n_nb, const fassmvs_planes* pl, float* depth,
+                                     float* normal, float* conf, void* stream)
+{
+    int slot = 0;
+    FM_TRY(estimate_host_enqueue(c, ref, W, H, pitch, nbrs, n_nb, pl, depth, normal, conf, stream, &slot));
+    // the maps copies run in order on one stream: this call's are the last
+    return cuda_check(c, cudaEventSynchronize(c->hp_out[slot]), "device to host copy");
 }
 
 fassmvs_status fassmvs_profile_enable(fassmvs_ctx* c, int on)

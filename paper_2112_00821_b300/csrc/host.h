@@ -48,6 +48,13 @@ struct fassmvs_ctx {
     size_t host_cap = 0;
     cudaEvent_t arena_ev[2] = {nullptr, nullptr};
     int arena_half = 0;
+    // host-buffer estimates: two device slots of images and maps, a copy
+    // stream each way, and per slot the events "images copied", "estimate
+    // done" and "maps copied"
+    cudaStream_t hp_h2d = nullptr, hp_d2h = nullptr;
+    cudaEvent_t hp_in[2] = {nullptr, nullptr}, hp_comp[2] = {nullptr, nullptr}, hp_out[2] = {nullptr, nullptr};
+    int hp_slot = 0;
+    size_t hp_slot_bytes = 0;
     // per-frame scratch from the caller (the serving form) instead of by name
     fassmvs_status (*scratch_fn)(void* user, int frame, const char* name, size_t bytes, void** out) = nullptr;
     void* scratch_user = nullptr;

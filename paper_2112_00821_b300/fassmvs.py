@@ -94,6 +94,7 @@ _SIGS = {
     "fassmvs_set_cameras": [_VP, _VP, C.c_int, _VP, _VP, _VP],
     "fassmvs_estimate": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP],
     "fassmvs_estimate_host": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP],
+    "fassmvs_estimate_host_async": [_VP, _VP, C.c_int, C.c_int, C.c_int, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP],
     "fassmvs_pyramid_down": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
     "fassmvs_census": [_VP, _VP, C.c_int, C.c_int, _VP, _VP],
     "fassmvs_cost_volume": [_VP, _VP, _VP, C.c_int, _VP, C.c_int, C.c_int, _VP, _VP, _VP, _VP,
@@ -249,11 +250,13 @@ class Context:
                                            _stream()))
         return depth, normal, conf
 
-    def estimate_host(self, ref, nbrs, planes, depth=None, normal=None, conf=None):
-        """The estimate from host images to host maps (fassmvs_estimate_host):
-        ref and nbrs are CPU uint8 tensors (page-locked or not) of one layout;
-        depth / normal / conf are CPU float32 tensors (allocated here when
-        absent).  Returns once the maps are in them."""
+    def estimate_host(self, ref, nbrs, planes, depth=None, normal=None, conf=None, wait=True):
+        """The estimate from host images to host maps: ref and nbrs are CPU
+        uint8 tensors (page-locked or not) of one layout; depth / normal / conf
+        are CPU float32 tensors (allocated here when absent).  wait: return
+        once the maps are in them (fassmvs_estimate_host); otherwise once the
+        images are copied, the maps following by the next sync() or waiting
+        call (fassmvs_estimate_host_async)."""
         import torch
         H, W = ref.shape
         pitch = ref.stride(0)
@@ -268,10 +271,10 @@ class Context:
             if t.device.type != "cpu" or t.dtype != torch.float32 or tuple(t.shape) != shp or not t.is_contiguous():
                 raise ValueError("outputs must be contiguous CPU float32 tensors of the map shapes")
         arr = (C.c_void_p * len(nbrs))(*[x.data_ptr() for x in nbrs])
-        self._check(lib().fassmvs_estimate_host(self._h, C.c_void_p(ref.data_ptr()), W, H, pitch, arr, len(nbrs),
-                                                C.byref(planes), C.c_void_p(depth.data_ptr()),
-                                                C.c_void_p(normal.data_ptr()), C.c_void_p(conf.data_ptr()),
-                                                _stream()))
+        fn = lib().fassmvs_estimate_host if wait else lib().fassmvs_estimate_host_async
+        self._check(fn(self._h, C.c_void_p(ref.data_ptr()), W, H, pitch, arr, len(nbrs), C.byref(planes),
+                       C.c_void_p(depth.data_ptr()), C.c_void_p(normal.data_ptr()), C.c_void_p(conf.data_ptr()),
+                       _stream()))
         return depth, normal, conf
 
     # ------------------------------------------------------------ batched form

@@ -1,7 +1,9 @@
-"""The estimate from host images to host maps (fassmvs_estimate_host) equals
-the estimate on device copies of the same images, bit for bit: page-locked
-and pageable host memory, a row pitch wider than the image and a width that
-is not a multiple of 16 (the device copies are padded to 16-byte rows)."""
+"""The estimate from host images to host maps (fassmvs_estimate_host and its
+pipelined form) equals the estimate on device copies of the same images, bit
+for bit: page-locked and pageable host memory, a row pitch wider than the
+image, a width that is not a multiple of 16 (the device copies are padded to
+16-byte rows), and sequences of frames whose copies overlap the kernels,
+with a change of image size inside the sequence."""
 import numpy as np
 import pytest
 
@@ -75,4 +77,33 @@ def test_host_estimate_rejects_bad_arguments(scene):
         c.estimate_host(ref, nbrs[:-1], fassmvs.planes_of(sc))          # view count differs from the cameras
     with pytest.raises(ValueError):
         c.estimate_host(ref.cuda(), nbrs, fassmvs.planes_of(sc))        # device tensors are not host images
+    c.close()
+
+
+def test_pipelined_sequence_equals_one_estimate_per_frame():
+    """Four frames through the pipelined call (two device slots, so the third
+    and fourth reuse them), a fifth of another size, then one sync."""
+    from paper_2112_00821_b300 import fassmvs, synth
+    scs = [synth.make_frame("planes", 70 + i, W=203, H=141, G0=64, n_left=2, n_right=1) for i in range(4)]
+    scs.append(synth.make_frame("planes", 75, W=160, H=120, G0=64, n_left=2, n_right=1))
+    exp = []
+    for sc in scs:
+        c = _ctx(sc)
+        exp.append(_device_estimate(c, sc))
+        c.close()
+    c = _ctx(scs[0])
+    outs = []
+    for sc in scs:
+        c.set_cameras(sc.K, sc.R, sc.t, sc.side)
+        ref = torch.from_numpy(sc.ref).pin_memory()
+        nbrs = [torch.from_numpy(x).pin_memory() for x in sc.nbrs]
+        H, W = sc.ref.shape
+        o = (torch.empty((H, W)).pin_memory(), torch.empty((H, W, 3)).pin_memory(), torch.empty((H, W)).pin_memory())
+        c.estimate_host(ref, nbrs, fassmvs.planes_of(sc), *o, wait=False)
+        del ref, nbrs                      # the images have been copied when the call returns
+        outs.append(o)
+    c.sync()
+    for o, e in zip(outs, exp):
+        for g, x in zip(o, e):
+            assert torch.equal(g, x)
     c.close()
