@@ -196,6 +196,16 @@ def _cores():
         return os.cpu_count()
 
 
+def _cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def cpu_baseline(seed, reps=3):
     tot_v, tot_t = 0, 0.0
     for _ in range(reps):
@@ -203,6 +213,7 @@ def cpu_baseline(seed, reps=3):
         tot_v += v
         tot_t += t
     return {"value": round(tot_v / tot_t / 1e6, 3), "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "cpu_model": _cpu_model(),
             "sample": "full 4-level estimate of a centred 480x270 crop of the 1920x1080 frame "
                       "(same planes, views and settings), %d run(s), %.1f s" % (reps, tot_t)}
 
@@ -226,6 +237,7 @@ def run_reference(a):
             "config": {"workload": WORKLOAD, "sample": "centred 480x270 crop per step", "levels": 4,
                        "planes_finest": 256, "views": 5, "variant": "path-gradient", "paths": 8},
             "cpu_baseline": {"value": round(val, 3), "unit": UNIT, "cores": _cores(), "kind": "oracle",
+                             "cpu_model": _cpu_model(),
                              "sample": "centred 480x270 crop of the frame, full estimate per step"},
             "e2e": {"value": round(val, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -353,6 +365,12 @@ def run_ours(a):
               "peak": hbm, "unit": "GB/s", "frac": round(sgm_ach / hbm, 4),
               "peak_source": "measured" if peaks else "fallback",
               "traffic": _traffic("sgm_batch_dir_kernel", sum(w * h * d for w, h, d in lv) / len(lv))}
+    if rl_sgm["traffic"] and sgm_ms > 0:
+        # the same launches on their real DRAM traffic (the design moves more
+        # than the 4 B algorithmic minimum per voxel)
+        real = rl_sgm["traffic"] * sgm_n / (sgm_ms * 1e-3) / 1e9
+        rl_sgm["traffic_achieved"] = round(real, 1)
+        rl_sgm["traffic_frac"] = round(real / hbm, 4)
     dominant = rl_cost if cost_ms >= sgm_ms else rl_sgm
     step_ms = {k: round(v[0] / a.steps, 3) for k, v in stages.items()}
     line = {

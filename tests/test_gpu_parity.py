@@ -107,6 +107,41 @@ def test_cost_volume_tiny_scene_vs_fp64(ctx, orc):
     assert diff <= 1e-4, diff
 
 
+def test_cost_volume_points_behind_a_neighbour(ctx, orc):
+    """A neighbour turned 75 degrees about the vertical axis sees part of
+    every plane behind it (homogeneous w <= 0): those samples take the
+    behind-the-camera position of the sampling reading and the views whose
+    centre sample lies there are invalid.  Both the stage entry point (global
+    taps) and the estimate's level-0 volume (staged taps, a box that cannot be
+    planned for such pairs) against the oracle."""
+    from paper_2112_00821_b300 import fassmvs, synth
+    sc = synth.make_frame("planes", 81, W=120, H=90, G0=24, n_left=1, n_right=2)
+    a = math.radians(75.0)
+    R = np.array(sc.R, dtype=np.float64).copy()
+    R[1] = [[math.cos(a), 0.0, math.sin(a)], [0.0, 1.0, 0.0], [-math.sin(a), 0.0, math.cos(a)]]
+    sc.R = R
+    # precondition: some pixel of some plane lies behind the turned view
+    Ki = np.linalg.inv(sc.K)
+    ys, xs = np.mgrid[0:90, 0:120]
+    rays = np.stack([xs, ys, np.ones_like(xs)], -1).reshape(-1, 3) @ Ki.T
+    behind = 0
+    for g in (0, 23):
+        X = rays / (sc.rho_far + g * sc.drho)
+        behind += int(np.sum((X @ R[1].T + sc.t[1])[:, 2] <= 0))
+    assert behind > 100
+    got, exp = _scene_cost(ctx, orc, sc, 24)
+    assert np.mean(got != exp) <= 1e-4
+    c = fassmvs.Context(fassmvs.default_config(levels=1, D=[24], paths=8, variant=0, p1=24))
+    c.set_cameras(sc.K, sc.R, sc.t, sc.side)
+    c.debug_capture(0)
+    c.estimate(dev(sc.ref), [dev(x) for x in sc.nbrs], fassmvs.planes_of(sc))
+    vol, _ = c.debug_dump(0, "cost")
+    c.sync()
+    est = host(vol, np.uint16)[..., :24]
+    c.close()
+    assert np.mean(est != exp) <= 1e-4
+
+
 @pytest.mark.parametrize("nl,nr", [(2, 3), (1, 0), (3, 1)])
 def test_cost_volume_ragged_unequal_subsets_windows(ctx, orc, nl, nr):
     from paper_2112_00821_b300 import synth
