@@ -113,13 +113,17 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
         cp_async_commit();
     }
 
+    // element offsets of the step's pixel and of the step PF ahead; a step moves
+    // them by dstep
+    const ptrdiff_t dstep = ((ptrdiff_t)dy * W + dx) * (ptrdiff_t)a.pstride;
+    ptrdiff_t off = (ptrdiff_t)(((size_t)y0 * W + x0) * a.pstride + soff);
+    ptrdiff_t pf_off = off + PF * dstep;
     for (int base = 0; base < n; base += PF) {
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
             const int step = base + u;
             if (step >= n) break;              // warp-uniform
             const int x = x0 + step * dx, y = y0 + step * dy;
-            const size_t pix = (size_t)y * W + x;
             const int lo_p = __shfl_sync(FULL, q.lo, u);
             const int pk = __shfl_sync(FULL, (q.ipix & 0xFF) | (q.dsn * 256), u);
             const int cur_ipix = pk & 0xFF, cur_dsn = pk >> 8;
@@ -129,10 +133,9 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
             __syncwarp();
             if (step + PF < n) {
                 const int xx = x + PF * dx, yy = y + PF * dy;
-                const size_t pp = ((size_t)yy * W + xx) * a.pstride + soff;
                 if (act) {
-                    cp_async16(&rg[u][0][lane], a.S + pp);
-                    if (!first) cp_async16(&rg[u][1][lane], Sb + pp);
+                    cp_async16(&rg[u][0][lane], a.S + pf_off);
+                    if (!first) cp_async16(&rg[u][1][lane], Sb + pf_off);
                 }
                 if (lane == u) load_scal(a, r, xx, yy, q);
             }
@@ -233,8 +236,10 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
                     o = make_uint4(acc.x + (L[0] & vmask[0]), acc.y + (L[1] & vmask[1]),
                                    acc.z + (L[2] & vmask[2]), acc.w + (L[3] & vmask[3]));
                 }
-                *reinterpret_cast<uint4*>(Sb + pix * a.pstride + soff) = o;
+                *reinterpret_cast<uint4*>(Sb + off) = o;
             }
+            off += dstep;
+            pf_off += dstep;
 #pragma unroll
             for (int j = 0; j < 4; ++j) Lp[j] = L[j];
             lo_prev = lo_p;
