@@ -123,10 +123,6 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
     if (gwin) gwin[p] = g;
 }
 
-// ---------------------------------------------------------------- volume relayout
-// [Ds / 16][np][16] -> [np][Ds]: warp w moves pixels 32 w .. 32 w + 31, lane l
-// pixel 32 w + l; per 16-plane block the warp reads 1 KB contiguous and every
-// lane writes one whole 32-byte sector of its pixel's row.
 // sum of the aggregation's partial sums (debug capture): out[i] = sum_p Sbar[p * stride + i]
 __global__ void sum_parts_kernel(const uint16_t* __restrict__ Sbar, int parts, size_t stride, size_t n,
                                  uint16_t* __restrict__ out)
@@ -138,18 +134,29 @@ __global__ void sum_parts_kernel(const uint16_t* __restrict__ Sbar, int parts, s
     out[i] = (uint16_t)v;
 }
 
-__global__ void relayout16_kernel(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst, size_t np,
-                                  int Ds)
+// ---------------------------------------------------------------- volume relayout
+// [Ds / 16][np][16] -> [np][Ds], 32 pixels per block of 256 threads: their
+// 16-plane blocks are read coalesced (1 KB per block index) into shared
+// memory, then written back pixel-major as one contiguous run of 32 x Ds
+// planes.  Shared rows are 66 uint4 apart, so that the four pairs of uint4 a
+// quarter-warp reads on the way out fall in different banks.
+constexpr int kRelPix = 32, kRelRow = 66;
+__global__ void __launch_bounds__(256) relayout16_kernel(const uint16_t* __restrict__ src,
+                                                         uint16_t* __restrict__ dst, size_t np, int Ds)
 {
-    const size_t p = ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
-    if (p >= np) return;
-    const uint4* s = reinterpret_cast<const uint4*>(src + p * 16);
-    uint4* d = reinterpret_cast<uint4*>(dst + p * (size_t)Ds);
-    const size_t bs = np * 2;                  // block stride in uint4
-    for (int b = 0; b < Ds / 16; ++b) {
-        const uint4 v0 = __ldcs(s + b * bs), v1 = __ldcs(s + b * bs + 1);
-        d[2 * b] = v0;
-        d[2 * b + 1] = v1;
+    __shared__ uint4 sm[kMaxSlots / 16][kRelRow];
+    const size_t p0 = (size_t)blockIdx.x * kRelPix;
+    const int npx = (int)min((size_t)kRelPix, np - p0);
+    const int nb = Ds / 16, per = 2 * nb;      // uint4 per pixel
+    for (int i = threadIdx.x; i < nb * 2 * kRelPix; i += blockDim.x) {
+        const int b = i / (2 * kRelPix), j = (i >> 1) & (kRelPix - 1), h = i & 1;
+        if (j < npx) sm[b][2 * j + h] = __ldcs(reinterpret_cast<const uint4*>(src + ((size_t)b * np + p0 + j) * 16) + h);
+    }
+    __syncthreads();
+    uint4* d = reinterpret_cast<uint4*>(dst + p0 * (size_t)Ds);
+    for (int i = threadIdx.x; i < npx * per; i += blockDim.x) {
+        const int j = i / per, k = i - j * per;
+        d[i] = sm[k >> 1][2 * j + (k & 1)];
     }
 }
 
@@ -365,7 +372,7 @@ void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, in
 void launch_relayout16(const uint16_t* src, uint16_t* dst, size_t np, int Ds, cudaStream_t st)
 {
     if (np == 0) return;
-    relayout16_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(src, dst, np, Ds);
+    relayout16_kernel<<<(unsigned)((np + kRelPix - 1) / kRelPix), 256, 0, st>>>(src, dst, np, Ds);
     count_launch();
 }
 
