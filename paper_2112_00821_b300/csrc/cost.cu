@@ -667,6 +667,9 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         }
         // -------------------------------------------------------------- store
         if (do_cost && tx0 + pc < W) {
+            // the chunk's pixels are W * pstride elements apart, row by row
+            size_t roff = ((size_t)(ty0 + pr0) * W + tx0 + pc) * a.pstride;
+            const size_t rstride = (size_t)W * a.pstride;
 #pragma unroll
             for (int r = 0; r < CH; ++r) {
                 const int py = ty0 + pr0 + r;
@@ -677,9 +680,10 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     // (x * ceil(2^32 / n)) >> 32 == x / n exactly for x < 2^16, n <= 16
                     if (a.nL > 0) vl = (uint32_t)(((uint64_t)(sl * a.nmax + (a.nL >> 1)) * a.mL) >> 32);
                     if (a.nR > 0) vr = (uint32_t)(((uint64_t)(sr * a.nmax + (a.nR >> 1)) * a.mR) >> 32);
-                    a.S[((size_t)py * W + tx0 + pc) * a.pstride + (size_t)(s >> a.bshift) * a.bstride +
-                        (s & ((1 << a.bshift) - 1))] = (uint16_t)min(vl, vr);
+                    a.S[roff + (size_t)(s >> a.bshift) * a.bstride + (s & ((1 << a.bshift) - 1))] =
+                        (uint16_t)min(vl, vr);
                 }
+                roff += rstride;
             }
         }
     }

@@ -25,11 +25,12 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 // The data costs and running aggregate of the pixel PF steps down the line
 // are copied into a per-warp shared ring with cp.async (each lane its own 16
 // bytes, so a per-thread wait suffices); the small per-pixel values (window
-// start, image value, surface-normal jump) are prefetched in registers.  A
-// short ring and at most 80 registers let six CTAs (24 warps, i.e. 24 path
-// lines) share an SM: more lines in flight hide the step-to-step latency
-// better than a deeper prefetch (measured: PF 4 / 6 CTAs 15 % faster than
-// PF 8 / 4 CTAs on the 1080p estimate).
+// start, image value, surface-normal jump) are prefetched in registers, a
+// block of PF steps at a time.  A short ring and at most 80 registers (71
+// used) let six or more CTAs (24 warps, i.e. 24 path lines) share an SM: more
+// lines in flight hide the step-to-step latency better than a deeper
+// prefetch (measured: PF 4 / 6 CTAs 15 % faster than PF 8 / 4 CTAs on the
+// 1080p estimate).
 constexpr int PF = 4;
 
 struct StepScal {
@@ -98,8 +99,10 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
     // per-step scalars (window start, intensity, index jump) are fetched PF
     // steps ahead and spread over the lanes: lane u holds those of the steps
     // congruent to u modulo PF, broadcast when the step comes
-    StepScal q{0, 0, 0};
-    if (lane < PF && lane < n) load_scal(a, r, x0 + lane * dx, y0 + lane * dy, q);
+    // (double-buffered: at the start of each block of PF steps lanes 0 .. PF-1
+    // fetch the next block's, so that one lane-divergent load serves PF steps)
+    StepScal q{0, 0, 0}, qn{0, 0, 0};
+    if (lane < PF && lane < n) load_scal(a, r, x0 + lane * dx, y0 + lane * dy, qn);
 #pragma unroll
     for (int u = 0; u < PF; ++u) {
         if (u < n) {
@@ -119,11 +122,13 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
     ptrdiff_t off = (ptrdiff_t)(((size_t)y0 * W + x0) * a.pstride + soff);
     ptrdiff_t pf_off = off + PF * dstep;
     for (int base = 0; base < n; base += PF) {
+        q = qn;
+        if (lane < PF && base + PF + lane < n)
+            load_scal(a, r, x0 + (base + PF + lane) * dx, y0 + (base + PF + lane) * dy, qn);
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
             const int step = base + u;
             if (step >= n) break;              // warp-uniform
-            const int x = x0 + step * dx, y = y0 + step * dy;
             const int lo_p = __shfl_sync(FULL, q.lo, u);
             const int pk = __shfl_sync(FULL, (q.ipix & 0xFF) | (q.dsn * 256), u);
             const int cur_ipix = pk & 0xFF, cur_dsn = pk >> 8;
@@ -131,13 +136,9 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
             const uint4 sraw = rg[u][0][lane];
             const uint4 acc = rg[u][1][lane];
             __syncwarp();
-            if (step + PF < n) {
-                const int xx = x + PF * dx, yy = y + PF * dy;
-                if (act) {
-                    cp_async16(&rg[u][0][lane], a.S + pf_off);
-                    if (!first) cp_async16(&rg[u][1][lane], Sb + pf_off);
-                }
-                if (lane == u) load_scal(a, r, xx, yy, q);
+            if (step + PF < n && act) {
+                cp_async16(&rg[u][0][lane], a.S + pf_off);
+                if (!first) cp_async16(&rg[u][1][lane], Sb + pf_off);
             }
             cp_async_commit();
             const uint32_t Sv[4] = {sraw.x, sraw.y, sraw.z, sraw.w};
