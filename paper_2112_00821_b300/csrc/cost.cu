@@ -331,8 +331,11 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
 
 // One tile (bx, by) of one frame, plane chunk bz of nz, with the census (NCC
 // false) or NCC 5x5 cost.  Called by the single-frame grid kernel and by the
-// multi-frame kernel.
-template <bool NCC>
+// multi-frame kernel.  ROWSTEP: the volume stores step a 64-bit offset from
+// row to row (fewer instructions; the multi-frame kernel, whose arguments sit
+// in shared memory, has the registers for it, the single-frame one would
+// spill).
+template <bool NCC, bool ROWSTEP>
 __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int bz, int nz, SmemCost& sm,
                                           uint8_t* stg, uint32_t& phase)
 {
@@ -668,8 +671,8 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         // -------------------------------------------------------------- store
         if (do_cost && tx0 + pc < W) {
             // the chunk's pixels are W * pstride elements apart, row by row
-            size_t roff = ((size_t)(ty0 + pr0) * W + tx0 + pc) * a.pstride;
-            const size_t rstride = (size_t)W * a.pstride;
+            size_t roff = ROWSTEP ? ((size_t)(ty0 + pr0) * W + tx0 + pc) * a.pstride : 0;
+            const size_t rstride = ROWSTEP ? (size_t)W * a.pstride : 0;
 #pragma unroll
             for (int r = 0; r < CH; ++r) {
                 const int py = ty0 + pr0 + r;
@@ -680,7 +683,8 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     // (x * ceil(2^32 / n)) >> 32 == x / n exactly for x < 2^16, n <= 16
                     if (a.nL > 0) vl = (uint32_t)(((uint64_t)(sl * a.nmax + (a.nL >> 1)) * a.mL) >> 32);
                     if (a.nR > 0) vr = (uint32_t)(((uint64_t)(sr * a.nmax + (a.nR >> 1)) * a.mR) >> 32);
-                    a.S[roff + (size_t)(s >> a.bshift) * a.bstride + (s & ((1 << a.bshift) - 1))] =
+                    const size_t poff = ROWSTEP ? roff : ((size_t)py * W + tx0 + pc) * a.pstride;
+                    a.S[poff + (size_t)(s >> a.bshift) * a.bstride + (s & ((1 << a.bshift) - 1))] =
                         (uint16_t)min(vl, vr);
                 }
                 roff += rstride;
@@ -696,7 +700,7 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
     SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
     stage_init(sm);
     uint32_t phase = 0;
-    cost_tile<NCC>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm, nullptr, phase);
+    cost_tile<NCC, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm, nullptr, phase);
 }
 
 // Batched form: work items (frame, tile x, tile y, chunk | chunks << 16) of
@@ -732,7 +736,7 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
             for (int i = threadIdx.x; i < (int)(sizeof(CostArgs) / sizeof(int)); i += THREADS) dst[i] = src[i];
         }
         __syncthreads();
-        cost_tile<NCC>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm, stg, phase);
+        cost_tile<NCC, true>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm, stg, phase);
         __syncthreads();
         if (!counter) break;
     }
