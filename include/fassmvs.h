@@ -209,7 +209,9 @@ FASSMVS_API fassmvs_status fassmvs_set_graph(fassmvs_ctx* ctx, int on);
 
 /* Work decomposition of the batched form; no setting changes any result.
  *   chunk_planes  planes per work item of the persistent cost kernel, 1..256,
- *                 or 0: enough items for about three waves (chunks >= 8)
+ *                 or 0: automatic, at least about three waves of items
+ *                 (chunks >= 8 planes), the count up to twice that whose
+ *                 items fill their last wave best
  *   ctas_per_sm   persistent cost CTAs per SM, 1 or 2, or 0: one short-lived
  *                 CTA per work item (lets stream priorities act per CTA)
  *   sgm_parts     partial sums of the aggregation, 1, 2, 4 or 8 (at most the

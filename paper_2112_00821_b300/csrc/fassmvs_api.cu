@@ -933,15 +933,32 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
         std::sort(order.begin(), order.end(), [&](int x, int y) {
             return (long long)fr[x].V * fr[x].D * fr[x].w * fr[x].h > (long long)fr[y].V * fr[y].D * fr[y].w * fr[y].h;
         });
-        // plane chunks per tile: fixed size, or (automatic) enough items for
-        // about three waves of the persistent CTAs, chunks of at least 8 planes
+        // plane chunks per tile: fixed size, or (automatic) at least about
+        // three waves of the persistent CTAs, chunks of at least 8 planes
         long long tiles = 0;
         for (int f = 0; f < n; ++f) tiles += (long long)fm::cost_tiles_x(fr[f].w) * fm::cost_tiles_y(fr[f].h);
         const int auto_nz = (int)std::max(1LL, (3LL * wave + tiles - 1) / tiles);
+        // automatic: from auto_nz up to twice that (chunks of >= 8 planes), the
+        // count whose items fill their last wave of persistent CTAs best
+        auto fill = [&](long long items) {
+            const long long w = (items + wave - 1) / wave;
+            return (double)items / (double)(w * wave);
+        };
+        int best_nz = auto_nz;
+        {
+            int dmax = 1;
+            for (int f = 0; f < n; ++f) dmax = std::max(dmax, fr[f].D);
+            const int hi = std::max(1, std::min(2 * auto_nz, (dmax + 7) / 8));
+            double bf = -1.0;
+            for (int z = std::min(auto_nz, hi); z <= hi; ++z) {
+                const double q = fill(tiles * z);
+                if (q > bf + 0.02) { bf = q; best_nz = z; }
+            }
+        }
         for (int f : order) {
             const FrameRun& F = fr[f];
             const int nz = chunk_planes > 0 ? std::max(1, (F.D + chunk_planes - 1) / chunk_planes)
-                                            : std::max(1, std::min(auto_nz, (F.D + 7) / 8));
+                                            : std::max(1, std::min(best_nz, (F.D + 7) / 8));
             const int tx = fm::cost_tiles_x(F.w), ty = fm::cost_tiles_y(F.h);
             for (int z = 0; z < nz; ++z)
                 for (int y = 0; y < ty; ++y)
