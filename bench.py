@@ -212,10 +212,21 @@ def cpu_baseline(seed, reps=3):
         v, t = oracle_sample(seed)
         tot_v += v
         tot_t += t
-    return {"value": round(tot_v / tot_t / 1e6, 3), "unit": UNIT, "cores": _cores(), "kind": "oracle",
-            "cpu_model": _cpu_model(),
-            "sample": "full 4-level estimate of a centred 480x270 crop of the 1920x1080 frame "
-                      "(same planes, views and settings), %d run(s), %.1f s" % (reps, tot_t)}
+    out = {"value": round(tot_v / tot_t / 1e6, 3), "unit": UNIT, "cores": _cores(), "kind": "oracle",
+           "cpu_model": _cpu_model(),
+           "sample": "full 4-level estimate of a centred 480x270 crop of the 1920x1080 frame "
+                     "(same planes, views and settings), %d run(s), %.1f s" % (reps, tot_t)}
+    # the same oracle on one thread, on a smaller crop
+    import oracle
+    n0 = oracle.threads()
+    oracle.threads(1)
+    try:
+        v1, t1 = oracle_sample(seed, crop=(240, 136))
+    finally:
+        oracle.threads(n0)
+    out["single_thread"] = {"value": round(v1 / t1 / 1e6, 3), "unit": UNIT, "cores": 1,
+                            "sample": "full 4-level estimate of a centred 240x136 crop, 1 run, %.1f s" % t1}
+    return out
 
 
 def run_reference(a):

@@ -58,6 +58,8 @@ def lib():
         _lib.or_estimate.restype = C.c_int
         _lib.or_plane_bounds.restype = C.c_int
         _lib.or_cross_ratio_planes.restype = C.c_int
+        _lib.or_threads.restype = C.c_int
+        _lib.or_threads.argtypes = [C.c_int]
     return _lib
 
 
@@ -355,3 +357,9 @@ def estimate(scene, cfg):
     if rc != 0:
         raise ValueError("or_estimate rc=%d" % rc)
     return depth, normal, conf
+
+
+def threads(n=0):
+    """Thread count of the oracle's parallel loops (timing only); n >= 1 sets
+    it.  Returns the count in force."""
+    return int(lib().or_threads(int(n)))

@@ -29,6 +29,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_EXPORT __attribute__((visibility("default")))
 
@@ -44,6 +47,20 @@
 /* pixel (x, y) is the blurred input at (2x, 2y) with clamp-to-edge, rounded */
 /* half up after dividing by 2^16; the output size is ceil(W/2) x ceil(H/2). */
 /* ------------------------------------------------------------------------ */
+/* Thread count of the parallel loops over independent pixels and lines
+   (timing only: no result depends on it).  n >= 1 sets it, 0 leaves it;
+   returns the count in force. */
+OR_EXPORT int or_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 OR_EXPORT void or_pyr_weights(int32_t w[3])
 {
     double g1 = exp(-0.5), g0 = 1.0;

@@ -896,3 +896,22 @@ def test_dsn_with_a_slanted_sweep_normal_matches_the_plane_index_step(orc):
                     assert di[r, y, x] == int(math.copysign(math.floor(abs(ex) + 0.5), ex)), (mv, nv, r, x, y)
                     nonzero += di[r, y, x] != 0
             assert nonzero > 0                                    # a slanted sweep sees steps even on fronto planes
+
+
+def test_oracle_results_do_not_depend_on_its_thread_count():
+    """The oracle's parallel loops run over independent pixels and lines: one
+    thread and all threads give the same estimate, bit for bit."""
+    import oracle
+    from paper_2112_00821_b300 import synth
+    sc, cfg = synth.workload("tiny_160x120_g64", 0, want_gt=False)
+    oc = oracle.make_config(**cfg)
+    many = oracle.estimate(sc, oc)
+    n0 = oracle.threads()
+    oracle.threads(1)
+    try:
+        assert oracle.threads() == 1
+        one = oracle.estimate(sc, oc)
+    finally:
+        oracle.threads(n0)
+    for x, y in zip(many, one):
+        assert np.array_equal(x, y)
