@@ -485,7 +485,9 @@ FASSMVS_API fassmvs_status fassmvs_sgm_aggregate(fassmvs_ctx* ctx, const uint16_
  * (lowest slot on ties), parabola through the winner and its neighbours at
  * their plane distances (none at a window edge), clamped between them;
  * depth = -delta / (n^T K^-1 (x, y, 1)^T).  gwin (optional, int32 [H][W])
- * receives the winning plane index lo + s. */
+ * receives the winning plane index lo + s.  Every window start must satisfy
+ * 0 <= lo_p <= G - D (a start outside that range is clamped into the
+ * G-entry plane table, and its result is meaningless). */
 FASSMVS_API fassmvs_status fassmvs_wta_refine(fassmvs_ctx* ctx, const uint16_t* Sbar, const int32_t* lo, int W,
                                   int H, int D, int Ds, const double K[9], const double n[3],
                                   double rho0, double drho, int G, float* depth, int32_t* gwin,
@@ -499,9 +501,12 @@ FASSMVS_API fassmvs_status fassmvs_wta_refine(fassmvs_ctx* ctx, const uint16_t* 
  * takes no context and allocates nothing.  The plane-distance table it needs
  * lives in one static device array of FASSMVS_NOALLOC_MAX_PLANES floats
  * (16 KB, held by every device that loads the library until the process
- * exits); G beyond that limit returns FASSMVS_EINVAL.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * exits); G beyond that limit returns FASSMVS_EINVAL.  Every call looks up
+ * the array's device address (cudaGetSymbolAddress, a host-side lookup that
+ * allocates nothing) on the current device; the first call on a device can
+ * also load the library's device code there, so make that first call before
+ * any stream capture.  Window starts must satisfy 0 <= lo_p <= G - D, as for
+ * fassmvs_wta_refine.  All calls
  * share the array and it keeps the last call's table: calls that overlap on
  * the GPU (on different streams) race on it.  Runs on the current device.
  * The paper has no counterpart of this entry point. */

@@ -511,7 +511,7 @@ fassmvs_status fassmvs_wta_refine(fassmvs_ctx* c, const uint16_t* Sbar, const in
     FM_TRY(ensure(c, "delta_wta", sizeof(float) * (size_t)G, &delta));
     fm::launch_delta_table(rho0, drho, G, (float*)delta, S(stream));
     float nf[3] = {(float)n[0], (float)n[1], (float)n[2]};
-    fm::launch_wta_refine(Sbar, lo, W, H, D, Ds, (const float*)delta, intr(K), nf, depth, gwin, S(stream));
+    fm::launch_wta_refine(Sbar, lo, W, H, D, Ds, G, (const float*)delta, intr(K), nf, depth, gwin, S(stream));
     c->last = S(stream);
     return launch_status(c, "wta launch");
 }
@@ -1052,7 +1052,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             const float nf[3] = {(float)X.planes.n[0], (float)X.planes.n[1], (float)X.planes.n[2]};
             {
                 StageTimer tm(c, FASSMVS_STAGE_WTA, st);
-                fm::launch_wta_refine((const uint16_t*)F.pSb, (const int32_t*)F.plo, F.w, F.h, F.D, F.Ds,
+                fm::launch_wta_refine((const uint16_t*)F.pSb, (const int32_t*)F.plo, F.w, F.h, F.D, F.Ds, F.Gl,
                                       (const float*)F.delta, intr(F.Kl), nf,
                                       cfg.median5 ? (float*)F.pdraw : (float*)F.pdmed,
                                       dbg && f == 0 ? (int32_t*)dbg_gwin : nullptr, st, parts,

@@ -132,7 +132,7 @@ struct Intr {
 
 // Sbar may hold nparts partial sums, part_stride elements apart (summed here);
 // pstride / bstride / bshift as in CostArgs (pstride 0: the [H][W][Ds] layout)
-void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
+void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds, int G,
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
                        cudaStream_t st, int nparts = 1, size_t part_stride = 0, size_t pstride = 0,
                        size_t bstride = 0, int bshift = 3);

@@ -7,7 +7,6 @@
 // cost volume and the aggregation.
 #include <math.h>
 
-#include <mutex>
 
 #include "../../include/fassmvs.h"
 #include "fm_internal.cuh"
@@ -63,7 +62,7 @@ __global__ void census_kernel(const uint8_t* __restrict__ img, int W, int H, int
 // Sbar may be split into nparts partial sums (part_stride elements apart):
 // their packed pairs add without carries, as every total stays below 2^16.
 __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __restrict__ lo, int W,
-                           int H, int D, int Ds, const float* __restrict__ delta, Intr K, float n0,
+                           int H, int D, int Ds, int G, const float* __restrict__ delta, Intr K, float n0,
                            float n1, float n2, float* __restrict__ depth, int32_t* __restrict__ gwin,
                            int nparts, size_t part_stride, size_t pstride, size_t bstride, int bshift)
 {
@@ -104,11 +103,13 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
     vp = __shfl_sync(0xFFFFFFFFu, vp, sp >> 3);
     if (lane != 0) return;
     const int x = (int)(p % W), y = (int)(p / W);
-    const int g = (lo ? lo[p] : 0) + s;
+    // a window start with lo + D > G (a caller's map out of contract) stays
+    // inside the G-entry table
+    const int g = min(max((lo ? lo[p] : 0) + s, 0), G - 1);
     const float x0 = delta[g];
     float xs = x0;
     if (s > 0 && s < D - 1) {
-        const float xm = delta[g - 1], xp = delta[g + 1];
+        const float xm = delta[max(g - 1, 0)], xp = delta[min(g + 1, G - 1)];
         const float c0 = (float)(key >> 8), cm = (float)vm, cp = (float)vp;
         const float A = (x0 - xm) * (c0 - cp);
         const float B = (x0 - xp) * (c0 - cm);
@@ -351,7 +352,7 @@ void launch_census(const uint8_t* img, int W, int H, int pitch, uint64_t* out, c
     count_launch();
 }
 
-void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds,
+void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds, int G,
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,
                        cudaStream_t st, int nparts, size_t part_stride, size_t pstride, size_t bstride,
                        int bshift)
@@ -363,8 +364,8 @@ void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, in
     }
     size_t np = (size_t)W * H;
     int per = 8;
-    wta_kernel<<<(unsigned)((np + per - 1) / per), per * 32, 0, st>>>(Sbar, lo, W, H, D, Ds, delta, K, n[0],
-                                                                  n[1], n[2], depth, gwin, nparts,
+    wta_kernel<<<(unsigned)((np + per - 1) / per), per * 32, 0, st>>>(Sbar, lo, W, H, D, Ds, G, delta, K,
+                                                                  n[0], n[1], n[2], depth, gwin, nparts,
                                                                   part_stride, pstride, bstride, bshift);
     count_launch();
 }
@@ -432,21 +433,17 @@ void launch_dsn(const float* dc, const float* nc, int Wc, int Hc, int W, int H, 
 // shared by every call (see the header for the contract).
 namespace {
 static __device__ __align__(256) float g_noalloc_delta[FASSMVS_NOALLOC_MAX_PLANES];
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-float* g_noalloc_ptr[kMaxDevices] = {};
 
-// device address of the table on the current device, looked up once per device
-cudaError_t noalloc_table(int dev, float** out)
+// device address of the table in the module loaded by the current context.
+// Looked up on every call: it is a host-side lookup that allocates nothing,
+// and a cached address would dangle once the module is loaded again (after
+// cudaDeviceReset, or under another context on the same device).
+cudaError_t noalloc_table(float** out)
 {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_delta);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<float*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_delta);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<float*>(p);
     return cudaSuccess;
 }
 
@@ -470,18 +467,14 @@ extern "C" fassmvs_status fassmvs_wta_refine_noalloc(const uint16_t* Sbar, const
         return noalloc_fail(FASSMVS_EINVAL, "G exceeds the static plane table of the no-alloc entry point (4096)");
     if (reinterpret_cast<uintptr_t>(Sbar) & 15)
         return noalloc_fail(FASSMVS_EINVAL, "volume must be 16-byte aligned");
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return noalloc_fail(FASSMVS_ECUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(FASSMVS_EINVAL, "device index beyond 63");
     float* table = nullptr;
-    e = noalloc_table(dev, &table);
+    cudaError_t e = noalloc_table(&table);
     if (e != cudaSuccess) return noalloc_fail(FASSMVS_ECUDA, cudaGetErrorString(e));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     fm::launch_delta_table(rho0, drho, G, table, st);
     float nf[3] = {(float)n[0], (float)n[1], (float)n[2]};
     fm::Intr ki{(float)K[0], (float)K[4], (float)K[2], (float)K[5]};
-    fm::launch_wta_refine(Sbar, lo, W, H, D, Ds, table, ki, nf, depth, gwin, st);
+    fm::launch_wta_refine(Sbar, lo, W, H, D, Ds, G, table, ki, nf, depth, gwin, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return noalloc_fail(FASSMVS_ECUDA, cudaGetErrorString(e));
     return FASSMVS_OK;

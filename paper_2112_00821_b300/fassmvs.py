@@ -625,12 +625,20 @@ def wta_refine_noalloc(Sbar, D, K, n, rho0, drho, G, lo=None, depth=None, gwin=N
     allocating them here)."""
     import torch
     H, W, Ds = Sbar.shape
-    depth = depth if depth is not None else torch.empty((H, W), dtype=torch.float32, device=Sbar.device)
-    gwin = gwin if gwin is not None else torch.empty((H, W), dtype=torch.int32, device=Sbar.device)
+    dev = Sbar.device
+    if dev.type != "cuda":
+        raise ValueError("Sbar must be a CUDA tensor")
+    depth = depth if depth is not None else torch.empty((H, W), dtype=torch.float32, device=dev)
+    gwin = gwin if gwin is not None else torch.empty((H, W), dtype=torch.int32, device=dev)
+    for name, t in (("Sbar", Sbar), ("lo", lo), ("depth", depth), ("gwin", gwin)):
+        if t is not None and (t.device != dev or not t.is_contiguous()):
+            raise ValueError("%s must be a contiguous tensor on %s" % (name, dev))
     k_, kp = _dbl(K, 9)
     n_, npp = _dbl(n, 3)
-    st = lib().fassmvs_wta_refine_noalloc(_ptr(Sbar), _ptr(lo), W, H, int(D), Ds, kp, npp, rho0, drho,
-                                          int(G), _ptr(depth), _ptr(gwin), _stream())
+    # the library runs on the current device and stream: make them Sbar's
+    with torch.cuda.device(dev):
+        st = lib().fassmvs_wta_refine_noalloc(_ptr(Sbar), _ptr(lo), W, H, int(D), Ds, kp, npp, rho0, drho,
+                                              int(G), _ptr(depth), _ptr(gwin), _stream())
     if st != OK:
         raise FassmvsError(st, (lib().fassmvs_last_error(None) or b"").decode())
     return depth, gwin

@@ -48,6 +48,34 @@ def test_noalloc_wta_matches_allocating_entry_point_twice():
     ctx.close()
 
 
+def test_noalloc_wta_allocates_no_device_memory():
+    """The property the entry point exists for: with the outputs passed in and
+    the library's device code loaded by a first call, further calls (the
+    largest plane list included) leave the device's free memory unchanged."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_00821_b300 import fassmvs
+    n = [0.0, 0.0, -1.0]
+    cases = []
+    for seed, (H, W, D, G) in ((3, (40, 64, 32, 500)), (4, (24, 40, 64, 4096))):
+        Sb, lo, K, rho0, drho = _case(seed, H, W, D, G)
+        Sb_d = torch.from_numpy(Sb.view(np.int16)).cuda()
+        lo_d = torch.from_numpy(lo).cuda()
+        depth = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        gwin = torch.empty((H, W), dtype=torch.int32, device="cuda")
+        cases.append((Sb_d, D, K, rho0, drho, G, lo_d, depth, gwin))
+    # warm-up: loads the module on this device
+    c = cases[0]
+    fassmvs.wta_refine_noalloc(c[0], c[1], c[2], n, c[3], c[4], c[5], lo=c[6], depth=c[7], gwin=c[8])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        for Sb_d, D, K, rho0, drho, G, lo_d, depth, gwin in cases:
+            fassmvs.wta_refine_noalloc(Sb_d, D, K, n, rho0, drho, G, lo=lo_d, depth=depth, gwin=gwin)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_wta_rejects_plane_lists_beyond_the_static_table():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
