@@ -51,7 +51,7 @@ def lib():
         _lib.or_lr_combine.restype = C.c_uint16
         _lib.or_parabola_vertex.restype = C.c_double
         _lib.or_parabola_vertex.argtypes = [C.c_double] * 6
-        _lib.or_warp_sample.restype = C.c_int32
+        _lib.or_warp_sample.restype = C.c_double
         _lib.or_cost_volume.restype = C.c_int
         _lib.or_ncc_window.restype = C.c_int
         _lib.or_sgm_aggregate.restype = C.c_int
@@ -105,9 +105,11 @@ def homography(K, R, t, n, delta):
 
 
 def warp_image(img, Hm):
+    """Alg. 1 warp of a whole image: FP64 lerp-form bilinear values (not
+    rounded) and whether each position lies on the image grid."""
     img = _c(img, np.uint8)
     H, W = img.shape
-    out = np.zeros((H, W), np.int32)
+    out = np.zeros((H, W), np.float64)
     val = np.zeros((H, W), np.uint8)
     lib().or_warp_image(_p(img), W, H, _p(_c(Hm, np.float64).ravel()), _p(out), _p(val))
     return out, val.astype(bool)
@@ -118,10 +120,10 @@ def lr_combine(sL, nL, sR, nR):
 
 
 def ncc_window(a, b):
-    """NCC cost of two 5x5 windows (reference uint8 values, warped values at
-    16 x grey level), reading of Sec. 2.2.1 in fassmvs_oracle.c."""
-    a = _c(np.asarray(a).ravel(), np.int32)
-    b = _c(np.asarray(b).ravel(), np.int32)
+    """NCC cost of two 5x5 windows (reference grey levels, warped real
+    values), reading of Sec. 2.2.1 in fassmvs_oracle.c."""
+    a = _c(np.asarray(a, np.float64).ravel(), np.float64)
+    b = _c(np.asarray(b, np.float64).ravel(), np.float64)
     assert a.size == 25 and b.size == 25
     return lib().or_ncc_window(_p(a), _p(b))
 

@@ -113,10 +113,10 @@ OR_EXPORT void or_census_u8(const uint8_t* img, int W, int H, uint64_t* out)
         }
 }
 
-/* census over an int32 image (the warped neighbour patches) */
-static uint64_t census_i32_at(const int32_t* img, int W, int H, int x, int y)
+/* census over a warped image of real values (the warped neighbour patches) */
+static uint64_t census_f64_at(const double* img, int W, int H, int x, int y)
 {
-    int32_t c = img[(size_t)y * W + x];
+    double c = img[(size_t)y * W + x];
     uint64_t bits = 0;
     for (int dy = -3; dy <= 3; ++dy)
         for (int dx = -4; dx <= 4; ++dx) {
@@ -187,67 +187,58 @@ OR_EXPORT void or_homography(const double K[9], const double R[9], const double 
 /* ------------------------------------------------------------------------ */
 /* Alg. 1 (patch warping step): bringing the neighbour patch around H p into */
 /* the reference view is the same as sampling I_k at H q for every q of the */
-/* reference support window.  Reading of the sampling                       */
-/* (the paper does not fix it): positions are taken on a 1/256-pixel grid,  */
-/* P = floor(256 u) (as GPU texture units quantise bilinear weights), the    */
-/* bilinear blend is exact integer arithmetic with 8-bit weights, and the    */
-/* blended value is kept at 1/16 grey level, rounded half up:               */
-/* V = (blend + 2048) >> 12, in [0, 4080].  Positions are clamped to the    */
-/* image (clamp-to-edge).  A point behind the neighbour camera (homogeneous */
+/* reference support window.  Reading of the sampling (the paper does not   */
+/* fix it): the position (u, v) = H q is taken in FP64 without rounding,    */
+/* clamped to the image (clamp-to-edge), and the image is interpolated      */
+/* bilinearly in lerp form from the 2x2 pixels around it:                   */
+/*   top = I00 + a (I01 - I00), bottom = I10 + a (I11 - I10),                */
+/*   value = top + b (bottom - top),                                         */
+/* with a, b the offsets of the clamped position from the top-left pixel    */
+/* (equal corners give that grey level exactly).  The value is a real      */
+/* number, not rounded.  A point behind the neighbour camera (homogeneous   */
 /* w <= 0) is treated as lying at (-inf, -inf).                             */
 /* ------------------------------------------------------------------------ */
-#define OR_PMAX (1 << 24)
-
-static int64_t fixpos(double u)
-{
-    double s = floor(u * 256.0);
-    if (!(s > -(double)OR_PMAX)) return -OR_PMAX;     /* also catches NaN */
-    if (s > (double)OR_PMAX) return OR_PMAX;
-    return (int64_t)s;
-}
-
-/* position of reference pixel (x, y) in the neighbour, on the 1/256 grid;
-   returns 0 when the point is behind the neighbour camera */
-static int warp_pos(const double* Hm, int x, int y, int64_t* Pu, int64_t* Pv)
+/* position of reference pixel (x, y) in the neighbour; returns 0 when the
+   point is behind the neighbour camera */
+static int warp_pos(const double* Hm, int x, int y, double* u, double* v)
 {
     double a = Hm[0] * x + Hm[1] * y + Hm[2];
     double b = Hm[3] * x + Hm[4] * y + Hm[5];
     double w = Hm[6] * x + Hm[7] * y + Hm[8];
-    if (!(w > 0.0)) { *Pu = -OR_PMAX; *Pv = -OR_PMAX; return 0; }
-    *Pu = fixpos(a / w);
-    *Pv = fixpos(b / w);
+    if (!(w > 0.0)) { *u = -INFINITY; *v = -INFINITY; return 0; }
+    *u = a / w;
+    *v = b / w;
     return 1;
 }
 
-static int32_t bilinear_fix(const uint8_t* img, int W, int H, int64_t Pu, int64_t Pv)
+static double bilinear(const uint8_t* img, int W, int H, double u, double v)
 {
-    int64_t cu = Pu < 0 ? 0 : (Pu > 256LL * (W - 1) ? 256LL * (W - 1) : Pu);
-    int64_t cv = Pv < 0 ? 0 : (Pv > 256LL * (H - 1) ? 256LL * (H - 1) : Pv);
-    int iu = (int)(cu >> 8), iv = (int)(cv >> 8);
+    double cu = u > 0.0 ? (u < (double)(W - 1) ? u : (double)(W - 1)) : 0.0;   /* NaN -> 0 */
+    double cv = v > 0.0 ? (v < (double)(H - 1) ? v : (double)(H - 1)) : 0.0;
+    int iu = (int)floor(cu), iv = (int)floor(cv);
     if (iu > W - 2) iu = W - 2;
     if (iv > H - 2) iv = H - 2;
-    int A = (int)(cu - 256LL * iu), B = (int)(cv - 256LL * iv);
+    double a = cu - iu, b = cv - iv;
     const uint8_t* r0 = img + (size_t)iv * W + iu;
     const uint8_t* r1 = r0 + W;
-    int32_t top = r0[0] * (256 - A) + r0[1] * A;
-    int32_t bot = r1[0] * (256 - A) + r1[1] * A;
-    return (top * (256 - B) + bot * B + 2048) >> 12;
+    double top = r0[0] + a * ((double)r0[1] - r0[0]);
+    double bot = r1[0] + a * ((double)r1[1] - r1[0]);
+    return top + b * (bot - top);
 }
 
 /* value of the warped neighbour at reference pixel (x, y); *valid tells
    whether the (unclamped) position lies on the image grid */
-OR_EXPORT int32_t or_warp_sample(const uint8_t* img, int W, int H, const double Hm[9],
-                                 int x, int y, int32_t* valid)
+OR_EXPORT double or_warp_sample(const uint8_t* img, int W, int H, const double Hm[9], int x, int y,
+                                int32_t* valid)
 {
-    int64_t Pu, Pv;
-    int front = warp_pos(Hm, x, y, &Pu, &Pv);
-    if (valid)
-        *valid = front && Pu >= 0 && Pu <= 256LL * (W - 1) && Pv >= 0 && Pv <= 256LL * (H - 1);
-    return bilinear_fix(img, W, H, Pu, Pv);
+    double u, v;
+    int front = warp_pos(Hm, x, y, &u, &v);
+    if (valid) *valid = front && u >= 0.0 && u <= (double)(W - 1) && v >= 0.0 && v <= (double)(H - 1);
+    return bilinear(img, W, H, u, v);
 }
 
-OR_EXPORT void or_warp_image(const uint8_t* img, int W, int H, const double Hm[9],
-                             int32_t* out, uint8_t* valid)
+OR_EXPORT void or_warp_image(const uint8_t* img, int W, int H, const double Hm[9], double* out,
+                             uint8_t* valid)
 {
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
@@ -278,40 +269,37 @@ OR_EXPORT uint16_t or_lr_combine(uint32_t sL, int nL, uint32_t sR, int nR)
 /* ------------------------------------------------------------------------ */
 /* Sec. 2.2.1, the NCC alternative to the census (Sec. 3.4 selects a 5x5     */
 /* support region; the maximal cost is normalised to 255).  Reading: the     */
-/* correlation of the reference window a (uint8) and the warped window b     */
-/* (1/16 grey level, as for the census), ncc = cov / sqrt(var_a var_b),      */
+/* correlation coefficient of the reference window a (grey levels) and the   */
+/* warped window b (real values, as for the census),                         */
+/* ncc = sum (a - mean a)(b - mean b) / sqrt(sum (a - mean a)^2 sum (b - mean b)^2), */
 /* negated, truncated at zero correlation and scaled:                        */
 /* C = round_half_up(255 (1 - max(ncc, 0))); a flat window (zero variance)   */
-/* costs 255, as does an invalid view.  The window sums are exact integers;  */
-/* the last steps are single precision, each correctly rounded, in the       */
-/* order written here (floating point decides an integer cost).              */
+/* costs 255, as does an invalid view.                                       */
 /* ------------------------------------------------------------------------ */
-OR_EXPORT int or_ncc_window(const int32_t a[25], const int32_t b[25])
+OR_EXPORT int or_ncc_window(const double a[25], const double b[25])
 {
-    int64_t Sa = 0, Saa = 0, Sb = 0, Sbb = 0, Sab = 0;
+    double ma = 0.0, mb = 0.0;
+    for (int i = 0; i < 25; ++i) { ma += a[i]; mb += b[i]; }
+    ma /= 25.0;
+    mb /= 25.0;
+    double cov = 0.0, va = 0.0, vb = 0.0;
     for (int i = 0; i < 25; ++i) {
-        Sa += a[i];
-        Saa += (int64_t)a[i] * a[i];
-        Sb += b[i];
-        Sbb += (int64_t)b[i] * b[i];
-        Sab += (int64_t)a[i] * b[i];
+        cov += (a[i] - ma) * (b[i] - mb);
+        va += (a[i] - ma) * (a[i] - ma);
+        vb += (b[i] - mb) * (b[i] - mb);
     }
-    const int64_t cov = 25 * Sab - Sa * Sb;
-    const int64_t va = 25 * Saa - Sa * Sa;
-    const int64_t vb = 25 * Sbb - Sb * Sb;
-    if (va <= 0 || vb <= 0 || cov <= 0) return 255;
-    const float fa = (float)va, fb = (float)vb, fc = (float)cov;
-    const float ncc = fc / sqrtf(fa * fb);
-    const float c = 255.0f * (1.0f - ncc);
-    int ci = (int)floorf(c + 0.5f);
-    return ci < 0 ? 0 : (ci > 255 ? 255 : ci);
+    if (!(va > 0.0) || !(vb > 0.0)) return 255;
+    double ncc = cov / sqrt(va * vb);
+    if (ncc < 0.0) ncc = 0.0;
+    int c = (int)floor(255.0 * (1.0 - ncc) + 0.5);
+    return c < 0 ? 0 : (c > 255 ? 255 : c);
 }
 
 /* NCC cost of pixel (x, y): 5x5 windows with clamp-to-edge in the reference
-   grid over the reference image and the warped image (values 16 x grey). */
-static int ncc_at(const uint8_t* ref, const int32_t* wimg, int W, int H, int x, int y)
+   grid over the reference image and the warped image. */
+static int ncc_at(const uint8_t* ref, const double* wimg, int W, int H, int x, int y)
 {
-    int32_t a[25], b[25];
+    double a[25], b[25];
     int i = 0;
     for (int dy = -2; dy <= 2; ++dy)
         for (int dx = -2; dx <= 2; ++dx, ++i) {
@@ -358,7 +346,7 @@ OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int
     for (int k = 0; k < V; ++k) {
 #pragma omp parallel
         {
-            int32_t* wimg = (int32_t*)malloc(np * sizeof(int32_t));
+            double* wimg = (double*)malloc(np * sizeof(double));
             uint8_t* wval = (uint8_t*)malloc(np);
             double Hm[9];
 #pragma omp for schedule(dynamic, 1)
@@ -373,7 +361,7 @@ OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int
                         int h = cost ? 255 : 62;
                         if (wval[p])
                             h = cost ? ncc_at(ref, wimg, W, H, x, y)
-                                     : or_hamming(cref[p], census_i32_at(wimg, W, H, x, y));
+                                     : or_hamming(cref[p], census_f64_at(wimg, W, H, x, y));
                         if (side[k] < 0) sL[p * D + s] += (uint32_t)h;
                         else sR[p * D + s] += (uint32_t)h;
                     }
@@ -416,10 +404,10 @@ OR_EXPORT void or_cost_at(const uint8_t* ref, const uint8_t* const* nbrs, int V,
         for (int k = 0; k < V; ++k) {
             or_homography(K, R + 9 * k, t + 3 * k, n, plane_delta(rho0, drho, gs[i]), Hm);
             int32_t valid;
-            int32_t cen = or_warp_sample(nbrs[k], W, H, Hm, x, y, &valid);
+            double cen = or_warp_sample(nbrs[k], W, H, Hm, x, y, &valid);
             int h = cost ? 255 : 62;
             if (valid && cost) {
-                int32_t a[25], b[25];
+                double a[25], b[25];
                 int i = 0;
                 for (int dy = -2; dy <= 2; ++dy)
                     for (int dx = -2; dx <= 2; ++dx, ++i) {

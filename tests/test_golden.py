@@ -54,8 +54,8 @@ def test_oracle_ncc_window_and_range(orc):
     n = GOLD["ncc_window"][0] * GOLD["ncc_window"][1]
     g = np.random.default_rng(5)
     a = g.integers(0, 256, n)
-    assert orc.ncc_window(a, 16 * a) == 0                           # perfect correlation
-    assert orc.ncc_window(a, 16 * (255 - a)) == GOLD["ncc_max_cost"]  # anti-correlated: truncated
+    assert orc.ncc_window(a, a) == 0                                # perfect correlation
+    assert orc.ncc_window(a, 255 - a) == GOLD["ncc_max_cost"]       # anti-correlated: truncated
 
 
 def test_geometric_filter_defaults_are_the_papers(orc, fm):
