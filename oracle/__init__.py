@@ -53,6 +53,7 @@ def lib():
         _lib.or_parabola_vertex.argtypes = [C.c_double] * 6
         _lib.or_warp_sample.restype = C.c_double
         _lib.or_cost_volume.restype = C.c_int
+        _lib.or_cost_band.restype = C.c_int
         _lib.or_ncc_window.restype = C.c_int
         _lib.or_sgm_aggregate.restype = C.c_int
         _lib.or_estimate.restype = C.c_int
@@ -147,6 +148,26 @@ def cost_volume(ref, nbrs, side, K, R, t, n, rho0, drho, G, lo=None, D=None, Ds=
     return S
 
 
+def cost_band(ref, nbrs, side, K, R, t, n, rho0, drho, G, y0, y1, lo=None, D=None, Ds=None, cost=0):
+    """Rows y0 .. y1 - 1 of the cost volume (warps of the rows they reach)."""
+    ref = _c(ref, np.uint8)
+    H, W = ref.shape
+    V = len(nbrs)
+    nb = [_c(x, np.uint8) for x in nbrs]
+    arr = (C.c_void_p * V)(*[x.ctypes.data for x in nb])
+    D = G if D is None else D
+    Ds = D if Ds is None else Ds
+    S = np.zeros((y1 - y0, W, Ds), np.uint16)
+    lo_a = None if lo is None else _c(lo, np.int32)
+    rc = lib().or_cost_band(_p(ref), arr, V, _p(_c(side, np.int8)), W, H, _p(_c(K, np.float64)),
+                            _p(_c(R, np.float64)), _p(_c(t, np.float64)), _p(_c(n, np.float64)),
+                            C.c_double(rho0), C.c_double(drho), G,
+                            None if lo_a is None else _p(lo_a), D, Ds, int(cost), int(y0), int(y1), _p(S))
+    if rc != 0:
+        raise ValueError("or_cost_band rc=%d" % rc)
+    return S
+
+
 def cost_at(ref, nbrs, side, K, R, t, n, rho0, drho, xs, ys, gs, cost=0):
     ref = _c(ref, np.uint8)
     H, W = ref.shape
@@ -236,6 +257,15 @@ def normals(depth, img, K, radius=2, beta=10.0):
     lib().or_normals(_p(depth), _p(_c(img, np.uint8)), W, H, _p(_c(K, np.float64)), int(radius),
                      C.c_double(beta), _p(out), _p(raw))
     return out, raw
+
+
+def normals_smooth(raw, img, radius=2, beta=10.0):
+    """Eq. normal-smooth + Eq. normal on a given raw normal field (H, W, 3)."""
+    raw = _c(raw, np.float64)
+    H, W, _ = raw.shape
+    out = np.zeros((H, W, 3), np.float32)
+    lib().or_normals_smooth(_p(raw), _p(_c(img, np.uint8)), W, H, int(radius), C.c_double(beta), _p(out))
+    return out
 
 
 def confidence(normal, nPi=(0.0, 0.0, -1.0), rho_deg=60.0):

@@ -113,16 +113,17 @@ OR_EXPORT void or_census_u8(const uint8_t* img, int W, int H, uint64_t* out)
         }
 }
 
-/* census over a warped image of real values (the warped neighbour patches) */
-static uint64_t census_f64_at(const double* img, int W, int H, int x, int y)
+/* census over a warped image of real values (the warped neighbour patches),
+   whose rows ya .. are stored in img */
+static uint64_t census_f64_at(const double* img, int W, int H, int ya, int x, int y)
 {
-    double c = img[(size_t)y * W + x];
+    double c = img[(size_t)(y - ya) * W + x];
     uint64_t bits = 0;
     for (int dy = -3; dy <= 3; ++dy)
         for (int dx = -4; dx <= 4; ++dx) {
             int xx = clampi(x + dx, 0, W - 1), yy = clampi(y + dy, 0, H - 1);
             int k = (dy + 3) * 9 + (dx + 4);
-            if (img[(size_t)yy * W + xx] < c) bits |= (uint64_t)1 << k;
+            if (img[(size_t)(yy - ya) * W + xx] < c) bits |= (uint64_t)1 << k;
         }
     return bits;
 }
@@ -296,8 +297,9 @@ OR_EXPORT int or_ncc_window(const double a[25], const double b[25])
 }
 
 /* NCC cost of pixel (x, y): 5x5 windows with clamp-to-edge in the reference
-   grid over the reference image and the warped image. */
-static int ncc_at(const uint8_t* ref, const double* wimg, int W, int H, int x, int y)
+   grid over the reference image and the warped image, whose rows ya .. are
+   stored in wimg. */
+static int ncc_at(const uint8_t* ref, const double* wimg, int W, int H, int ya, int x, int y)
 {
     double a[25], b[25];
     int i = 0;
@@ -305,7 +307,7 @@ static int ncc_at(const uint8_t* ref, const double* wimg, int W, int H, int x, i
         for (int dx = -2; dx <= 2; ++dx, ++i) {
             const int xx = clampi(x + dx, 0, W - 1), yy = clampi(y + dy, 0, H - 1);
             a[i] = ref[(size_t)yy * W + xx];
-            b[i] = wimg[(size_t)yy * W + xx];
+            b[i] = wimg[(size_t)(yy - ya) * W + xx];
         }
     return or_ncc_window(a, b);
 }
@@ -315,68 +317,87 @@ static int ncc_at(const uint8_t* ref, const double* wimg, int W, int H, int x, i
 static double plane_delta(double rho0, double drho, int g) { return 1.0 / (rho0 + g * drho); }
 
 /*
- * Cost volume of one pyramid level (Alg. 1).  For every neighbour view and
- * every plane g of the level list needed by some pixel, the neighbour image is
- * warped into the reference view, its census is taken at the pixels whose
- * window [lo_p, lo_p + D) contains g, and the Hamming distance to the
+ * Cost volume of one pyramid level (Alg. 1), rows y0 .. y1 - 1 of the
+ * reference.  For every neighbour view and every plane g of the level list
+ * needed by some pixel, the neighbour image is warped into the reference view
+ * (the rows the band's windows reach), its census is taken at the pixels
+ * whose window [lo_p, lo_p + D) contains g, and the Hamming distance to the
  * reference census is accumulated into the left or right subset sum (cost
  * 0), or the NCC cost of the 5x5 windows (cost 1) is.
- * R: V x 9 (row-major), t: V x 3, side: -1 left / +1 right.
+ * R: V x 9 (row-major), t: V x 3, side: -1 left / +1 right; lo: [H][W] of the
+ * whole image (or NULL); S: [y1 - y0][W][Ds].
  */
-OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int V,
-                             const int8_t* side, int W, int H, const double K[9],
-                             const double* R, const double* t, const double n[3],
-                             double rho0, double drho, int G, const int32_t* lo,
-                             int D, int Ds, int cost, uint16_t* S)
+OR_EXPORT int or_cost_band(const uint8_t* ref, const uint8_t* const* nbrs, int V,
+                           const int8_t* side, int W, int H, const double K[9],
+                           const double* R, const double* t, const double n[3],
+                           double rho0, double drho, int G, const int32_t* lo,
+                           int D, int Ds, int cost, int y0, int y1, uint16_t* S)
 {
-    if (W < 2 || H < 2 || D < 1 || Ds < D || G < D) return -1;
-    size_t np = (size_t)W * H;
-    uint64_t* cref = (uint64_t*)malloc(np * sizeof(uint64_t));
-    uint32_t* sL = (uint32_t*)calloc(np * D, sizeof(uint32_t));
-    uint32_t* sR = (uint32_t*)calloc(np * D, sizeof(uint32_t));
+    if (W < 2 || H < 2 || D < 1 || Ds < D || G < D || y0 < 0 || y1 > H || y0 >= y1) return -1;
+    const int ya = y0 - 3 < 0 ? 0 : y0 - 3, yb = y1 + 3 > H ? H : y1 + 3;   /* warped rows */
+    const size_t nb = (size_t)W * (y1 - y0), nw = (size_t)W * (yb - ya);
+    uint64_t* cref = (uint64_t*)malloc((size_t)W * H * sizeof(uint64_t));
+    uint32_t* sL = (uint32_t*)calloc(nb * D, sizeof(uint32_t));
+    uint32_t* sR = (uint32_t*)calloc(nb * D, sizeof(uint32_t));
     int nL = 0, nR = 0;
     for (int k = 0; k < V; ++k) { if (side[k] < 0) ++nL; else ++nR; }
     or_census_u8(ref, W, H, cref);
     int gmin = G, gmax = -1;
-    for (size_t i = 0; i < np; ++i) {
-        int l = lo ? lo[i] : 0;
-        if (l < gmin) gmin = l;
-        if (l + D - 1 > gmax) gmax = l + D - 1;
-    }
+    for (int y = y0; y < y1; ++y)
+        for (int x = 0; x < W; ++x) {
+            int l = lo ? lo[(size_t)y * W + x] : 0;
+            if (l < gmin) gmin = l;
+            if (l + D - 1 > gmax) gmax = l + D - 1;
+        }
     for (int k = 0; k < V; ++k) {
 #pragma omp parallel
         {
-            double* wimg = (double*)malloc(np * sizeof(double));
-            uint8_t* wval = (uint8_t*)malloc(np);
+            double* wimg = (double*)malloc(nw * sizeof(double));
+            uint8_t* wval = (uint8_t*)malloc(nw);
             double Hm[9];
 #pragma omp for schedule(dynamic, 1)
             for (int g = gmin; g <= gmax; ++g) {
                 or_homography(K, R + 9 * k, t + 3 * k, n, plane_delta(rho0, drho, g), Hm);
-                or_warp_image(nbrs[k], W, H, Hm, wimg, wval);
-                for (int y = 0; y < H; ++y)
+                for (int y = ya; y < yb; ++y)
                     for (int x = 0; x < W; ++x) {
-                        size_t p = (size_t)y * W + x;
+                        int32_t v;
+                        wimg[(size_t)(y - ya) * W + x] = or_warp_sample(nbrs[k], W, H, Hm, x, y, &v);
+                        wval[(size_t)(y - ya) * W + x] = (uint8_t)v;
+                    }
+                for (int y = y0; y < y1; ++y)
+                    for (int x = 0; x < W; ++x) {
+                        size_t p = (size_t)y * W + x, pb = (size_t)(y - y0) * W + x;
                         int s = g - (lo ? lo[p] : 0);
                         if (s < 0 || s >= D) continue;
                         int h = cost ? 255 : 62;
-                        if (wval[p])
-                            h = cost ? ncc_at(ref, wimg, W, H, x, y)
-                                     : or_hamming(cref[p], census_f64_at(wimg, W, H, x, y));
-                        if (side[k] < 0) sL[p * D + s] += (uint32_t)h;
-                        else sR[p * D + s] += (uint32_t)h;
+                        if (wval[(size_t)(y - ya) * W + x])
+                            h = cost ? ncc_at(ref, wimg, W, H, ya, x, y)
+                                     : or_hamming(cref[p], census_f64_at(wimg, W, H, ya, x, y));
+                        if (side[k] < 0) sL[pb * D + s] += (uint32_t)h;
+                        else sR[pb * D + s] += (uint32_t)h;
                     }
             }
             free(wimg);
             free(wval);
         }
     }
-    for (size_t p = 0; p < np; ++p)
+    for (size_t p = 0; p < nb; ++p)
         for (int s = 0; s < Ds; ++s)
             S[p * Ds + s] = s < D ? or_lr_combine(sL[p * D + s], nL, sR[p * D + s], nR) : 0;
     free(cref);
     free(sL);
     free(sR);
     return 0;
+}
+
+/* the whole image */
+OR_EXPORT int or_cost_volume(const uint8_t* ref, const uint8_t* const* nbrs, int V,
+                             const int8_t* side, int W, int H, const double K[9],
+                             const double* R, const double* t, const double n[3],
+                             double rho0, double drho, int G, const int32_t* lo,
+                             int D, int Ds, int cost, uint16_t* S)
+{
+    return or_cost_band(ref, nbrs, V, side, W, H, K, R, t, n, rho0, drho, G, lo, D, Ds, cost, 0, H, S);
 }
 
 /* The same cost for a list of individual voxels (pixel (x, y), plane g of
@@ -711,11 +732,14 @@ OR_EXPORT void or_normals_raw(const float* depth, int W, int H, const double K[9
         }
 }
 
-OR_EXPORT void or_normals(const float* depth, const uint8_t* img, int W, int H, const double K[9],
-                          int radius, double beta, float* normal_out, float* raw_out)
+/* Eq. normal-smooth on a given raw normal field nr [H][W][3]: the pixel's own
+   normal plus the Gaussian- and appearance-weighted sum over the window of
+   radius `radius` (p included, out-of-image q skipped), sigma = radius,
+   weight (2 pi sigma^2)^-1/2 exp(-|q - p|^2 / (2 sigma^2) - |I_p - I_q| / beta);
+   Eq. normal then normalises (a zero sum stays zero). */
+OR_EXPORT void or_normals_smooth(const double* nr, const uint8_t* img, int W, int H, int radius, double beta,
+                                 float* normal_out)
 {
-    double* nr = (double*)malloc(sizeof(double) * 3 * (size_t)W * H);
-    or_normals_raw(depth, W, H, K, nr);
     double sigma = (double)radius;
     double norm = 1.0 / sqrt(2.0 * M_PI * sigma * sigma);
     for (int y = 0; y < H; ++y)
@@ -732,11 +756,18 @@ OR_EXPORT void or_normals(const float* depth, const uint8_t* img, int W, int H, 
                     for (int c = 0; c < 3; ++c) s[c] += nr[3 * q + c] * wgt;
                 }
             double len = sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
-            for (int c = 0; c < 3; ++c) {
-                normal_out[3 * p + c] = len > 0.0 ? (float)(s[c] / len) : 0.0f;
-                if (raw_out) raw_out[3 * p + c] = (float)nr[3 * p + c];
-            }
+            for (int c = 0; c < 3; ++c) normal_out[3 * p + c] = len > 0.0 ? (float)(s[c] / len) : 0.0f;
         }
+}
+
+OR_EXPORT void or_normals(const float* depth, const uint8_t* img, int W, int H, const double K[9],
+                          int radius, double beta, float* normal_out, float* raw_out)
+{
+    double* nr = (double*)malloc(sizeof(double) * 3 * (size_t)W * H);
+    or_normals_raw(depth, W, H, K, nr);
+    or_normals_smooth(nr, img, W, H, radius, beta, normal_out);
+    if (raw_out)
+        for (size_t i = 0; i < 3 * (size_t)W * H; ++i) raw_out[i] = (float)nr[i];
     free(nr);
 }
 

@@ -381,8 +381,37 @@ def make_scene(quads, W, H, f, centers, targets, sides, G0, d_near, d_far, seed,
         Rs.append(Rk)
         ts.append(tk)
     rho_far, drho = _sweep(d_near, d_far, G0)
+    meta = dict(meta or {})
+    meta["quads"] = quads
     return Scene(W, H, K, ref, nbrs, np.stack(Rs), np.stack(ts), np.asarray(sides, dtype=np.int8),
-                 np.array([0.0, 0.0, -1.0]), rho_far, drho, G0, depth, normal, dict(meta or {}))
+                 np.array([0.0, 0.0, -1.0]), rho_far, drho, G0, depth, normal, meta)
+
+
+def visibility_mask(sc, rel_tol=1e-2):
+    """Ground-truth visibility of the reference pixels of a rendered scene:
+    True where the surface point seen by the reference pixel is also the one
+    seen by every neighbour at its projection (inside the image, in front of
+    the camera, its depth there within rel_tol of the neighbour's rendered
+    depth).  Scene geometry only: occluded and out-of-view pixels are False."""
+    quads = sc.meta["quads"]
+    H, W = sc.H, sc.W
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    rays = np.stack([xs, ys, np.ones_like(xs)], -1) @ np.linalg.inv(sc.K).T
+    X = rays * sc.depth_gt[..., None]
+    vis = np.ones((H, W), bool)
+    for k in range(sc.n_views):
+        _, dk, _, _ = render_view(quads, sc.K, sc.R[k], sc.t[k], W, H, return_gt=True)
+        Xk = X @ sc.R[k].T + sc.t[k]
+        z = Xk[..., 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = sc.K[0, 0] * Xk[..., 0] / z + sc.K[0, 2]
+            v = sc.K[1, 1] * Xk[..., 1] / z + sc.K[1, 2]
+        ok = (z > 0) & (u >= 0) & (u <= W - 1) & (v >= 0) & (v <= H - 1)
+        ui = np.clip(np.rint(np.where(ok, u, 0)), 0, W - 1).astype(int)
+        vi = np.clip(np.rint(np.where(ok, v, 0)), 0, H - 1).astype(int)
+        ok &= np.abs(dk[vi, ui] - z) <= rel_tol * np.abs(z)
+        vis &= ok
+    return vis
 
 
 # --- recipes --------------------------------------------------------------

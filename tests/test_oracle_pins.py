@@ -635,6 +635,57 @@ def test_normal_smoothing_stops_at_image_edges(orc):
     assert np.degrees(np.arccos(np.clip(sm_u[10, 18] @ n2, -1, 1))) > 0.5
 
 
+# ------------------------------------------------------------------ normal smoothing weights
+# Hand-built raw normal fields whose smoothed normal has a closed form; the
+# expected values are written as numbers (sigma = radius = 2, beta = 10).
+
+def _field(H=9, W=9):
+    return np.zeros((H, W, 3)), np.full((H, W), 100, np.uint8)
+
+
+def test_normal_smoothing_sigma_is_the_window_radius(orc):
+    """Only the pixels at distance 1 and 2 right of p carry a normal, (1,0,0)
+    and (0,1,0): the smoothed normal at p is their weights' direction, whose
+    ratio is exp(-(4 - 1) / (2 sigma^2)) = exp(-3/8) = 0.687289 for sigma = 2
+    (sigma = 1 would give 0.223130)."""
+    nr, img = _field()
+    nr[4, 5] = (1.0, 0.0, 0.0)
+    nr[4, 6] = (0.0, 1.0, 0.0)
+    n = orc.normals_smooth(nr, img)[4, 4]
+    r = 0.6872892787909722
+    assert np.allclose(n, [1.0 / math.sqrt(1 + r * r), r / math.sqrt(1 + r * r), 0.0], atol=1e-6)
+
+
+def test_normal_smoothing_own_term_and_gaussian_factor(orc):
+    """p's raw normal is (1,0,0), every other pixel's (0,1,0), flat image.  The
+    smoothed sum is (1 + c) e_x + c S e_y with c = (2 pi sigma^2)^-1/2 =
+    0.199471 and S = sum over the 24 other window pixels of exp(-d^2 / 8) =
+    14.824923; its y/x ratio is c S / (1 + c) = 2.465373.  Dropping the
+    standalone n_p term gives 14.8249, dropping the factor c gives 7.41246,
+    leaving p out of the window sum gives 2.95714."""
+    nr, img = _field()
+    nr[...] = (0.0, 1.0, 0.0)
+    nr[4, 4] = (1.0, 0.0, 0.0)
+    n = orc.normals_smooth(nr, img)[4, 4]
+    assert abs(n[2]) < 1e-7
+    assert abs(n[1] / n[0] - 2.4653734) < 2e-6
+
+
+def test_normal_smoothing_intensity_weight_beta(orc):
+    """Neighbours left and right of p at distance 1 carry (0,0,1) and (0,1,0);
+    the left one differs from p by 20 grey levels (once brighter, once
+    darker): the ratio of the two weights is exp(-20 / beta) = exp(-2) =
+    0.135335 for beta = 10."""
+    for dI in (20, -20):
+        nr, img = _field()
+        nr[4, 3] = (0.0, 0.0, 1.0)
+        nr[4, 5] = (0.0, 1.0, 0.0)
+        img[4, 3] = 100 + dI
+        n = orc.normals_smooth(nr, img)[4, 4]
+        assert abs(n[0]) < 1e-7
+        assert abs(n[2] / n[1] - 0.1353352832366127) < 1e-6
+
+
 # ------------------------------------------------------------------ NCC 5x5
 def test_ncc_perfect_affine_anti_and_flat_windows(orc):
     g = np.random.default_rng(31)
