@@ -562,7 +562,8 @@ enum {
     FASSMVS_STAGE_MEDIAN = 5,  /* 5x5 median */
     FASSMVS_STAGE_NORMALS = 6, /* normals, smoothing, confidence */
     FASSMVS_STAGE_WINDOW = 7,  /* plane windows + surface-normal jumps */
-    FASSMVS_NSTAGES = 8
+    FASSMVS_STAGE_RELAYOUT = 8, /* blocked cost volume -> pixel-major layout */
+    FASSMVS_NSTAGES = 9
 };
 FASSMVS_API fassmvs_status fassmvs_profile_enable(fassmvs_ctx* ctx, int on);
 /* ms[FASSMVS_NSTAGES], counts[FASSMVS_NSTAGES] (either may be NULL); reset != 0

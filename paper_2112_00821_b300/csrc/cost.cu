@@ -4,30 +4,26 @@
 // plane its windows need, one (plane, view) pair per iteration:
 //   1. sampling: the 64 x 58 warped sample tile (tile + 9x7 census halo) is
 //      produced cooperatively -- each warp owns 7 or 8 sample rows, each
-//      lane two sample columns (coalesced
-//      neighbour-image reads), the homography is stepped down the column in
-//      double-float arithmetic; samples are stored as FP16 pairs (V(x),
-//      V(x+1)) so the census can load two at a time;
+//      lane two sample columns (coalesced neighbour-image reads); the
+//      homography's rows are stepped down the column in double-float
+//      arithmetic, the position's cell is the floor of an FP32 quotient and
+//      its offsets inside the cell come from the double-float residual
+//      N - cell * D, so they are accurate to ~1e-7 px; the value is the
+//      bilinear blend in lerp form in FP32, unrounded;
 //   2. one __syncthreads (the sample tile is double-buffered);
 //   3. census: warp w < 7 takes columns 8w .. 8w + 7 of the tile, lane l
 //      column 8w + l % 8 and rows 13 (l / 8) .. + 12 (every lane of the seven
 //      warps busy; rows 72 words apart so the four row chunks fall in
-//      different shared-memory banks); for every
-//      window row, five packed FP16 saturating subtractions give ten
-//      comparison bits [V(q) < V(p)] which five packed FMAs add, with
-//      power-of-two weights, into four FP16x2 accumulators (10 bits per half,
-//      biased by 1024 so the half's bit pattern holds the integer); the XOR
-//      with the reference census (pre-arranged in the same layout) and four
+//      different shared-memory banks); every comparison bit [V(q) < V(p)] is
+//      the sign of the FP32 difference V(q) - V(p) (exact: equal values give
+//      +0), funnel-shifted into two words per pixel; the XOR with the
+//      reference census (pre-arranged in the same bit order) and two
 //      popcounts give the Hamming distance; left / right sums accumulate in
 //      registers over the views and the plane's costs are stored after the
 //      last view.
-// Sampling reading (shared with the oracle): 1/256-pixel fixed-point
-// positions floor(256 u), exact integer bilinear blend with 8-bit weights,
-// value kept at 1/16 grey level.  Values lie in [0, 4080]; shifted by -2040
-// they are exact FP16 integers, and the FP16 difference of two of them keeps
-// its sign and its >= 1 test, so the census comparisons are exact.
-#include <cuda_fp16.h>
-
+// Sampling reading (Alg. 1, shared with the oracle): the value of the
+// neighbour image at the unrounded position H q, bilinear in lerp form,
+// positions clamped to the image.
 #include <type_traits>
 
 #include "fm_internal.cuh"
@@ -46,21 +42,24 @@ constexpr int kPlanWarp = NWARP - 1;     // plans and issues the staging copies
 __host__ __device__ constexpr int row_start(int w) { return (SH * w) / NWARP; }
 constexpr int kMaxRows = 8;              // the largest share
 static_assert(row_start(NWARP) - row_start(NWARP - 1) <= kMaxRows, "row shares");
-constexpr int PMAX = 1 << 24;
 constexpr float MAGIC = 12582912.0f;     // 1.5 * 2^23: adding it leaves an integer in the mantissa
 constexpr int MAGIC_BITS = 0x4B400000;
-constexpr uint32_t LAYOUT_MASK = 0x03FF03FFu;
+constexpr int BYTE_BITS = 0x4B000000;    // 2^23 + b as a float, for a byte b
+constexpr float TWO23 = 8388608.0f;
 
 struct SmemCost {
     uint64_t mbar[2];                    // staging: completion of the tensor copy into slot 0 / 1
     int stg_x0[2], stg_y0[2], stg_ok[2]; // staging: box origin in the view image, and whether it was issued
     int stg_dead;                        // a staged copy missed its bound: no further staging in this CTA
-    uint32_t pair[2][SH][SW];            // census: FP16x2 (V(x) - 2040, V(x+1) - 2040); NCC: u16x2 (V(x), V(x+1))
+    float val[2][SH][SW];                // warped values minus 128 (FP32, unrounded)
     uint32_t okm[2][PH][2];              // centre-in-image bit per pixel column
+    float hdf[2][18];                    // census: the pair's homography (high, low words), for near ties
+    uint8_t rkcol[2][NWARP][64];         // census: per sampling warp and pixel column, its rows whose
+                                         // window columns hold a risky sample (one bit per row)
     union {
-        uint4 refl[PH][PW];              // census: reference census in the accumulator layout
+        uint4 refl[PH][PW];              // census: reference census in the comparison words' sign bits
         struct {
-            uint32_t refp[SH][SW];       // NCC: reference values (a(x), a(x+1)) on the sample grid
+            float refv[SH][SW];          // NCC: reference grey levels on the sample grid
             int2 refs[PH][PW];           // NCC: (sum a, 25 sum a^2 - (sum a)^2) of each 5x5 window
         } ncc;
     };
@@ -87,9 +86,9 @@ __device__ __forceinline__ df df_add(df a, df b)
     return {s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
 }
 
-// Values whose high word lies on the 2^-10 grid with magnitude below 2^14
+// Values whose high word lies on the 2^-10 grid with magnitude below 2^12
 // add exactly in FP32, so stepping down a column costs two additions: the
-// homography is scaled (prep_level_kernel) so that |N|, |D| stay below 2^14
+// homography is scaled (prep_level_kernel) so that |N|, |D| stay below 2^12
 // over and well around the image, and the step's high words are on the grid.
 constexpr float GRID_MAGIC = 12288.0f;   // 1.5 * 2^13: rounds |x| < 2^12 to the 2^-10 grid
 __device__ __forceinline__ df to_grid(df a)
@@ -98,16 +97,6 @@ __device__ __forceinline__ df to_grid(df a)
     return {h, __fadd_rn(a.lo, __fsub_rn(a.hi, h))};
 }
 __device__ __forceinline__ df grid_add(df a, df b) { return {__fadd_rn(a.hi, b.hi), __fadd_rn(a.lo, b.lo)}; }
-// The denominator D is carried divided by 256 (exact: a power of two), which
-// puts its high words on the 2^-18 grid with |D / 256| < 2^4 and lets the
-// reciprocal give 256 / D directly.
-constexpr float DGRID_MAGIC = 48.0f;     // 1.5 * 2^5: rounds |x| < 2^4 to the 2^-18 grid
-__device__ __forceinline__ df to_dgrid(df a)
-{
-    float h = __fsub_rn(__fadd_rn(a.hi, DGRID_MAGIC), DGRID_MAGIC);
-    return {h, __fadd_rn(a.lo, __fsub_rn(a.hi, h))};
-}
-__device__ __forceinline__ df df_scale(df a, float s) { return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)}; }
 
 // a * b for an integer-valued b (|b| < 2^24)
 __device__ __forceinline__ df df_mul_int(df a, float b)
@@ -128,69 +117,80 @@ __device__ __forceinline__ float rcp_approx(float x)
 
 __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h + i), __ldg(h + 9 + i)}; }
 
-// floor(256 N / D) for D > 0, given Dn = D / 256 and r ~ 256 / D, for
-// |N / D| < 16000: q = 256 N / D to a few ulps, the double-float residual
-// N - (q / 256) D = N - q Dn gives the correction, and the floors come from
-// adding 1.5 * 2^23 with round-down.  The words of N and D are split on a
-// grid, so the low words are not small: q and r are formed from the summed
-// words.
-__device__ __forceinline__ int fix_pos(df N, df Dn, float r)
+// One coordinate of a warped sample.  N / D is the position (D > 0, r ~ 1 / D;
+// r = 0 for a point behind the camera, which then reads cell 0 at offset 0,
+// the clamped position of (-inf, -inf)).  The cell is the floor of the
+// position, from the nearest integer c to the FP32 quotient and the sign of
+// the double-float residual f = (N - c D) / D (accurate to ~3e-7 px, so the
+// cell can be off by one only within that distance of an integer, where both
+// cells give the same value); clamped to [0, cmax] (cmax = image size - 2)
+// with the offset saturated to [0, 1], which is the clamp of the position to
+// the image.  in: the position lies on [0, cmax + 1].
+struct Coord { int i; float f; bool in; };
+__device__ __forceinline__ Coord coord(df N, df D, float r, float cmax)
 {
-    float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
-    float e1 = __fmaf_rn(-q, Dn.hi, N.hi);
-    float e2 = __fmaf_rn(-q, Dn.lo, N.lo);
-    float corr = __fmul_rn(__fadd_rn(e1, e2), r);
-    float a = fminf(fmaxf(q, -4194000.0f), 4194000.0f);
-    float t1 = __fadd_rd(a, MAGIC);
-    float fa = __fsub_rn(t1, MAGIC);
-    float rem = __fadd_rn(corr, __fsub_rn(a, fa));
-    float t2 = __fadd_rd(rem, MAGIC);
-    return (__float_as_int(t1) - MAGIC_BITS) + (__float_as_int(t2) - MAGIC_BITS);
+    const float q = fminf(fmaxf(__fmul_rn(__fadd_rn(N.hi, N.lo), r), -2.0f), cmax + 3.0f);   // NaN -> -2
+    const float c = rintf(q);
+    const float f = __fmul_rn(__fadd_rn(__fmaf_rn(-c, D.hi, N.hi), __fmaf_rn(-c, D.lo, N.lo)), r);
+    const bool neg = f < 0.0f;
+    const float cell = neg ? __fsub_rn(c, 1.0f) : c;
+    const float fr = neg ? __fadd_rn(f, 1.0f) : f;
+    const float cc = fminf(fmaxf(cell, 0.0f), cmax);
+    const float a = __saturatef(__fadd_rn(__fsub_rn(cell, cc), fr));
+    const bool in = cell >= 0.0f && (cell <= cmax || (cell == cmax + 1.0f && fr == 0.0f));
+    return {__float_as_int(__fadd_rn(cc, MAGIC)) - MAGIC_BITS, a, in};
 }
 
-// The clamped tap position of one warped sample and whether the position
-// lies on the image grid.  Dn is the denominator divided by 256; its sign is
-// that of the exact sum of its words (rounding keeps the sign).
-struct SPos { int iu, iv, A, B; };
+// The clamped cell and offsets of one warped sample, and whether its position
+// lies on the image grid.
+struct SPos { int iu, iv; float a, b; };
 
 template <bool WANT_OK>
-__device__ __forceinline__ SPos sample_pos(int W, int H, df Nu, df Nv, df Dn, bool& ok)
+__device__ __forceinline__ SPos sample_pos(float wm2, float hm2, df Nu, df Nv, df Dn, bool& ok)
 {
-    int Pu = -PMAX, Pv = -PMAX;
     const float dsum = __fadd_rn(Dn.hi, Dn.lo);
     const bool front = dsum > 0.0f;
-    if (front) {
-        const float r = rcp_approx(dsum);
-        Pu = fix_pos(Nu, Dn, r);
-        Pv = fix_pos(Nv, Dn, r);
-    }
-    const int wmax = 256 * (W - 1), hmax = 256 * (H - 1);
-    if (WANT_OK) ok = front && Pu >= 0 && Pu <= wmax && Pv >= 0 && Pv <= hmax;
-    const int cu = min(max(Pu, 0), wmax), cv = min(max(Pv, 0), hmax);
-    const int iu = min(cu >> 8, W - 2), iv = min(cv >> 8, H - 2);
-    return {iu, iv, cu - 256 * iu, cv - 256 * iv};
+    // 1 / D to about half an ulp (one Newton step on the approximation)
+    const float r0 = rcp_approx(dsum);
+    const float r = front ? __fmaf_rn(r0, __fmaf_rn(-dsum, r0, 1.0f), r0) : 0.0f;
+    const Coord cu = coord(Nu, Dn, r, wm2);
+    const Coord cv = coord(Nv, Dn, r, hm2);
+    if (WANT_OK) ok = front && cu.in && cv.in;
+    return {cu.i, cv.i, cu.f, cv.f};
 }
 
-// exact integer bilinear blend with 8-bit weights: V = 16 x grey level in [0, 4080]
-__device__ __forceinline__ int blend(int i00, int i01, int i10, int i11, int A, int B)
+// 2^23 + b as a float for a byte b (exact)
+__device__ __forceinline__ float bf(int b) { return __int_as_float(BYTE_BITS + b); }
+
+// bilinear blend in lerp form: top = I00 + a (I01 - I00), bottom likewise,
+// value = top + b (bottom - top).  The values are carried minus 128 (the byte
+// differences and the shifted corners are exact), which halves their
+// magnitude and so their rounding error; the census compares differences and
+// the NCC deviations from the window mean, so the shift changes no result.
+constexpr float VBIAS = TWO23 + 128.0f;
+// pl: the four taps are equal (a plateau sample: its value is that integer, exactly)
+__device__ __forceinline__ float blend(int i00, int i01, int i10, int i11, float a, float b, bool& pl)
 {
-    const int top = (i00 << 8) + A * (i01 - i00);
-    const int bot = (i10 << 8) + A * (i11 - i10);
-    return ((top << 8) + B * (bot - top) + 2048) >> 12;
+    const float t00 = bf(i00), t10 = bf(i10);
+    const float d0 = __fsub_rn(bf(i01), t00), d1 = __fsub_rn(bf(i11), t10);
+    pl = d0 == 0.0f && d1 == 0.0f && t00 == t10;
+    const float top = __fmaf_rn(a, d0, __fsub_rn(t00, VBIAS));
+    const float bot = __fmaf_rn(a, d1, __fsub_rn(t10, VBIAS));
+    return __fmaf_rn(b, __fsub_rn(bot, top), top);
 }
 
 // the 2x2 taps from global memory
-__device__ __forceinline__ int taps_global(const uint8_t* __restrict__ img, int pitch, SPos p)
+__device__ __forceinline__ float taps_global(const uint8_t* __restrict__ img, int pitch, SPos p, bool& pl)
 {
     const uint8_t* r0 = img + (size_t)p.iv * pitch + p.iu;
-    return blend(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + pitch), __ldg(r0 + pitch + 1), p.A, p.B);
+    return blend(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + pitch), __ldg(r0 + pitch + 1), p.a, p.b, pl);
 }
 
 // the 2x2 taps from the staged box whose origin is (sx0, sy0) (in_box true)
-__device__ __forceinline__ int taps_staged(const uint8_t* stg, int sx0, int sy0, SPos p)
+__device__ __forceinline__ float taps_staged(const uint8_t* stg, int sx0, int sy0, SPos p, bool& pl)
 {
     const uint8_t* r0 = stg + (p.iv - sy0) * kStageBX + (p.iu - sx0);
-    return blend(r0[0], r0[1], r0[kStageBX], r0[kStageBX + 1], p.A, p.B);
+    return blend(r0[0], r0[1], r0[kStageBX], r0[kStageBX + 1], p.a, p.b, pl);
 }
 
 __device__ __forceinline__ bool in_box(int sx0, int sy0, SPos p)
@@ -198,33 +198,159 @@ __device__ __forceinline__ bool in_box(int sx0, int sy0, SPos p)
     return (unsigned)(p.iu - sx0) <= (unsigned)(kStageBX - 2) && (unsigned)(p.iv - sy0) <= (unsigned)(kStageBY - 2);
 }
 
-// V - 2040 as a float (exact), ready for FP16
-__device__ __forceinline__ float v16_centred(int v16) { return __int_as_float(MAGIC_BITS + v16) - (MAGIC + 2040.0f); }
+// ---------------------------------------------------------------- exact census
+// A census comparison [V(q) < V(p)] is decided on the FP32 values (V = warped
+// value - 128) by the sign of x = 4096 (V(q) - V(p)), one rounding of an exact
+// difference; bit 30 of x records |x| >= 2, i.e. |V(q) - V(p)| >= 2^-11, and a
+// funnel shift by two keeps both bits.  The FP32 values lie within 2e-4 of the
+// FP64 ones (cell offsets within ~3e-7 of the exact ones times tap
+// differences of at most 255, plus the blend's three roundings), so a
+// comparison whose FP32 difference reaches 2^-11 has the FP64 comparison's
+// sign.  The others -- near ties, a few in ten thousand -- are decided again:
+// equal integer values (both samples on plateaus of equal pixels) are a tie
+// in FP64 as well; anything else is recomputed in double-float arithmetic
+// from the homography and the image (cen_fix).
+//
+// The 62 comparisons of a pixel, in window order k = 9 dy + dx (k = 31, the
+// centre, skipped), go to four words: k 0-15, 16-30, 32-47, 48-62.
+__host__ __device__ constexpr int cword(int k) { return k < 16 ? 0 : (k < 31 ? 1 : (k < 48 ? 2 : 3)); }
+__host__ __device__ constexpr int cbase(int w) { return w == 0 ? 0 : (w == 1 ? 16 : (w == 2 ? 32 : 48)); }
+__host__ __device__ constexpr int ccount(int w) { return (w & 1) ? 15 : 16; }
+// bit of the sign of comparison k in its word (the big-difference bit is one below)
+__host__ __device__ constexpr int cbit(int k) { return 2 * (ccount(cword(k)) - 1 - (k - cbase(cword(k)))) + 1; }
+constexpr uint32_t SIGN_BITS = 0xAAAAAAAAu;
+__host__ __device__ constexpr uint32_t big_bits(int w) { return (w & 1) ? 0x15555555u : 0x55555555u; }
 
-// canonical 9x7 census word -> four accumulator words: window row dy, pair p
-// (columns 2p, 2p+1) is packed-FMA number m = 5 dy + p, which lands in word
-// m / 10 at bit m % 10 of the low (even column) / high (odd column) half
+// canonical 9x7 census word -> the sign bits of the four comparison words
 __device__ __forceinline__ uint4 to_layout(uint64_t c)
 {
-    uint32_t w[4];
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int R = 0; R < 4; ++R) {
-        uint32_t v = 0x64006400u;
-#pragma unroll
-        for (int b = 0; b < 10; ++b) {
-            const int m = 10 * R + b;
-            if (m >= 35) break;
-            const int dy = m / 5, p = m % 5;
-            v |= (uint32_t)((c >> (dy * 9 + 2 * p)) & 1u) << b;
-            if (2 * p + 1 <= 8) v |= (uint32_t)((c >> (dy * 9 + 2 * p + 1)) & 1u) << (16 + b);
-        }
-        w[R] = v;
+    for (int k = 0; k < 63; ++k) {
+        if (k == 31) continue;
+        w[cword(k)] |= (uint32_t)((c >> k) & 1u) << cbit(k);
     }
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-__device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
-__device__ __forceinline__ uint32_t as_u32(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+// ---- double-float evaluation of one warped sample, for the near ties
+__device__ __forceinline__ df two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// N / D for D > 0 (a few ulps of double-float)
+__device__ __forceinline__ df df_div(df N, df D)
+{
+    const float r0 = rcp_approx(D.hi);
+    const float r = __fmaf_rn(r0, __fmaf_rn(-D.hi, r0, 1.0f), r0);
+    const float qh = __fmul_rn(N.hi, r);
+    const df p = two_prod(qh, D.hi);
+    const float rem = __fadd_rn(__fsub_rn(__fsub_rn(N.hi, p.hi), p.lo), __fsub_rn(N.lo, __fmul_rn(qh, D.lo)));
+    return two_sum(qh, __fmul_rn(rem, r));
+}
+
+// the cell (clamped to [0, cmax]) and offset (clamped to [0, 1]) of a position
+// u in double-float
+__device__ __forceinline__ int df_cell(df u, int cmax, df& a)
+{
+    float fl = floorf(u.hi);
+    df f = {__fsub_rn(u.hi, fl), u.lo};                     // the first word exact
+    if (__fadd_rn(f.hi, f.lo) < 0.0f) { fl = __fsub_rn(fl, 1.0f); f.hi = __fadd_rn(f.hi, 1.0f); }
+    else if (__fadd_rn(f.hi, f.lo) >= 1.0f) { fl = __fadd_rn(fl, 1.0f); f.hi = __fsub_rn(f.hi, 1.0f); }
+    if (fl < 0.0f) { a = {0.0f, 0.0f}; return 0; }
+    if (fl > (float)cmax) { a = {1.0f, 0.0f}; return cmax; }
+    a = f;
+    return (int)fl;
+}
+
+// t0 + a (t1 - t0) for taps t0, t1 and a double-float offset a
+__device__ __forceinline__ df df_lerp_taps(float t0, float t1, df a)
+{
+    const float d = __fsub_rn(t1, t0);
+    const df p = two_prod(a.hi, d);
+    const df s = two_sum(t0, p.hi);
+    return {s.hi, __fadd_rn(s.lo, __fadd_rn(p.lo, __fmul_rn(a.lo, d)))};
+}
+
+// value - 128 of the warped neighbour k at reference pixel (X, Y) under the
+// homography h (18 floats: the high then the low words of the nine entries),
+// in double-float arithmetic: the reading of the sampling evaluated to ~1e-11
+// grey levels
+__device__ __forceinline__ df sample_exact(const CostArgs& a, const float* h, int k, int X, int Y)
+{
+    const float fx = (float)X, fy = (float)Y;
+    auto e = [&](int i) { return df{h[i], h[9 + i]}; };
+    const df N = df_add(df_add(df_mul_int(e(0), fx), df_mul_int(e(1), fy)), e(2));
+    const df M = df_add(df_add(df_mul_int(e(3), fx), df_mul_int(e(4), fy)), e(5));
+    const df D = df_add(df_add(df_mul_int(e(6), fx), df_mul_int(e(7), fy)), e(8));
+    df au = {0.0f, 0.0f}, av = {0.0f, 0.0f};
+    int iu = 0, iv = 0;
+    if (__fadd_rn(D.hi, D.lo) > 0.0f) {
+        iu = df_cell(df_div(N, D), a.W - 2, au);
+        iv = df_cell(df_div(M, D), a.H - 2, av);
+    }
+    const uint8_t* r0 = a.views.img[k] + (size_t)iv * a.pitch + iu;
+    const float i00 = (float)__ldg(r0) - 128.0f, i01 = (float)__ldg(r0 + 1) - 128.0f;
+    const float i10 = (float)__ldg(r0 + a.pitch) - 128.0f, i11 = (float)__ldg(r0 + a.pitch + 1) - 128.0f;
+    const df top = df_lerp_taps(i00, i01, au), bot = df_lerp_taps(i10, i11, au);
+    // top + b (bot - top)
+    const df dd = df_add(bot, {-top.hi, -top.lo});
+    const df p = two_prod(av.hi, dd.hi);
+    const float pl = __fadd_rn(p.lo, __fadd_rn(__fmul_rn(av.hi, dd.lo), __fmul_rn(av.lo, dd.hi)));
+    return df_add(top, {p.hi, pl});
+}
+
+// The correction to the FP32 Hamming distance of pixel (sample row j0 + 3,
+// column c0 + 4) once its near ties -- the comparisons whose FP32 difference
+// stays below 2^-11 -- are decided exactly, computed by the whole warp (lane l
+// takes window positions l and l + 32; the same value returned in every
+// lane).  Equal values of one reference position (a window clamped at the
+// image border) or of two plateaus of equal pixels are ties in FP64 as well;
+// the rest are recomputed in double-float.  Sample rows past jlast (below the
+// image) read row jlast, as the census does.
+__device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW], const float* h, int k, int tx0, int ty0,
+                                       int j0, int c0, int jlast, uint4 rf, int lane)
+{
+    const float vp = vt[min(j0 + 3, jlast)][c0 + 4];
+    const float cs = __fmul_rn(4096.0f, vp);
+    const int xp = min(max(tx0 + c0, 0), a.W - 1), yp = min(max(ty0 + j0, 0), a.H - 1);
+    int delta = 0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int kk = lane + 32 * t;
+        if (kk == 31 || kk >= 63) continue;
+        const int dy = kk / 9, dx = kk - 9 * (kk / 9);
+        const float vq = vt[min(j0 + dy, jlast)][c0 + dx];
+        const float x = __fmaf_rn(vq, 4096.0f, -cs);
+        if (fabsf(x) >= 2.0f) continue;
+        const int xq = min(max(tx0 - 4 + c0 + dx, 0), a.W - 1), yq = min(max(ty0 - 3 + j0 + dy, 0), a.H - 1);
+        if (vq == vp && ((xq == xp && yq == yp) || vq == rintf(vq))) continue;
+        const df ep = sample_exact(a, h, k, xp, yp);
+        const df eq = sample_exact(a, h, k, xq, yq);
+        const df d = two_sum(eq.hi, -ep.hi);
+        const float diff = __fadd_rn(d.hi, __fadd_rn(d.lo, __fsub_rn(eq.lo, ep.lo)));
+        const uint32_t exact = diff < 0.0f ? 1u : 0u;
+        const uint32_t fp = __float_as_uint(x) >> 31;
+        if (exact != fp) {
+            const int w = cword(kk);
+            const uint32_t rw = w == 0 ? rf.x : (w == 1 ? rf.y : (w == 2 ? rf.z : rf.w));
+            const uint32_t rb = (rw >> (2 * (ccount(w) - 1 - (kk - cbase(w))) + 1)) & 1u;
+            delta += fp == rb ? 1 : -1;
+        }
+    }
+    return __reduce_add_sync(0xFFFFFFFFu, delta);
+}
+
+// slr[r] += v for a run-time r (a register array indexed by constants only)
+template <int N>
+__device__ __forceinline__ void add_at(uint32_t (&slr)[N], int r, uint32_t v)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i == r) slr[i] += v;
+}
 
 // ---------------------------------------------------------------- staging
 // For each (plane, view) pair one elected thread copies a kStageBX x kStageBY
@@ -361,12 +487,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     __syncthreads();
     if constexpr (NCC) {
         // reference values on the sample grid (clamp-to-edge), then each pixel's
-        // 5x5 window sums
+        // 5x5 window sums (exact integers)
         for (int i = tid; i < SH * SW; i += THREADS) {
             const int j = i / SW, c = i % SW;
             const uint8_t* row = a.ref + (size_t)min(max(ty0 - 3 + j, 0), H - 1) * a.ref_pitch;
-            const int x0 = min(max(tx0 - 4 + c, 0), W - 1), x1 = min(max(tx0 - 3 + c, 0), W - 1);
-            sm.ncc.refp[j][c] = (uint32_t)__ldg(row + x0) | ((uint32_t)__ldg(row + x1) << 16);
+            sm.ncc.refv[j][c] = (float)__ldg(row + min(max(tx0 - 4 + c, 0), W - 1));
         }
         __syncthreads();
         for (int i = tid; i < PH * PW; i += THREADS) {
@@ -376,7 +501,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             for (int dy = 0; dy < 5; ++dy)
 #pragma unroll
                 for (int dx = 0; dx < 5; ++dx) {
-                    const int v = (int)(sm.ncc.refp[r + 1 + dy][c + 2 + dx] & 0xFFFFu);
+                    const int v = (int)sm.ncc.refv[r + 1 + dy][c + 2 + dx];
                     sa += v;
                     saa += v * v;
                 }
@@ -397,7 +522,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         sm.rlo[r] = l;
         sm.rhi[r] = h;
     }
-    for (int i = tid; i < 2 * SH * SW; i += THREADS) (&sm.pair[0][0][0])[i] = 0u;
+    for (int i = tid; i < 2 * SH * SW; i += THREADS) (&sm.val[0][0][0])[i] = 0.0f;
     for (int i = tid; i < 2 * PH * 2; i += THREADS) (&sm.okm[0][0][0])[i] = 0u;
     // planes of this tile (guarded against an out-of-range window map), split
     // into nz consecutive chunks
@@ -427,6 +552,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     const int rs = row_start(warp), re = row_start(warp + 1);
     const int X0 = min(max(tx0 - 4 + lane, 0), W - 1);
     const int X1 = min(max(tx0 + 28 + lane, 0), W - 1);
+    const float wm2 = (float)(W - 2), hm2 = (float)(H - 2);
+    // tile-relative sample row of the image's last row: rows past it are read
+    // from it (computing them anew would round differently from the row that
+    // was stepped there, and break the exact ties the clamped reading makes)
+    const int jlast = H - 1 - (ty0 - 3);
     // Windows differ across the tile (a per-pixel range of D planes), so a
     // warp skips a plane its rows do not need.  Sample row j feeds the census
     // of pixel rows j - 6 .. j (NCC: j - 5 .. j - 1, a subset) and the centre
@@ -484,21 +614,22 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 const int sx0 = ready ? sm.stg_x0[buf] : 0, sy0 = ready ? sm.stg_y0[buf] : 0;
                 const float* h = a.htab + ((size_t)g * a.V + k) * 18;
                 const uint8_t* img = a.views.img[k];
+                if (!NCC && lane < 18) sm.hdf[buf][lane] = __ldg(h + lane);
                 const df h0 = load_df(h, 0), h1 = load_df(h, 1), h2 = load_df(h, 2);
                 const df h3 = load_df(h, 3), h4 = load_df(h, 4), h5 = load_df(h, 5);
-                const df h6 = df_scale(load_df(h, 6), 0.00390625f), h7 = df_scale(load_df(h, 7), 0.00390625f);
-                const df h8 = df_scale(load_df(h, 8), 0.00390625f);     // the denominator row / 256
+                const df h6 = load_df(h, 6), h7 = load_df(h, 7), h8 = load_df(h, 8);
                 const float fy = (float)min(max(ty0 - 3 + rs, 0), H - 1);
                 const float fx0 = (float)X0, fx1 = (float)X1;
                 const df by_u = df_add(df_mul_int(h1, fy), h2);
                 const df by_v = df_add(df_mul_int(h4, fy), h5);
                 const df by_d = df_add(df_mul_int(h7, fy), h8);
                 df u0 = to_grid(df_add(df_mul_int(h0, fx0), by_u)), v0 = to_grid(df_add(df_mul_int(h3, fx0), by_v));
-                df d0 = to_dgrid(df_add(df_mul_int(h6, fx0), by_d));
+                df d0 = to_grid(df_add(df_mul_int(h6, fx0), by_d));
                 df u1 = to_grid(df_add(df_mul_int(h0, fx1), by_u)), v1 = to_grid(df_add(df_mul_int(h3, fx1), by_v));
-                df d1 = to_dgrid(df_add(df_mul_int(h6, fx1), by_d));
-                const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_dgrid(h7);
-                uint32_t(*prow)[SW] = sm.pair[buf];
+                df d1 = to_grid(df_add(df_mul_int(h6, fx1), by_d));
+                const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
+                float(*vrow)[SW] = sm.val[buf];
+                uint32_t rk_lo = 0u, rk_hi = 0u;
                 // the row loop in two variants, chosen once per (plane, view):
                 // taps from the staged box (global memory outside it), or from
                 // global memory only
@@ -510,51 +641,59 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     const int j = rs + jj;
                     if (j >= re) break;
                     const int Y = ty0 - 3 + j;
+                    // rows below the image repeat its last row: the census and
+                    // NCC read that row for them (the same values bit for bit,
+                    // as the clamped reading makes them equal)
+                    if (Y > H - 1) break;
                     if (jj > 0 && Y >= 1 && Y <= H - 1) {
                         u0 = grid_add(u0, s1); v0 = grid_add(v0, s4); d0 = grid_add(d0, s7);
                         u1 = grid_add(u1, s1); v1 = grid_add(v1, s4); d1 = grid_add(d1, s7);
                     }
                     bool ok0 = false, ok1 = false;
                     const bool centre_row = j >= 3 && j < 3 + PH;
-                    int i0, i1;
                     SPos p0, p1;
                     if (centre_row) {
-                        p0 = sample_pos<true>(W, H, u0, v0, d0, ok0);
-                        p1 = sample_pos<true>(W, H, u1, v1, d1, ok1);
+                        p0 = sample_pos<true>(wm2, hm2, u0, v0, d0, ok0);
+                        p1 = sample_pos<true>(wm2, hm2, u1, v1, d1, ok1);
                     } else {
-                        p0 = sample_pos<false>(W, H, u0, v0, d0, ok0);
-                        p1 = sample_pos<false>(W, H, u1, v1, d1, ok1);
+                        p0 = sample_pos<false>(wm2, hm2, u0, v0, d0, ok0);
+                        p1 = sample_pos<false>(wm2, hm2, u1, v1, d1, ok1);
                     }
+                    float f0, f1;
+                    bool pl0, pl1;
                     if constexpr (ST) {
                         // a row whose taps all lie in the box (the usual case)
                         // takes one straight shared-memory path
                         const bool b0 = in_box(sx0, sy0, p0), b1 = in_box(sx0, sy0, p1);
                         if (__all_sync(0xFFFFFFFFu, b0 && b1)) {
-                            i0 = taps_staged(sp, sx0, sy0, p0);
-                            i1 = taps_staged(sp, sx0, sy0, p1);
+                            f0 = taps_staged(sp, sx0, sy0, p0, pl0);
+                            f1 = taps_staged(sp, sx0, sy0, p1, pl1);
                         } else {
-                            i0 = b0 ? taps_staged(sp, sx0, sy0, p0) : taps_global(img, a.pitch, p0);
-                            i1 = b1 ? taps_staged(sp, sx0, sy0, p1) : taps_global(img, a.pitch, p1);
+                            f0 = b0 ? taps_staged(sp, sx0, sy0, p0, pl0) : taps_global(img, a.pitch, p0, pl0);
+                            f1 = b1 ? taps_staged(sp, sx0, sy0, p1, pl1) : taps_global(img, a.pitch, p1, pl1);
                         }
                     } else {
-                        i0 = taps_global(img, a.pitch, p0);
-                        i1 = taps_global(img, a.pitch, p1);
+                        f0 = taps_global(img, a.pitch, p0, pl0);
+                        f1 = taps_global(img, a.pitch, p1, pl1);
                     }
-                    if constexpr (NCC) {
-                        int n0 = __shfl_sync(0xFFFFFFFFu, i0, (lane + 1) & 31);
-                        const int t1 = __shfl_sync(0xFFFFFFFFu, i1, 0);
-                        int n1 = __shfl_sync(0xFFFFFFFFu, i1, (lane + 1) & 31);
-                        if (lane == 31) { n0 = t1; n1 = 0; }
-                        prow[j][lane] = (uint32_t)i0 | ((uint32_t)n0 << 16);
-                        prow[j][32 + lane] = (uint32_t)i1 | ((uint32_t)n1 << 16);
-                    } else {
-                        const float q0 = v16_centred(i0), q1 = v16_centred(i1);
-                        float n0 = __shfl_sync(0xFFFFFFFFu, q0, (lane + 1) & 31);
-                        const float t1 = __shfl_sync(0xFFFFFFFFu, q1, 0);
-                        float n1 = __shfl_sync(0xFFFFFFFFu, q1, (lane + 1) & 31);
-                        if (lane == 31) { n0 = t1; n1 = 0.0f; }
-                        prow[j][lane] = as_u32(__floats2half2_rn(q0, n0));
-                        prow[j][32 + lane] = as_u32(__floats2half2_rn(q1, n1));
+                    vrow[j][lane] = f0;
+                    vrow[j][32 + lane] = f1;
+                    if constexpr (!NCC) {
+                        // risky samples: not a plateau but within 2^-10 of an
+                        // integer; per pixel column, whether its 9 window columns
+                        // hold one in this row (bit jj of the warp's byte)
+                        const bool rk0 = !pl0 && fabsf(__fsub_rn(f0, rintf(f0))) < 0x1p-10f;
+                        const bool rk1 = !pl1 && fabsf(__fsub_rn(f1, rintf(f1))) < 0x1p-10f;
+                        const uint32_t q0 = __ballot_sync(0xFFFFFFFFu, rk0), q1 = __ballot_sync(0xFFFFFFFFu, rk1);
+                        if (q0 | q1) {
+                            const uint64_t M = ((uint64_t)q1 << 32) | q0;
+                            uint64_t t = M | (M >> 1);
+                            t |= t >> 2;
+                            t |= t >> 4;
+                            t |= M >> 8;
+                            rk_lo |= (uint32_t)((t >> lane) & 1u) << jj;
+                            rk_hi |= (uint32_t)((t >> (lane + 32)) & 1u) << jj;
+                        }
                     }
                     if (centre_row) {
                         const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, ok0);
@@ -568,6 +707,10 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 };
                 if (sp) rows(std::true_type{});
                 else rows(std::false_type{});
+                if constexpr (!NCC) {
+                    sm.rkcol[buf][warp][lane] = (uint8_t)rk_lo;
+                    sm.rkcol[buf][warp][32 + lane] = (uint8_t)rk_hi;
+                }
             }
             if (staged) phase ^= 1u << buf;
             __syncthreads();
@@ -575,95 +718,137 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             if constexpr (NCC) {
                 if (do_cost) {
                     // window of output row r: sample rows pr0 + r + 1 .. + 5,
-                    // columns pc + 2 .. pc + 6; row sums slide down the column
-                    const uint32_t* bp = &sm.pair[buf][pr0 + 1][pc + 2];
-                    const uint32_t* ap = &sm.ncc.refp[pr0 + 1][pc + 2];
-                    int hb[5], hbb[5], hab[5];
-                    int Sb = 0, Sbb = 0, Sab = 0;
+                    // columns pc + 2 .. pc + 6; the last five rows are kept in
+                    // registers (a ring indexed by the unrolled row)
+                    const float* bp = &sm.val[buf][0][pc + 2];
+                    const float* ap = &sm.ncc.refv[pr0 + 1][pc + 2];
+                    float rb[5][5], ra[5][5];
                     const int sh = a.views.side[k] < 0 ? 0 : 16;
 #pragma unroll
                     for (int jr = 0; jr < CH + 4; ++jr) {
-                        const uint32_t w0 = bp[jr * SW], w1 = bp[jr * SW + 2], w2 = bp[jr * SW + 4];
-                        const uint32_t x0 = ap[jr * SW], x1 = ap[jr * SW + 2], x2 = ap[jr * SW + 4];
-                        const int b0 = w0 & 0xFFFF, b1 = w0 >> 16, b2 = w1 & 0xFFFF, b3 = w1 >> 16, b4 = w2 & 0xFFFF;
-                        const int a0 = x0 & 0xFFFF, a1 = x0 >> 16, a2 = x1 & 0xFFFF, a3 = x1 >> 16, a4 = x2 & 0xFFFF;
-                        const int rb = b0 + b1 + b2 + b3 + b4;
-                        const int rbb = b0 * b0 + b1 * b1 + b2 * b2 + b3 * b3 + b4 * b4;
-                        const int rab = a0 * b0 + a1 * b1 + a2 * b2 + a3 * b3 + a4 * b4;
-                        Sb += rb;
-                        Sbb += rbb;
-                        Sab += rab;
-                        if (jr >= 5) {
-                            Sb -= hb[jr % 5];
-                            Sbb -= hbb[jr % 5];
-                            Sab -= hab[jr % 5];
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) {
+                            rb[jr % 5][c] = bp[min(pr0 + 1 + jr, jlast) * SW + c];
+                            ra[jr % 5][c] = ap[jr * SW + c];
                         }
-                        hb[jr % 5] = rb;
-                        hbb[jr % 5] = rbb;
-                        hab[jr % 5] = rab;
                         if (jr >= 4) {
                             const int r = jr - 4;
-                            const int2 rs = sm.ncc.refs[pr0 + r][pc];
-                            const long long cov = 25LL * Sab - (long long)rs.x * Sb;
-                            const long long vb = 25LL * Sbb - (long long)Sb * Sb;
-                            uint32_t c = 255u;
-                            if (rs.y > 0 && vb > 0 && cov > 0) {
-                                // single precision, each step correctly rounded, in the
-                                // oracle's order
-                                const float fa = __int2float_rn(rs.y), fb = __ll2float_rn(vb);
-                                const float ncc = __fdiv_rn(__ll2float_rn(cov), __fsqrt_rn(__fmul_rn(fa, fb)));
+                            const int2 rs2 = sm.ncc.refs[pr0 + r][pc];
+                            // mean of b, then the deviations: sum (b - mb)^2 and
+                            // 25 cov = sum (25 a - sum a)(b - mb) (integer weights)
+                            float sb = 0.0f;
+#pragma unroll
+                            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                                for (int c = 0; c < 5; ++c) sb = __fadd_rn(sb, rb[i][c]);
+                            const float mb = __fdiv_rn(sb, 25.0f);
+                            const float nsa = (float)(-rs2.x);
+                            float vb = 0.0f, cv = 0.0f;
+#pragma unroll
+                            for (int i = 0; i < 5; ++i)
+#pragma unroll
+                                for (int c = 0; c < 5; ++c) {
+                                    const float e = __fsub_rn(rb[i][c], mb);
+                                    vb = __fmaf_rn(e, e, vb);
+                                    cv = __fmaf_rn(__fmaf_rn(25.0f, ra[i][c], nsa), e, cv);
+                                }
+                            uint32_t cost = 255u;
+                            if (rs2.y > 0 && vb > 0.0f && cv > 0.0f) {
+                                // ncc = cov / sqrt(va vb) = cv / (5 sqrt(25 va' vb)), 25 va' = refs.y
+                                const float ncc = __fdiv_rn(cv, __fmul_rn(5.0f, __fsqrt_rn(__fmul_rn((float)rs2.y, vb))));
                                 const float cf = __fmul_rn(255.0f, __fsub_rn(1.0f, ncc));
-                                c = (uint32_t)min(max((int)floorf(__fadd_rn(cf, 0.5f)), 0), 255);
+                                cost = (uint32_t)min(max((int)floorf(__fadd_rn(cf, 0.5f)), 0), 255);
                             }
                             const bool ok = (sm.okm[buf][pr0 + r][pc >> 5] >> (pc & 31)) & 1u;
-                            if (!ok) c = 255u;
-                            slr[r] += c << sh;
+                            if (!ok) cost = 255u;
+                            slr[r] += cost << sh;
                         }
                     }
                 }
             } else
             // ---------------------------------------------------------- census
             if (do_cost) {
-                const uint32_t* base = &sm.pair[buf][pr0][pc];
-                __half2 cen[CH];
-                __half2 acc[CH][4];
-                const __half2 bias = __floats2half2_rn(1024.0f, 1024.0f);
+                const float(*vt)[SW] = sm.val[buf];
+                const float* base = &vt[0][pc];
+                const int jl = jlast - pr0;
+                float cs[CH];
+                uint32_t w[CH][4];
 #pragma unroll
                 for (int r = 0; r < CH; ++r) {
-                    cen[r] = __low2half2(as_h2(base[(r + 3) * SW + 4]));
+                    cs[r] = __fmul_rn(4096.0f, base[(pr0 + min(r + 3, jl)) * SW + 4]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[r][q] = bias;
+                    for (int q = 0; q < 4; ++q) w[r][q] = 0u;
                 }
 #pragma unroll
                 for (int jr = 0; jr < CH + 6; ++jr) {
-                    __half2 wv[5];
+                    float wv[9];
+                    const float* rowp = base + (pr0 + min(jr, jl)) * SW;
 #pragma unroll
-                    for (int p = 0; p < 5; ++p) wv[p] = as_h2(base[jr * SW + 2 * p]);
+                    for (int c = 0; c < 9; ++c) wv[c] = rowp[c];
 #pragma unroll
                     for (int r = 0; r < CH; ++r) {
                         const int dy = jr - r;
                         if (dy < 0 || dy > 6) continue;
 #pragma unroll
-                        for (int p = 0; p < 5; ++p) {
-                            const int m = dy * 5 + p;
-                            const float wt = (float)(1 << (m % 10));
-                            const __half2 w2 = __floats2half2_rn(wt, p == 4 ? 0.0f : wt);
-                            const __half2 bits = __hsub2_sat(cen[r], wv[p]);
-                            acc[r][m / 10] = __hfma2(bits, w2, acc[r][m / 10]);
+                        for (int c = 0; c < 9; ++c) {
+                            const int kb = dy * 9 + c;
+                            if (kb == 31) continue;
+                            // 4096 (V(q) - V(p)): sign = [V(q) < V(p)], bit 30 = the
+                            // difference reaches 2^-11
+                            const float x = __fmaf_rn(wv[c], 4096.0f, -cs[r]);
+                            w[r][cword(kb)] = __funnelshift_l(__float_as_uint(x), w[r][cword(kb)], 2);
                         }
                     }
                 }
                 const int sh = a.views.side[k] < 0 ? 0 : 16;
+                uint32_t fmask = 0u;
 #pragma unroll
                 for (int r = 0; r < CH; ++r) {
                     const uint4 rf = sm.refl[pr0 + r][pc];
-                    uint32_t hcost = __popc((as_u32(acc[r][0]) ^ rf.x) & LAYOUT_MASK) +
-                                     __popc((as_u32(acc[r][1]) ^ rf.y) & LAYOUT_MASK) +
-                                     __popc((as_u32(acc[r][2]) ^ rf.z) & LAYOUT_MASK) +
-                                     __popc((as_u32(acc[r][3]) ^ rf.w) & LAYOUT_MASK);
+                    int hcost = __popc((w[r][0] ^ rf.x) & SIGN_BITS) + __popc((w[r][1] ^ rf.y) & SIGN_BITS) +
+                                __popc((w[r][2] ^ rf.z) & SIGN_BITS) + __popc((w[r][3] ^ rf.w) & SIGN_BITS);
+                    const uint32_t near = (~w[r][0] & big_bits(0)) | (~w[r][1] & big_bits(1)) |
+                                          (~w[r][2] & big_bits(2)) | (~w[r][3] & big_bits(3));
                     const bool ok = (sm.okm[buf][pr0 + r][pc >> 5] >> (pc & 31)) & 1u;
                     if (!ok) hcost = kCensusMax;
-                    slr[r] += hcost << sh;
+                    fmask |= (ok && near) ? (1u << r) : 0u;
+                    slr[r] += (uint32_t)hcost << sh;
+                }
+                // near ties of pixels inside the image.  A pixel whose centre is
+                // an integer and whose window holds no risky sample has only
+                // plateau ties: its FP32 census is exact already.
+                {
+                    const int m = tx0 + pc < W ? jlast - 3 - pr0 : -1;   // last chunk row inside the image
+                    fmask &= m >= CH - 1 ? 0xFFFFFFFFu : (m < 0 ? 0u : (2u << m) - 1u);
+                }
+                if (fmask) {
+                    uint64_t rows = 0;
+#pragma unroll
+                    for (int sw = 0; sw < NWARP; ++sw) rows |= (uint64_t)sm.rkcol[buf][sw][pc] << row_start(sw);
+                    // rows past jlast were not sampled: they repeat row jlast
+                    if (jlast < 63 && ((rows >> jlast) & 1u)) rows |= ~0ull << jlast;
+                    const uint32_t rr = (uint32_t)(rows >> pr0);
+                    uint32_t f = fmask;
+                    while (f) {
+                        const int r = __ffs(f) - 1;
+                        f &= f - 1u;
+                        const float vp = vt[min(pr0 + r + 3, jlast)][pc + 4];
+                        if (vp == rintf(vp) && !((rr >> r) & 0x7Fu)) fmask &= ~(1u << r);
+                    }
+                }
+                uint32_t pend = __ballot_sync(0xFFFFFFFFu, fmask != 0u);
+                while (pend) {
+                    const int src = __ffs(pend) - 1;
+                    const uint32_t fm = __shfl_sync(0xFFFFFFFFu, fmask, src);
+                    const int r = __ffs(fm) - 1;
+                    const int c0 = __shfl_sync(0xFFFFFFFFu, pc, src);
+                    const int j0 = __shfl_sync(0xFFFFFFFFu, pr0, src) + r;
+                    const int d = cen_fix(a, vt, sm.hdf[buf], k, tx0, ty0, j0, c0, jlast, sm.refl[j0][c0], lane);
+                    if (lane == src) {
+                        fmask &= fmask - 1u;
+                        if (d) add_at(slr, r, (uint32_t)(d * (1 << sh)));
+                    }
+                    pend = __ballot_sync(0xFFFFFFFFu, fmask != 0u);
                 }
             }
             buf ^= 1;

@@ -975,7 +975,7 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                                   (int)items.size(), (int*)counter, ctas, cfg.cost != 0, st);
         }
         {
-            StageTimer tm(c, FASSMVS_STAGE_COST, st);
+            StageTimer tm(c, FASSMVS_STAGE_RELAYOUT, st);
             for (int f = 0; f < n; ++f)
                 fm::launch_relayout16((const uint16_t*)fr[f].pSblk, (uint16_t*)fr[f].pS, (size_t)fr[f].w * fr[f].h,
                                       fr[f].Ds, st);

@@ -370,7 +370,7 @@ class Context:
                                              tp, float(eta_r), int(eta_h), _ptr(hits), _stream()))
         return hits
 
-    STAGES = ("pyramid", "census", "cost", "sgm", "wta", "median", "normals", "window")
+    STAGES = ("pyramid", "census", "cost", "sgm", "wta", "median", "normals", "window", "relayout")
 
     DUMPS = ("cost", "window", "dsn", "agg", "argmin", "depth_raw", "depth", "normal")
 
@@ -407,8 +407,8 @@ class Context:
 
     def profile_read(self, reset=True):
         """{stage: (total ms, stage launches)} accumulated since the last reset."""
-        ms = (C.c_double * 8)()
-        cnt = (C.c_uint64 * 8)()
+        ms = (C.c_double * len(self.STAGES))()
+        cnt = (C.c_uint64 * len(self.STAGES))()
         self._check(lib().fassmvs_profile_read(self._h, ms, cnt, 1 if reset else 0))
         return {n: (ms[i], int(cnt[i])) for i, n in enumerate(self.STAGES)}
 

@@ -92,6 +92,29 @@ def _last_use(s):
     return lu
 
 
+def relative_pose(Rr, tr, Rk, tk):
+    """Reference -> view k pose from two world -> camera poses,
+    X_k = R_k R_r^T X_r + (t_k - R_k R_r^T t_r), summed in the order the
+    server forms it (plain FP64 products and sums, no fused multiply-add), so
+    that one estimate per keyframe and the server get identical cameras."""
+    Rr = [[float(v) for v in row] for row in np.asarray(Rr, np.float64)]
+    Rk_ = [[float(v) for v in row] for row in np.asarray(Rk, np.float64)]
+    R = np.zeros((3, 3))
+    for i in range(3):
+        for j in range(3):
+            v = 0.0
+            for m in range(3):
+                v += Rk_[i][m] * Rr[j][m]          # (R_k R_r^T)_ij
+            R[i, j] = v
+    t = np.zeros(3)
+    for i in range(3):
+        v = float(tk[i])
+        for m in range(3):
+            v -= float(R[i, m]) * float(tr[m])
+        t[i] = v
+    return R, t
+
+
 def _pinned(shape):
     import torch
     return torch.empty(shape, dtype=torch.float32, pin_memory=True)
@@ -203,9 +226,9 @@ def run_plain(streams, cfg, fps=30.0, keep=False):
         Rs, ts, side = [], [], []
         for k in idx:
             Rk, tk = s.poses[k]
-            Rrel = Rk @ Rr.T
+            Rrel, trel = relative_pose(Rr, tr, Rk, tk)
             Rs.append(Rrel)
-            ts.append(tk - Rrel @ tr)
+            ts.append(trel)
             side.append(-1 if k < r else 1)
         ctx.set_cameras(s.K, np.stack(Rs), np.stack(ts), np.array(side, np.int8))
         d, n, c = ctx.estimate(dev[(si, r)], [dev[(si, k)] for k in idx], _planes(G0))

@@ -65,15 +65,18 @@ def test_census_bit_exact(ctx, orc, H, W):
 
 # ------------------------------------------------------------------ cost volume
 def _shift_scene(seed, W=44, H=30, f=64.0):
+    """Fronto views whose images are the reference shifted by 3 and -2 px; f,
+    the baselines and the plane distances are binary fractions, so plane 2's
+    homographies shift by exactly 3 and -2 px in FP64 and in the kernel."""
     g = np.random.default_rng(seed)
     big = rand_img(g, H, W + 20)
     ref = np.ascontiguousarray(big[:, 10:10 + W])
     nb1 = np.ascontiguousarray(big[:, 13:13 + W])
     nb2 = np.ascontiguousarray(big[:, 8:8 + W])
     z = 16.0
-    k1, k2 = 3 - 1 / 1024, -2 - 1 / 1024
+    k1, k2 = 3, -2
     ts = np.array([[-k1 * z / f, 0, 0], [-k2 * z / f, 0, 0]])
-    drho = 1.0 / (k1 * z)
+    drho = 1.0 / 64.0
     rho0 = 1.0 / z - 2 * drho
     K = np.array([[f, 0, (W - 1) / 2], [0, f, (H - 1) / 2], [0, 0, 1]])
     return ref, [nb1, nb2], [1, -1], K, np.stack([np.eye(3)] * 2), ts, rho0, drho
@@ -153,25 +156,62 @@ def test_cost_volume_ragged_unequal_subsets_windows(ctx, orc, nl, nr):
 
 
 def test_cost_volume_fhd_sampled(ctx, orc):
-    """Full 1920x1080 x 256 planes x 5 views volume, checked on 4000 voxels
-    computed one by one by the oracle."""
+    """Full 1920x1080 x 256 planes x 5 views volume, checked on 200,000
+    voxels computed one by one by the oracle (image borders and the first /
+    last plane included): at most 1e-4 of them may differ."""
     from paper_2112_00821_b300 import synth
     sc, _ = synth.workload("fhd_1920x1080_g256_l4", 0, want_gt=False)
     got = ctx.cost_volume(dev(sc.ref), [dev(x) for x in sc.nbrs], sc.side, sc.K, sc.R, sc.t,
                           sc.plane_n, sc.rho_far, sc.drho, 256)
+    n = 200_000
     g = np.random.default_rng(1)
-    xs = g.integers(0, 1920, 4000)
-    ys = g.integers(0, 1080, 4000)
-    gs = g.integers(0, 256, 4000)
-    # include the image border and the first / last plane
-    xs[:40] = np.r_[np.zeros(20, int), np.full(20, 1919)]
-    gs[40:80] = np.r_[np.zeros(20, int), np.full(20, 255)]
+    xs = g.integers(0, 1920, n)
+    ys = g.integers(0, 1080, n)
+    gs = g.integers(0, 256, n)
+    xs[:400] = np.r_[np.zeros(200, int), np.full(200, 1919)]
+    ys[400:800] = np.r_[np.zeros(200, int), np.full(200, 1079)]
+    gs[800:1200] = np.r_[np.zeros(200, int), np.full(200, 255)]
     exp = orc.cost_at(sc.ref, sc.nbrs, sc.side, sc.K, sc.R, sc.t, sc.plane_n, sc.rho_far, sc.drho,
                       xs, ys, gs)
     gv = host(got[torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda(),
                   torch.from_numpy(gs).cuda()], np.uint16)
-    assert np.mean(gv != exp) <= 1e-3   # 4000 samples: at most a few
+    frac = float(np.mean(gv != exp))
+    print("PARITY cost fhd sampled %d voxels: differing %.3g" % (n, frac))
+    assert frac <= 1e-4, frac
     assert int(host(got, np.uint16).max()) <= 62 * 3
+
+
+def test_cost_volume_fhd_band_every_voxel(ctx, orc):
+    """Every voxel of a 1920 x 128 band through the middle of the benchmark's
+    1080p frame (all 256 planes, 5 views, 31.5 M voxels) against the FP64
+    oracle's band: at most 1e-4 may differ."""
+    from paper_2112_00821_b300 import synth
+    sc, _ = synth.workload("fhd_1920x1080_g256_l4", 0, want_gt=False)
+    got = ctx.cost_volume(dev(sc.ref), [dev(x) for x in sc.nbrs], sc.side, sc.K, sc.R, sc.t,
+                          sc.plane_n, sc.rho_far, sc.drho, 256)
+    y0, y1 = 476, 604
+    band = host(got[y0:y1], np.uint16)[..., :256]
+    exp = orc.cost_band(sc.ref, sc.nbrs, sc.side, sc.K, sc.R, sc.t, sc.plane_n, sc.rho_far, sc.drho, 256,
+                        y0, y1)
+    frac = float(np.mean(band != exp))
+    print("PARITY cost fhd band 1920x128x256: differing %.3g (max |diff| %d)"
+          % (frac, int(np.abs(band.astype(int) - exp).max())))
+    assert frac <= 1e-4, frac
+
+
+def test_cost_volume_vga_scene_vs_fp64(ctx, orc):
+    """The 640x480 random-planes frame (noise 2 DN, 2L + 2R views) over 128
+    planes spanning its sweep: at most 1e-4 of the voxels may differ."""
+    from paper_2112_00821_b300 import synth
+    sc, _ = synth.workload("vga_640x480_g512_l3", 0, want_gt=False)
+    G = 128
+    drho = sc.drho * (sc.G0 - 1) / (G - 1)
+    exp = orc.cost_volume(sc.ref, sc.nbrs, sc.side, sc.K, sc.R, sc.t, sc.plane_n, sc.rho_far, drho, G)
+    got = host(ctx.cost_volume(dev(sc.ref), [dev(x) for x in sc.nbrs], sc.side, sc.K, sc.R, sc.t,
+                               sc.plane_n, sc.rho_far, drho, G), np.uint16)[..., :G]
+    frac = float(np.mean(got != exp))
+    print("PARITY cost vga 640x480x128: differing %.3g" % frac)
+    assert frac <= 1e-4, frac
 
 
 # ------------------------------------------------------------------ SGM
@@ -321,8 +361,25 @@ def _run_estimate(ctx_cfg, sc):
     return out
 
 
+def _erode(m, r):
+    out = m.copy()
+    H, W = m.shape
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            sh = np.zeros_like(m)
+            sh[max(dy, 0):H + min(dy, 0), max(dx, 0):W + min(dx, 0)] = \
+                m[max(-dy, 0):H + min(-dy, 0), max(-dx, 0):W + min(-dx, 0)]
+            out &= sh
+    return out
+
+
 @pytest.mark.parametrize("variant,levels", [(0, 1), (1, 3), (2, 3), (2, 2)])
 def test_estimate_end_to_end(orc, variant, levels):
+    """The whole estimate against the FP64 oracle's on non-occluded pixels
+    (ground-truth visibility in every view, eroded by the 3-pixel reach of the
+    median and the normal window): depth L1-rel <= 1e-3, the 99.9th percentile
+    of the normal angle <= 0.5 degree, confidence within 2e-3 on average.  The
+    numbers over all pixels are printed beside them."""
     from paper_2112_00821_b300 import fassmvs, synth
     if levels == 1:
         sc, _ = synth.workload("tiny_160x120_g64", 3)
@@ -335,10 +392,18 @@ def test_estimate_end_to_end(orc, variant, levels):
     ocfg = orc.make_config(**kw)
     d_e, n_e, c_e = orc.estimate(sc, ocfg)
     rel = np.abs(d - d_e) / d_e
-    assert np.mean(rel) <= 1e-3, np.mean(rel)
-    valid = (np.linalg.norm(n_e, axis=-1) > 0) & (rel < 1e-4)
-    assert np.median(_angle_deg(n[valid], n_e[valid])) <= 0.5
-    assert np.mean(np.abs(conf - c_e)) < 2e-3
+    vis = _erode(synth.visibility_mask(sc), 3) & (np.linalg.norm(n_e, axis=-1) > 0)
+    ang = _angle_deg(n[vis], n_e[vis])
+    cdiff = np.abs(conf - c_e)
+    print("PARITY estimate variant %d levels %d: on %d non-occluded px depth L1-rel %.3g, normal angle "
+          "p99.9 %.3g deg max %.3g deg, confidence mean abs %.3g; on all px depth L1-rel %.3g, "
+          "differing depth %.3g, confidence mean abs %.3g"
+          % (variant, levels, vis.sum(), np.mean(rel[vis]), np.percentile(ang, 99.9), ang.max(),
+             np.mean(cdiff[vis]), np.mean(rel), np.mean(rel > 1e-5), np.mean(cdiff)))
+    assert vis.mean() > 0.3
+    assert np.mean(rel[vis]) <= 1e-3, np.mean(rel[vis])
+    assert np.percentile(ang, 99.9) <= 0.5
+    assert np.mean(cdiff[vis]) < 2e-3
 
 
 def test_estimate_equals_the_stage_entry_points_at_full_size(ctx):
