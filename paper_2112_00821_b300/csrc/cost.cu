@@ -118,98 +118,115 @@ __device__ __forceinline__ float rcp_approx(float x)
 __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h + i), __ldg(h + 9 + i)}; }
 
 // One coordinate of a warped sample.  N / D is the position (D > 0, r ~ 1 / D;
-// r = 0 for a point behind the camera, which then reads cell 0 at offset 0,
-// the clamped position of (-inf, -inf)).  The cell is the floor of the
-// position, from the nearest integer c to the FP32 quotient and the sign of
-// the double-float residual f = (N - c D) / D (accurate to ~3e-7 px, so the
-// cell can be off by one only within that distance of an integer, where both
-// cells give the same value); clamped to [0, cmax] (cmax = image size - 2)
-// with the offset saturated to [0, 1], which is the clamp of the position to
-// the image.  in: the position lies on [0, cmax + 1].
-struct Coord { int i; float f; bool in; };
-__device__ __forceinline__ Coord coord(df N, df D, float r, float cmax)
+// r = 0 for a point behind the camera, which then reads pixel 0 with weight 0,
+// the clamped position of (-inf, -inf)).  The position is split into its
+// nearest integer c and the offset f = (N - c D) / D, both in double-float:
+// c D.hi is formed exactly, N.hi - c D.hi is exact (the terms are close), and
+// one correction step refines the quotient, so f is accurate to ~1e-12 px.
+// The bilinear blend weighs pixel c and its neighbour c + s (s = the sign of
+// f) with |f|, rounded to FP32 (within 1.5e-8); a position outside the image
+// reads the nearest image pixel with weight 0, its clamp.  in: the position
+// lies on [0, size - 1].
+struct Coord { int i, s; float w; bool in; };
+__device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 {
-    const float q = fminf(fmaxf(__fmul_rn(__fadd_rn(N.hi, N.lo), r), -2.0f), cmax + 3.0f);   // NaN -> -2
+    const float q = fminf(fmaxf(__fmul_rn(__fadd_rn(N.hi, N.lo), r), -1.0f), maxf + 1.0f);   // NaN -> -1
     const float c = rintf(q);
-    const float f = __fmul_rn(__fadd_rn(__fmaf_rn(-c, D.hi, N.hi), __fmaf_rn(-c, D.lo, N.lo)), r);
+    const float ph = __fmul_rn(c, D.hi);
+    const float pl = __fmaf_rn(c, D.hi, -ph);
+    const float rh = __fsub_rn(N.hi, ph);
+    const float rl = __fmaf_rn(-c, D.lo, __fsub_rn(N.lo, pl));
+    const float fh = __fmul_rn(__fadd_rn(rh, rl), r);
+    const float fl = __fmul_rn(__fmaf_rn(-fh, D.lo, __fadd_rn(__fmaf_rn(-fh, D.hi, rh), rl)), r);
+    const float f = __fadd_rn(fh, fl);
     const bool neg = f < 0.0f;
-    const float cell = neg ? __fsub_rn(c, 1.0f) : c;
-    const float fr = neg ? __fadd_rn(f, 1.0f) : f;
-    const float cc = fminf(fmaxf(cell, 0.0f), cmax);
-    const float a = __saturatef(__fadd_rn(__fsub_rn(cell, cc), fr));
-    const bool in = cell >= 0.0f && (cell <= cmax || (cell == cmax + 1.0f && fr == 0.0f));
-    return {__float_as_int(__fadd_rn(cc, MAGIC)) - MAGIC_BITS, a, in};
+    const float nb = neg ? __fsub_rn(c, 1.0f) : __fadd_rn(c, 1.0f);
+    const float cc = fminf(fmaxf(c, 0.0f), maxf);
+    const bool edge = cc != c || nb < 0.0f || nb > maxf;
+    const bool in = c >= 0.0f && c <= maxf && !(c == 0.0f && neg) && !(c == maxf && f > 0.0f);
+    return {__float_as_int(__fadd_rn(cc, MAGIC)) - MAGIC_BITS, edge ? 0 : (neg ? -1 : 1), edge ? 0.0f : fabsf(f), in};
 }
 
-// The clamped cell and offsets of one warped sample, and whether its position
-// lies on the image grid.
-struct SPos { int iu, iv; float a, b; };
+// The nearest pixel, neighbour steps and weights of one warped sample, and
+// whether its position lies on the image grid.
+struct SPos { int iu, iv, su, sv; float a, b; };
 
 template <bool WANT_OK>
-__device__ __forceinline__ SPos sample_pos(float wm2, float hm2, df Nu, df Nv, df Dn, bool& ok)
+__device__ __forceinline__ SPos sample_pos(float wm1, float hm1, df Nu, df Nv, df Dn, bool& ok)
 {
     const float dsum = __fadd_rn(Dn.hi, Dn.lo);
     const bool front = dsum > 0.0f;
     // 1 / D to about half an ulp (one Newton step on the approximation)
     const float r0 = rcp_approx(dsum);
     const float r = front ? __fmaf_rn(r0, __fmaf_rn(-dsum, r0, 1.0f), r0) : 0.0f;
-    const Coord cu = coord(Nu, Dn, r, wm2);
-    const Coord cv = coord(Nv, Dn, r, hm2);
+    const Coord cu = coord(Nu, Dn, r, wm1);
+    const Coord cv = coord(Nv, Dn, r, hm1);
     if (WANT_OK) ok = front && cu.in && cv.in;
-    return {cu.i, cv.i, cu.f, cv.f};
+    return {cu.i, cv.i, cu.s, cv.s, cu.w, cv.w};
 }
 
 // 2^23 + b as a float for a byte b (exact)
 __device__ __forceinline__ float bf(int b) { return __int_as_float(BYTE_BITS + b); }
 
-// bilinear blend in lerp form: top = I00 + a (I01 - I00), bottom likewise,
-// value = top + b (bottom - top).  The values are carried minus 128 (the byte
-// differences and the shifted corners are exact), which halves their
-// magnitude and so their rounding error; the census compares differences and
-// the NCC deviations from the window mean, so the shift changes no result.
+// bilinear blend in lerp form about the nearest pixel: top = I0 + a (Iu - I0)
+// along u, bottom likewise one row towards the position, value = top + b
+// (bottom - top) -- the usual bilinear value.  The values are carried minus
+// 128 (the byte differences and the shifted taps are exact), which halves
+// their magnitude and so their rounding error; the census compares
+// differences and the NCC deviations from the window mean, so the shift
+// changes no result.
 constexpr float VBIAS = TWO23 + 128.0f;
 // pl: the four taps are equal (a plateau sample: its value is that integer, exactly)
-__device__ __forceinline__ float blend(int i00, int i01, int i10, int i11, float a, float b, bool& pl)
+__device__ __forceinline__ float blend(int i0, int iu, int iv, int iuv, float a, float b, bool& pl)
 {
-    const float t00 = bf(i00), t10 = bf(i10);
-    const float d0 = __fsub_rn(bf(i01), t00), d1 = __fsub_rn(bf(i11), t10);
-    pl = d0 == 0.0f && d1 == 0.0f && t00 == t10;
-    const float top = __fmaf_rn(a, d0, __fsub_rn(t00, VBIAS));
-    const float bot = __fmaf_rn(a, d1, __fsub_rn(t10, VBIAS));
+    const float t0 = bf(i0), tv = bf(iv);
+    const float d0 = __fsub_rn(bf(iu), t0), d1 = __fsub_rn(bf(iuv), tv);
+    pl = d0 == 0.0f && d1 == 0.0f && t0 == tv;
+    const float top = __fmaf_rn(a, d0, __fsub_rn(t0, VBIAS));
+    const float bot = __fmaf_rn(a, d1, __fsub_rn(tv, VBIAS));
     return __fmaf_rn(b, __fsub_rn(bot, top), top);
 }
 
-// the 2x2 taps from global memory
+// the taps from global memory
 __device__ __forceinline__ float taps_global(const uint8_t* __restrict__ img, int pitch, SPos p, bool& pl)
 {
     const uint8_t* r0 = img + (size_t)p.iv * pitch + p.iu;
-    return blend(__ldg(r0), __ldg(r0 + 1), __ldg(r0 + pitch), __ldg(r0 + pitch + 1), p.a, p.b, pl);
+    const int dv = p.sv * pitch;
+    return blend(__ldg(r0), __ldg(r0 + p.su), __ldg(r0 + dv), __ldg(r0 + dv + p.su), p.a, p.b, pl);
 }
 
-// the 2x2 taps from the staged box whose origin is (sx0, sy0) (in_box true)
+// the taps from the staged box whose origin is (sx0, sy0) (in_box true)
 __device__ __forceinline__ float taps_staged(const uint8_t* stg, int sx0, int sy0, SPos p, bool& pl)
 {
     const uint8_t* r0 = stg + (p.iv - sy0) * kStageBX + (p.iu - sx0);
-    return blend(r0[0], r0[1], r0[kStageBX], r0[kStageBX + 1], p.a, p.b, pl);
+    const int dv = p.sv * kStageBX;
+    return blend(r0[0], r0[p.su], r0[dv], r0[dv + p.su], p.a, p.b, pl);
 }
 
+// the 2x2 footprint lies in the staged box
 __device__ __forceinline__ bool in_box(int sx0, int sy0, SPos p)
 {
-    return (unsigned)(p.iu - sx0) <= (unsigned)(kStageBX - 2) && (unsigned)(p.iv - sy0) <= (unsigned)(kStageBY - 2);
+    return (unsigned)(p.iu + min(p.su, 0) - sx0) <= (unsigned)(kStageBX - 2) &&
+           (unsigned)(p.iv + min(p.sv, 0) - sy0) <= (unsigned)(kStageBY - 2);
 }
 
 // ---------------------------------------------------------------- exact census
 // A census comparison [V(q) < V(p)] is decided on the FP32 values (V = warped
-// value - 128) by the sign of x = 4096 (V(q) - V(p)), one rounding of an exact
-// difference; bit 30 of x records |x| >= 2, i.e. |V(q) - V(p)| >= 2^-11, and a
-// funnel shift by two keeps both bits.  The FP32 values lie within 2e-4 of the
-// FP64 ones (cell offsets within ~3e-7 of the exact ones times tap
-// differences of at most 255, plus the blend's three roundings), so a
-// comparison whose FP32 difference reaches 2^-11 has the FP64 comparison's
-// sign.  The others -- near ties, a few in ten thousand -- are decided again:
-// equal integer values (both samples on plateaus of equal pixels) are a tie
-// in FP64 as well; anything else is recomputed in double-float arithmetic
-// from the homography and the image (cen_fix).
+// value - 128) by the sign of x = 2^15 (V(q) - V(p)), one rounding of an
+// exact difference; bit 30 of x records |x| >= 2, i.e. |V(q) - V(p)| >= 2^-14,
+// and a funnel shift by two keeps both bits.  An FP32 value lies within 2.1e-5
+// of the FP64 value of the sampling reading (the weights within 1.5e-8 of the
+// double-float offsets, times tap differences of at most 255, plus the
+// blend's roundings and the FP32 value itself), so a comparison whose FP32
+// difference reaches 2^-14 = 6.1e-5 has the FP64 comparison's sign.  The
+// others -- near ties -- are decided again: equal values of one reference
+// position or of two plateaus of equal pixels are ties in FP64 as well; the
+// rest are recomputed in double-float from the homography and the image
+// (cen_fix).  Pixels whose centre is an integer and whose window holds no
+// risky sample (a non-plateau value within 2^-13 of an integer) can only
+// have plateau ties and skip that step.
+constexpr float kCensusScale = 32768.0f;
+constexpr float kRiskyBound = 0x1p-13f;
 //
 // The 62 comparisons of a pixel, in window order k = 9 dy + dx (k = 31, the
 // centre, skipped), go to four words: k 0-15, 16-30, 32-47, 48-62.
@@ -304,7 +321,7 @@ __device__ __forceinline__ df sample_exact(const CostArgs& a, const float* h, in
 
 // The correction to the FP32 Hamming distance of pixel (sample row j0 + 3,
 // column c0 + 4) once its near ties -- the comparisons whose FP32 difference
-// stays below 2^-11 -- are decided exactly, computed by the whole warp (lane l
+// stays below 2^-14 -- are decided exactly, computed by the whole warp (lane l
 // takes window positions l and l + 32; the same value returned in every
 // lane).  Equal values of one reference position (a window clamped at the
 // image border) or of two plateaus of equal pixels are ties in FP64 as well;
@@ -314,7 +331,7 @@ __device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW],
                                        int j0, int c0, int jlast, uint4 rf, int lane)
 {
     const float vp = vt[min(j0 + 3, jlast)][c0 + 4];
-    const float cs = __fmul_rn(4096.0f, vp);
+    const float cs = __fmul_rn(kCensusScale, vp);
     const int xp = min(max(tx0 + c0, 0), a.W - 1), yp = min(max(ty0 + j0, 0), a.H - 1);
     int delta = 0;
 #pragma unroll
@@ -323,7 +340,7 @@ __device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW],
         if (kk == 31 || kk >= 63) continue;
         const int dy = kk / 9, dx = kk - 9 * (kk / 9);
         const float vq = vt[min(j0 + dy, jlast)][c0 + dx];
-        const float x = __fmaf_rn(vq, 4096.0f, -cs);
+        const float x = __fmaf_rn(vq, kCensusScale, -cs);
         if (fabsf(x) >= 2.0f) continue;
         const int xq = min(max(tx0 - 4 + c0 + dx, 0), a.W - 1), yq = min(max(ty0 - 3 + j0 + dy, 0), a.H - 1);
         if (vq == vp && ((xq == xp && yq == yp) || vq == rintf(vq))) continue;
@@ -552,7 +569,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     const int rs = row_start(warp), re = row_start(warp + 1);
     const int X0 = min(max(tx0 - 4 + lane, 0), W - 1);
     const int X1 = min(max(tx0 + 28 + lane, 0), W - 1);
-    const float wm2 = (float)(W - 2), hm2 = (float)(H - 2);
+    const float wm1 = (float)(W - 1), hm1 = (float)(H - 1);
     // tile-relative sample row of the image's last row: rows past it are read
     // from it (computing them anew would round differently from the row that
     // was stepped there, and break the exact ties the clamped reading makes)
@@ -653,11 +670,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     const bool centre_row = j >= 3 && j < 3 + PH;
                     SPos p0, p1;
                     if (centre_row) {
-                        p0 = sample_pos<true>(wm2, hm2, u0, v0, d0, ok0);
-                        p1 = sample_pos<true>(wm2, hm2, u1, v1, d1, ok1);
+                        p0 = sample_pos<true>(wm1, hm1, u0, v0, d0, ok0);
+                        p1 = sample_pos<true>(wm1, hm1, u1, v1, d1, ok1);
                     } else {
-                        p0 = sample_pos<false>(wm2, hm2, u0, v0, d0, ok0);
-                        p1 = sample_pos<false>(wm2, hm2, u1, v1, d1, ok1);
+                        p0 = sample_pos<false>(wm1, hm1, u0, v0, d0, ok0);
+                        p1 = sample_pos<false>(wm1, hm1, u1, v1, d1, ok1);
                     }
                     float f0, f1;
                     bool pl0, pl1;
@@ -679,11 +696,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     vrow[j][lane] = f0;
                     vrow[j][32 + lane] = f1;
                     if constexpr (!NCC) {
-                        // risky samples: not a plateau but within 2^-10 of an
+                        // risky samples: not a plateau but within 2^-13 of an
                         // integer; per pixel column, whether its 9 window columns
                         // hold one in this row (bit jj of the warp's byte)
-                        const bool rk0 = !pl0 && fabsf(__fsub_rn(f0, rintf(f0))) < 0x1p-10f;
-                        const bool rk1 = !pl1 && fabsf(__fsub_rn(f1, rintf(f1))) < 0x1p-10f;
+                        const bool rk0 = !pl0 && fabsf(__fsub_rn(f0, rintf(f0))) < kRiskyBound;
+                        const bool rk1 = !pl1 && fabsf(__fsub_rn(f1, rintf(f1))) < kRiskyBound;
                         const uint32_t q0 = __ballot_sync(0xFFFFFFFFu, rk0), q1 = __ballot_sync(0xFFFFFFFFu, rk1);
                         if (q0 | q1) {
                             const uint64_t M = ((uint64_t)q1 << 32) | q0;
@@ -775,7 +792,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 uint32_t w[CH][4];
 #pragma unroll
                 for (int r = 0; r < CH; ++r) {
-                    cs[r] = __fmul_rn(4096.0f, base[(pr0 + min(r + 3, jl)) * SW + 4]);
+                    cs[r] = __fmul_rn(kCensusScale, base[(pr0 + min(r + 3, jl)) * SW + 4]);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) w[r][q] = 0u;
                 }
@@ -793,9 +810,9 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                         for (int c = 0; c < 9; ++c) {
                             const int kb = dy * 9 + c;
                             if (kb == 31) continue;
-                            // 4096 (V(q) - V(p)): sign = [V(q) < V(p)], bit 30 = the
-                            // difference reaches 2^-11
-                            const float x = __fmaf_rn(wv[c], 4096.0f, -cs[r]);
+                            // 2^15 (V(q) - V(p)): sign = [V(q) < V(p)], bit 30 = the
+                            // difference reaches 2^-14
+                            const float x = __fmaf_rn(wv[c], kCensusScale, -cs[r]);
                             w[r][cword(kb)] = __funnelshift_l(__float_as_uint(x), w[r][cword(kb)], 2);
                         }
                     }
