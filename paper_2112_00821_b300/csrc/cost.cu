@@ -50,6 +50,7 @@ constexpr float TWO23 = 8388608.0f;
 struct SmemCost {
     uint64_t mbar[2];                    // staging: completion of the tensor copy into slot 0 / 1
     int stg_x0[2], stg_y0[2], stg_ok[2]; // staging: box origin in the view image, and whether it was issued
+    int stg_in[2];                       // staging: every sample of the pair maps 2 px or more inside the image
     int stg_dead;                        // a staged copy missed its bound: no further staging in this CTA
     float val[2][SH][SW];                // warped values minus 128 (FP32, unrounded)
     uint32_t okm[2][PH][2];              // centre-in-image bit per pixel column
@@ -119,26 +120,21 @@ __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h +
 
 // One coordinate of a warped sample.  N / D is the position (D > 0, r ~ 1 / D;
 // r = 0 for a point behind the camera, which then reads pixel 0 with weight 0,
-// the clamped position of (-inf, -inf)).  The position is split into its
-// nearest integer c and the offset f = (N - c D) / D, both in double-float:
-// c D.hi is formed exactly, N.hi - c D.hi is exact (the terms are close), and
-// one correction step refines the quotient, so f is accurate to ~1e-12 px.
-// The bilinear blend weighs pixel c and its neighbour c + s (s = the sign of
-// f) with |f|, rounded to FP32 (within 1.5e-8); a position outside the image
-// reads the nearest image pixel with weight 0, its clamp.  in: the position
-// lies on [0, size - 1].
+// the clamped position of (-inf, -inf)).  The quotient q = N / D in FP32 and
+// its residual e = N - q D (formed with fused multiply-adds, exact to far
+// below an ulp of q) give the position as q + e / D in double-float; with c
+// the nearest integer, the offset f = (q - c) + e / D (the first difference
+// exact) is accurate to ~1.5e-8 px.  The bilinear blend weighs pixel c and
+// its neighbour c + s (s = the sign of f) with |f|; a position outside the
+// image reads the nearest image pixel with weight 0, its clamp.  in: the
+// position lies on [0, size - 1].
 struct Coord { int i, s; float w; bool in; };
 __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 {
-    const float q = fminf(fmaxf(__fmul_rn(__fadd_rn(N.hi, N.lo), r), -1.0f), maxf + 1.0f);   // NaN -> -1
-    const float c = rintf(q);
-    const float ph = __fmul_rn(c, D.hi);
-    const float pl = __fmaf_rn(c, D.hi, -ph);
-    const float rh = __fsub_rn(N.hi, ph);
-    const float rl = __fmaf_rn(-c, D.lo, __fsub_rn(N.lo, pl));
-    const float fh = __fmul_rn(__fadd_rn(rh, rl), r);
-    const float fl = __fmul_rn(__fmaf_rn(-fh, D.lo, __fadd_rn(__fmaf_rn(-fh, D.hi, rh), rl)), r);
-    const float f = __fadd_rn(fh, fl);
+    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
+    const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
+    const float c = rintf(fminf(fmaxf(q, -1.0f), maxf + 1.0f));     // NaN -> -1
+    const float f = __fadd_rn(__fsub_rn(q, c), __fmul_rn(e, r));
     const bool neg = f < 0.0f;
     const float nb = neg ? __fsub_rn(c, 1.0f) : __fadd_rn(c, 1.0f);
     const float cc = fminf(fmaxf(c, 0.0f), maxf);
@@ -147,9 +143,32 @@ __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
     return {__float_as_int(__fadd_rn(cc, MAGIC)) - MAGIC_BITS, edge ? 0 : (neg ? -1 : 1), edge ? 0.0f : fabsf(f), in};
 }
 
+// The same for a position known to lie 2 px or more inside the image (a pair
+// whose whole sample tile maps there): no clamping, the same arithmetic, so
+// the same values as coord gives there, bit for bit.
+__device__ __forceinline__ Coord coord_in(df N, df D, float r)
+{
+    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
+    const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
+    const float c = rintf(q);
+    const float f = __fadd_rn(__fsub_rn(q, c), __fmul_rn(e, r));
+    return {__float_as_int(__fadd_rn(c, MAGIC)) - MAGIC_BITS, f < 0.0f ? -1 : 1, fabsf(f), true};
+}
+
 // The nearest pixel, neighbour steps and weights of one warped sample, and
 // whether its position lies on the image grid.
 struct SPos { int iu, iv, su, sv; float a, b; };
+
+// a sample of a pair whose whole tile maps 2 px or more inside the image
+__device__ __forceinline__ SPos sample_pos_in(df Nu, df Nv, df Dn)
+{
+    const float dsum = __fadd_rn(Dn.hi, Dn.lo);
+    const float r0 = rcp_approx(dsum);
+    const float r = __fmaf_rn(r0, __fmaf_rn(-dsum, r0, 1.0f), r0);
+    const Coord cu = coord_in(Nu, Dn, r);
+    const Coord cv = coord_in(Nv, Dn, r);
+    return {cu.i, cv.i, cu.s, cv.s, cu.w, cv.w};
+}
 
 template <bool WANT_OK>
 __device__ __forceinline__ SPos sample_pos(float wm1, float hm1, df Nu, df Nv, df Dn, bool& ok)
@@ -237,6 +256,40 @@ __host__ __device__ constexpr int ccount(int w) { return (w & 1) ? 15 : 16; }
 __host__ __device__ constexpr int cbit(int k) { return 2 * (ccount(cword(k)) - 1 - (k - cbase(cword(k)))) + 1; }
 constexpr uint32_t SIGN_BITS = 0xAAAAAAAAu;
 __host__ __device__ constexpr uint32_t big_bits(int w) { return (w & 1) ? 0x15555555u : 0x55555555u; }
+
+// The big-difference bits of the comparisons that a pixel on the image's left
+// (right) edge makes with itself: the window positions left (right) of the
+// centre in its row clamp back onto the pixel, ties in FP64 as in FP32.
+__host__ __device__ constexpr uint32_t self_bits(int w, int k0, int k1)
+{
+    uint32_t m = 0;
+    for (int k = k0; k <= k1; ++k)
+        if (k != 31 && cword(k) == w) m |= 1u << (cbit(k) - 1);
+    return m;
+}
+constexpr uint32_t kSelfLeft = self_bits(1, 27, 30);    // dy = 0, dx = -4 .. -1
+constexpr uint32_t kSelfRight = self_bits(2, 32, 35);   // dy = 0, dx = 1 .. 4
+
+// Whether a pixel on the top or bottom image row (sample row j0 + 3, column
+// c0 + 4, reference position (X, Y)) has a near tie that the census must
+// decide again, i.e. one that is not a tie of the pixel with itself (window
+// positions clamped back onto it) or of two plateaus.
+__device__ __noinline__ bool cen_border_near(const float (*vt)[SW], int j0, int c0, int jlast, int X, int Y, int W,
+                                             int H)
+{
+    const float vp = vt[min(j0 + 3, jlast)][c0 + 4];
+    const float cs = __fmul_rn(kCensusScale, vp);
+    for (int kk = 0; kk < 63; ++kk) {
+        if (kk == 31) continue;
+        const int dy = kk / 9, dx = kk - 9 * (kk / 9);
+        const float vq = vt[min(j0 + dy, jlast)][c0 + dx];
+        if (fabsf(__fmaf_rn(vq, kCensusScale, -cs)) >= 2.0f) continue;
+        const int xq = min(max(X - 4 + dx, 0), W - 1), yq = min(max(Y - 3 + dy, 0), H - 1);
+        if (vq == vp && ((xq == X && yq == Y) || vq == rintf(vq))) continue;
+        return true;
+    }
+    return false;
+}
 
 // canonical 9x7 census word -> the sign bits of the four comparison words
 __device__ __forceinline__ uint4 to_layout(uint64_t c)
@@ -386,6 +439,7 @@ __device__ __forceinline__ void stage_init(SmemCost& sm)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sm.stg_dead = 0;
         sm.stg_ok[0] = sm.stg_ok[1] = 0;
+        sm.stg_in[0] = sm.stg_in[1] = 0;
     }
     __syncthreads();
 }
@@ -454,7 +508,7 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
         vmax = fmaxf(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, o));
     }
     if (lane == 0) {
-        int ok = 0, x0 = 0, y0 = 0;
+        int ok = 0, x0 = 0, y0 = 0, in = 0;
         if (all_front && !sm.stg_dead) {
             const float wm = (float)(a.W - 1), hm = (float)(a.H - 1);
             const float ulo = fminf(fmaxf(umin, 0.0f), wm), uhi = fminf(fmaxf(umax, 0.0f), wm);
@@ -462,10 +516,16 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
             x0 = max((int)floorf(ulo) - 2, 0) & ~15;
             y0 = max((int)floorf(vlo) - 2, 0);
             ok = (int)floorf(uhi) + 3 <= x0 + kStageBX - 1 && (int)floorf(vhi) + 3 <= y0 + kStageBY - 1;
+            // a rectangle in front of the camera maps onto the convex hull of
+            // its corners' images, so with a corner error far below a pixel
+            // every sample of the pair then lies in [1, size - 2] with its
+            // neighbour taps, all inside the box
+            in = ok && umin >= 2.0f && vmin >= 2.0f && umax <= (float)(a.W - 3) && vmax <= (float)(a.H - 3);
         }
         sm.stg_x0[slot] = x0;
         sm.stg_y0[slot] = y0;
         sm.stg_ok[slot] = ok;
+        sm.stg_in[slot] = in;
         if (ok && !a.stage_test)
             stage_issue(&sm.mbar[slot], stg + slot * kStageBX * kStageBY,
                         static_cast<const char*>(a.tmaps) + (size_t)k * 128, x0, y0);
@@ -599,6 +659,10 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     }
     cplo = __reduce_min_sync(0xFFFFFFFFu, cplo);
     cphi = __reduce_max_sync(0xFFFFFFFFu, cphi);
+    // near-tie bits of the census words that count (a pixel on the left /
+    // right image edge leaves out its ties with itself)
+    const uint32_t keep1 = tx0 + pc == 0 ? big_bits(1) & ~kSelfLeft : big_bits(1);
+    const uint32_t keep2 = tx0 + pc == W - 1 ? big_bits(2) & ~kSelfRight : big_bits(2);
 
     int buf = 0;
     for (int g = glo; g < ghi; ++g) {
@@ -628,7 +692,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             // ---------------------------------------------------------- sampling
             if (do_sample) {
                 const uint8_t* sp = ready ? stg + buf * kStageBX * kStageBY : nullptr;
-                const int sx0 = ready ? sm.stg_x0[buf] : 0, sy0 = ready ? sm.stg_y0[buf] : 0;
+                const int sx0 = ready ? sm.stg_x0[buf] : -(1 << 20), sy0 = ready ? sm.stg_y0[buf] : -(1 << 20);
                 const float* h = a.htab + ((size_t)g * a.V + k) * 18;
                 const uint8_t* img = a.views.img[k];
                 if (!NCC && lane < 18) sm.hdf[buf][lane] = __ldg(h + lane);
@@ -648,10 +712,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 float(*vrow)[SW] = sm.val[buf];
                 uint32_t rk_lo = 0u, rk_hi = 0u;
                 // the row loop in two variants, chosen once per (plane, view):
-                // taps from the staged box (global memory outside it), or from
-                // global memory only
-                auto rows = [&](auto staged_tag) {
-                constexpr bool ST = decltype(staged_tag)::value;
+                // every sample 2 px inside the image with its taps in the staged
+                // box (no clamping, no box test), or taps from the staged box
+                // where it holds them and from global memory elsewhere
+                auto rows = [&](auto inner_tag) {
+                constexpr bool IN = decltype(inner_tag)::value;
                 // not unrolled: measured faster than unrolling by 2, 3 or 4
 #pragma unroll 1
                 for (int jj = 0; jj < kMaxRows; ++jj) {
@@ -669,7 +734,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     bool ok0 = false, ok1 = false;
                     const bool centre_row = j >= 3 && j < 3 + PH;
                     SPos p0, p1;
-                    if (centre_row) {
+                    if constexpr (IN) {
+                        p0 = sample_pos_in(u0, v0, d0);
+                        p1 = sample_pos_in(u1, v1, d1);
+                        ok0 = ok1 = true;
+                    } else if (centre_row) {
                         p0 = sample_pos<true>(wm1, hm1, u0, v0, d0, ok0);
                         p1 = sample_pos<true>(wm1, hm1, u1, v1, d1, ok1);
                     } else {
@@ -678,9 +747,13 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     }
                     float f0, f1;
                     bool pl0, pl1;
-                    if constexpr (ST) {
+                    if constexpr (IN) {
+                        f0 = taps_staged(sp, sx0, sy0, p0, pl0);
+                        f1 = taps_staged(sp, sx0, sy0, p1, pl1);
+                    } else {
                         // a row whose taps all lie in the box (the usual case)
-                        // takes one straight shared-memory path
+                        // takes one straight shared-memory path; without a box
+                        // (sp null, origin far away) every tap reads global memory
                         const bool b0 = in_box(sx0, sy0, p0), b1 = in_box(sx0, sy0, p1);
                         if (__all_sync(0xFFFFFFFFu, b0 && b1)) {
                             f0 = taps_staged(sp, sx0, sy0, p0, pl0);
@@ -689,9 +762,6 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                             f0 = b0 ? taps_staged(sp, sx0, sy0, p0, pl0) : taps_global(img, a.pitch, p0, pl0);
                             f1 = b1 ? taps_staged(sp, sx0, sy0, p1, pl1) : taps_global(img, a.pitch, p1, pl1);
                         }
-                    } else {
-                        f0 = taps_global(img, a.pitch, p0, pl0);
-                        f1 = taps_global(img, a.pitch, p1, pl1);
                     }
                     vrow[j][lane] = f0;
                     vrow[j][32 + lane] = f1;
@@ -722,7 +792,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     }
                 }
                 };
-                if (sp) rows(std::true_type{});
+                if (sp && sm.stg_in[buf]) rows(std::true_type{});
                 else rows(std::false_type{});
                 if constexpr (!NCC) {
                     sm.rkcol[buf][warp][lane] = (uint8_t)rk_lo;
@@ -824,8 +894,8 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     const uint4 rf = sm.refl[pr0 + r][pc];
                     int hcost = __popc((w[r][0] ^ rf.x) & SIGN_BITS) + __popc((w[r][1] ^ rf.y) & SIGN_BITS) +
                                 __popc((w[r][2] ^ rf.z) & SIGN_BITS) + __popc((w[r][3] ^ rf.w) & SIGN_BITS);
-                    const uint32_t near = (~w[r][0] & big_bits(0)) | (~w[r][1] & big_bits(1)) |
-                                          (~w[r][2] & big_bits(2)) | (~w[r][3] & big_bits(3));
+                    const uint32_t near = (~w[r][0] & big_bits(0)) | (~w[r][1] & keep1) | (~w[r][2] & keep2) |
+                                          (~w[r][3] & big_bits(3));
                     const bool ok = (sm.okm[buf][pr0 + r][pc >> 5] >> (pc & 31)) & 1u;
                     if (!ok) hcost = kCensusMax;
                     fmask |= (ok && near) ? (1u << r) : 0u;
@@ -850,7 +920,11 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                         const int r = __ffs(f) - 1;
                         f &= f - 1u;
                         const float vp = vt[min(pr0 + r + 3, jlast)][pc + 4];
+                        const int Y = ty0 + pr0 + r;
                         if (vp == rintf(vp) && !((rr >> r) & 0x7Fu)) fmask &= ~(1u << r);
+                        else if ((Y == 0 || Y == H - 1) &&
+                                 !cen_border_near(vt, pr0 + r, pc, jlast, tx0 + pc, Y, W, H))
+                            fmask &= ~(1u << r);
                     }
                 }
                 uint32_t pend = __ballot_sync(0xFFFFFFFFu, fmask != 0u);
