@@ -214,9 +214,19 @@ FASSMVS_API fassmvs_status fassmvs_set_graph(fassmvs_ctx* ctx, int on);
  *                 items fill their last wave best
  *   ctas_per_sm   persistent cost CTAs per SM, 1 or 2, or 0: one short-lived
  *                 CTA per work item (lets stream priorities act per CTA)
- *   sgm_parts     partial sums of the aggregation, 1, 2, 4 or 8 (at most the
- *                 path count), or 0: one per path.  With P parts, P
- *                 directions run concurrently in each of paths/P launches.
+ *   sgm_parts     the form of the aggregation.  1, 2, 4 or 8 (at most the
+ *                 path count): one launch per group of directions over path
+ *                 lines, with that many partial sums (P directions run
+ *                 concurrently in each of paths/P launches), then the
+ *                 winner-takes-all; 0 (default): one partial sum per path.
+ *                 -1: the two-pass wavefront form -- pass A runs the paths
+ *                 from the left and from above, top row first, and stores
+ *                 their sum; pass B runs the other paths from the bottom
+ *                 right, adds that sum and takes the winner, the parabola
+ *                 and the depth in place (8 bytes of DRAM traffic per voxel,
+ *                 no aggregate stored, no separate winner-takes-all);
+ *                 it needs cooperative launches, without them -1 means 0.
+ *                 Every form gives the same bits.
  *   no_staging    0: the cost kernel stages the view images in shared memory
  *                 by TMA where their rows are 16-byte aligned (default);
  *                 1: it reads them from global memory. */
@@ -557,8 +567,8 @@ enum {
     FASSMVS_STAGE_PYRAMID = 0, /* pyramid levels of all views */
     FASSMVS_STAGE_CENSUS = 1,  /* reference census + per-level homography tables */
     FASSMVS_STAGE_COST = 2,    /* plane-sweep cost volume kernel */
-    FASSMVS_STAGE_SGM = 3,     /* all aggregation paths */
-    FASSMVS_STAGE_WTA = 4,     /* winner-takes-all + refinement */
+    FASSMVS_STAGE_SGM = 3,     /* all aggregation paths (two-pass form: with the winner-takes-all) */
+    FASSMVS_STAGE_WTA = 4,     /* winner-takes-all + refinement (per-direction form only) */
     FASSMVS_STAGE_MEDIAN = 5,  /* 5x5 median */
     FASSMVS_STAGE_NORMALS = 6, /* normals, smoothing, confidence */
     FASSMVS_STAGE_WINDOW = 7,  /* plane windows + surface-normal jumps */

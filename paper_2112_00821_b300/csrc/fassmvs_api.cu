@@ -590,6 +590,7 @@ struct FrameRun {
     double drl = 0;
     void *pS = nullptr, *pSblk = nullptr, *pSb = nullptr, *pdraw = nullptr, *pdmed = nullptr, *pnraw = nullptr, *pnrm = nullptr;
     void *plo = nullptr, *pdI = nullptr, *htab = nullptr, *delta = nullptr, *cref = nullptr;
+    void* pring = nullptr;   // two-pass aggregation: rings between row blocks
 };
 
 fassmvs_status check_frame(fassmvs_ctx* c, const fassmvs_frame& f, int L, int idx)
@@ -626,7 +627,14 @@ std::string fname(int f, const char* what)
     return b;
 }
 
-void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0, int parts,
+// control words of the two-pass aggregation of up to kWaveBatch frames: the
+// two passes' tickets, then per frame its flags (fm::wave_flag_bytes of the
+// tallest frame the checks allow)
+constexpr size_t kWaveCtlHead = 256;
+constexpr size_t kWaveCtlFrame = 2 * 2 * 1024 * sizeof(int);
+constexpr size_t kWaveCtlBytes = kWaveCtlHead + fm::kWaveBatch * kWaveCtlFrame;
+
+void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0, int parts, int wave_cap,
                           std::vector<std::pair<std::string, size_t>>& out)
 {
     std::map<std::string, size_t> m;
@@ -641,7 +649,8 @@ void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0
         const size_t Ds = (size_t)((D + 15) & ~15);
         need("S", 2 * np * Ds);
         need("Sblk", 2 * np * Ds);
-        need("Sbar", 2 * np * Ds * parts);
+        if (parts > 0) need("Sbar", 2 * np * Ds * parts);
+        else need("wring", fm::wave_ring_bytes(w, h, wave_cap, nullptr));
         need("draw", 4 * np);
         need("nraw", 12 * np);
         need("cref", 8 * np);
@@ -680,9 +689,12 @@ fassmvs_status ctx_reserve(fassmvs_ctx* c, size_t bytes)
     FM_TRY(ensure(c, "stageA", bytes, &p));
     FM_TRY(ensure(c, "stageB", bytes, &p));
     FM_TRY(ensure(c, "counter", 256, &p));
-    const bool fresh = !c->bufs.count("cost_err");
-    FM_TRY(ensure(c, "cost_err", sizeof(int), &p));
-    if (fresh) FM_TRY(cuda_check(c, cudaMemset(p, 0, sizeof(int)), "memset"));
+    FM_TRY(ensure(c, "wave_ctl", kWaveCtlBytes, &p));
+    for (const char* name : {"cost_err", "sgm_err"}) {
+        const bool fresh = !c->bufs.count(name);
+        FM_TRY(ensure(c, name, sizeof(int), &p));
+        if (fresh) FM_TRY(cuda_check(c, cudaMemset(p, 0, sizeof(int)), "memset"));
+    }
     return FASSMVS_OK;
 }
 
@@ -693,11 +705,18 @@ fassmvs_status fscratch(fassmvs_ctx* c, int f, const char* name, size_t bytes, v
     return ensure(c, fname(f, name).c_str(), bytes, out);
 }
 
-// partial sums of the aggregation: one per direction when automatic
+// partial sums of the per-direction aggregation: one per direction when
+// automatic (and for the two-pass form's fallback)
 int sgm_parts(const fassmvs_tuning& t, int paths)
 {
-    const int p = t.sgm_parts ? t.sgm_parts : paths;
+    const int p = t.sgm_parts > 0 ? t.sgm_parts : paths;
     return p > paths ? paths : p;
+}
+
+int agg_parts(const fassmvs_tuning& t, int paths, int device)
+{
+    if (t.sgm_parts == kSgmTwoPass && fm::wave_capacity(device) > 0) return 0;
+    return sgm_parts(t, paths);
 }
 
 // Picks the staging half for one call and waits until the call that last used
@@ -736,7 +755,8 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
     const fassmvs_config& cfg = c->cfg;
     const int L = cfg.levels;
     const int chunk_planes = tn.chunk_planes, ctas_per_sm = tn.ctas_per_sm;
-    const int parts = sgm_parts(tn, cfg.paths);
+    const int parts = agg_parts(tn, cfg.paths, c->device);   // 0: two-pass form
+    const int wave_cap = parts == 0 ? fm::wave_capacity(c->device) : 0;
     const bool capturing = [&] {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(st, &cs);
@@ -778,6 +798,16 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
     const bool fresh_err = !c->bufs.count("cost_err");
     FM_TRY(ensure(c, "cost_err", sizeof(int), &cost_err));
     if (fresh_err) FM_TRY(cuda_check(c, cudaMemsetAsync(cost_err, 0, sizeof(int), st), "memset"));
+    // the two-pass aggregation's control words and its error word (a row
+    // whose wait on a neighbouring row gave up; read by fassmvs_sync)
+    void *wave_ctl = nullptr, *sgm_err = nullptr;
+    if (parts == 0) {
+        FM_TRY(ensure(c, "wave_ctl", kWaveCtlBytes, &wave_ctl));
+        const bool fresh = !c->bufs.count("sgm_err");
+        FM_TRY(ensure(c, "sgm_err", sizeof(int), &sgm_err));
+        if (fresh) FM_TRY(cuda_check(c, cudaMemsetAsync(sgm_err, 0, sizeof(int), st), "memset"));
+    }
+    static thread_local fm::WaveBatch wb;      // 12 KB: kept off the stack
     Stage sg = stage;
     std::vector<fm::SgmArgs> sargs;
     static thread_local fm::SgmBatch sb;       // 20 KB: kept off the stack
@@ -832,7 +862,8 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             F.Ds = (F.D + 15) & ~15;          // whole 16-plane blocks
             FM_TRY(fscratch(c, f, "S", sizeof(uint16_t) * np * F.Ds, &F.pS));
             FM_TRY(fscratch(c, f, "Sblk", sizeof(uint16_t) * np * F.Ds, &F.pSblk));
-            FM_TRY(fscratch(c, f, "Sbar", sizeof(uint16_t) * np * F.Ds * parts, &F.pSb));
+            if (parts > 0) FM_TRY(fscratch(c, f, "Sbar", sizeof(uint16_t) * np * F.Ds * parts, &F.pSb));
+            else FM_TRY(fscratch(c, f, "wring", fm::wave_ring_bytes(F.w, F.h, wave_cap, nullptr), &F.pring));
             FM_TRY(fscratch(c, f, "draw", sizeof(float) * np, &F.pdraw));
             FM_TRY(fscratch(c, f, "nraw", sizeof(float) * 3 * np, &F.pnraw));
             FM_TRY(fscratch(c, f, "cref", sizeof(uint64_t) * np, &F.cref));
@@ -998,7 +1029,56 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             FM_TRY(cuda_check(c, F.pdI ? cudaMemcpyAsync(p, F.pdI, 8 * np, cudaMemcpyDeviceToDevice, st)
                                        : cudaMemsetAsync(p, 0, 8 * np, st), "capture"));
         }
-        {
+        void *dbg_gwin = nullptr, *dbg_agg = nullptr;
+        if (dbg) {
+            const FrameRun& F = fr[0];
+            FM_TRY(ensure(c, "dbg:agg", 2 * (size_t)F.w * F.h * F.Ds, &dbg_agg));
+            FM_TRY(ensure(c, "dbg:gwin", 4 * (size_t)F.w * F.h, &dbg_gwin));
+        }
+        if (parts == 0) {
+            StageTimer tm(c, FASSMVS_STAGE_SGM, st);
+            // the two-pass form over groups of up to kWaveBatch frames; pass B
+            // takes the winner and writes the depth, so no winner-takes-all
+            // launch follows
+            for (int f0 = 0; f0 < n; f0 += fm::kWaveBatch) {
+                const int m = std::min(n - f0, fm::kWaveBatch);
+                FM_TRY(cuda_check(c, cudaMemsetAsync(wave_ctl, 0, kWaveCtlHead + m * kWaveCtlFrame, st), "memset"));
+                wb.nframes = m;
+                wb.ticket = (int*)wave_ctl;
+                wb.err = (int*)sgm_err;
+                int items = 0;
+                for (int i = 0; i < m; ++i) {
+                    const int f = f0 + i;
+                    const FrameRun& F = fr[f];
+                    const fassmvs_frame& X = *F.fr;
+                    fm::WaveFrame& Wf = wb.f[i];
+                    Wf.a = sargs[f];
+                    Wf.a.Sbar = dbg && f == 0 ? (uint16_t*)dbg_agg : nullptr;
+                    Wf.T1 = (uint16_t*)F.pSblk;   // the blocked volume is dead after the relayout
+                    Wf.delta = (const float*)F.delta;
+                    Wf.G = F.Gl;
+                    Wf.K = intr(F.Kl);
+                    Wf.n0 = (float)X.planes.n[0];
+                    Wf.n1 = (float)X.planes.n[1];
+                    Wf.n2 = (float)X.planes.n[2];
+                    Wf.depth = cfg.median5 ? (float*)F.pdraw : (float*)F.pdmed;
+                    Wf.gwin = dbg && f == 0 ? (int32_t*)dbg_gwin : nullptr;
+                    size_t scal_off = 0;
+                    fm::wave_ring_bytes(F.w, F.h, wave_cap, &scal_off);
+                    Wf.gring = (uint4*)F.pring;
+                    Wf.gscal = (int4*)((char*)F.pring + scal_off);
+                    Wf.ring = fm::wave_ring_cols(F.w, F.h, wave_cap);
+                    Wf.gflag = (int*)((char*)wave_ctl + kWaveCtlHead + i * kWaveCtlFrame);
+                    Wf.nblocks = fm::wave_blocks(F.h);
+                    wb.item0[i] = items;
+                    items += Wf.nblocks;
+                }
+                wb.item0[m] = items;
+                const int ctas = std::min(wave_cap, items);
+                fm::launch_sgm_wave(wb, 0, ctas, st);
+                fm::launch_sgm_wave(wb, 1, ctas, st);
+            }
+        } else {
             StageTimer tm(c, FASSMVS_STAGE_SGM, st);
             // `parts` partial sums: launch g runs, for every part k, direction
             // k * (paths / parts) + g into part k (writing it when g == 0), so
@@ -1037,20 +1117,16 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                 }
             }
         }
-        void* dbg_gwin = nullptr;
-        if (dbg) {
+        if (dbg && parts > 0) {
             const FrameRun& F = fr[0];
             const size_t nv = (size_t)F.w * F.h * F.Ds;
-            void* p;
-            FM_TRY(ensure(c, "dbg:agg", 2 * nv, &p));
-            fm::launch_sum_parts((const uint16_t*)F.pSb, parts, nv, nv, (uint16_t*)p, st);
-            FM_TRY(ensure(c, "dbg:gwin", 4 * (size_t)F.w * F.h, &dbg_gwin));
+            fm::launch_sum_parts((const uint16_t*)F.pSb, parts, nv, nv, (uint16_t*)dbg_agg, st);
         }
         for (int f = 0; f < n; ++f) {
             FrameRun& F = fr[f];
             const fassmvs_frame& X = *F.fr;
             const float nf[3] = {(float)X.planes.n[0], (float)X.planes.n[1], (float)X.planes.n[2]};
-            {
+            if (parts > 0) {
                 StageTimer tm(c, FASSMVS_STAGE_WTA, st);
                 fm::launch_wta_refine((const uint16_t*)F.pSb, (const int32_t*)F.plo, F.w, F.h, F.D, F.Ds, F.Gl,
                                       (const float*)F.delta, intr(F.Kl), nf,
@@ -1115,8 +1191,9 @@ fassmvs_status check_tuning(fassmvs_ctx* c, const fassmvs_tuning& t)
 {
     if (t.chunk_planes < 0 || t.chunk_planes > 256 || t.ctas_per_sm < 0 || t.ctas_per_sm > 2)
         return fail(c, FASSMVS_EINVAL, "chunk_planes 0 (automatic) or 1..256, ctas_per_sm 0 (one CTA per item), 1 or 2");
-    if (t.sgm_parts != 0 && t.sgm_parts != 1 && t.sgm_parts != 2 && t.sgm_parts != 4 && t.sgm_parts != 8)
-        return fail(c, FASSMVS_EINVAL, "sgm_parts 0 (automatic), 1, 2, 4 or 8");
+    if (t.sgm_parts != 0 && t.sgm_parts != kSgmTwoPass && t.sgm_parts != 1 && t.sgm_parts != 2 &&
+        t.sgm_parts != 4 && t.sgm_parts != 8)
+        return fail(c, FASSMVS_EINVAL, "sgm_parts 0 (automatic), -1 (two-pass), 1, 2, 4 or 8");
     if (t.no_staging != 0 && t.no_staging != 1) return fail(c, FASSMVS_EINVAL, "no_staging 0 or 1");
     return FASSMVS_OK;
 }
@@ -1218,9 +1295,10 @@ fassmvs_status fassmvs_autotune(fassmvs_ctx* c, const fassmvs_frame* frames, int
     FM_TRY(set_device(c));
     cudaStream_t st = S(stream);
     // candidates: plane chunks of the persistent cost kernel x resident CTAs
-    // x partial sums of the aggregation (directions run concurrently)
+    // x the aggregation's form (two-pass, or partial sums of concurrent
+    // directions)
     std::vector<fassmvs_tuning> cand;
-    for (int parts : {2, 4, 8}) {
+    for (int parts : {kSgmTwoPass, 2, 4, 8}) {
         if (parts > c->cfg.paths) continue;
         for (int chunk : {0, 64}) cand.push_back({chunk, 2, parts});
     }
@@ -1420,17 +1498,21 @@ fassmvs_status fassmvs_sync(fassmvs_ctx* c)
     FM_TRY(cuda_check(c, e, "device error"));
     // deferred device-side flags: a connected-component walk that hit its cap;
     // a staged copy of the cost kernel that missed its bound (the kernel then
-    // read global memory, so the volume is still right)
+    // read global memory, so the volume is still right); a wait between rows
+    // of the two-pass aggregation that gave up
     struct Flag {
         const char* buf;
         fassmvs_status status;
         const char* msg;
     };
-    const Flag flags[2] = {
+    const Flag flags[3] = {
         {"ccl_err", FASSMVS_EINTERNAL, "a connected-component walk reached its bound (DoG filter)"},
         {"cost_err", FASSMVS_ETIMEOUT,
          "a staged copy of the cost kernel did not complete within its bound (the volume was read from global "
-         "memory)"}};
+         "memory)"},
+        {"sgm_err", FASSMVS_ETIMEOUT,
+         "a row of the two-pass aggregation waited past its bound on a neighbouring row (the depth maps of that "
+         "estimate are not valid)"}};
     for (const Flag& fl : flags) {
         auto it = c->bufs.find(fl.buf);
         if (it == c->bufs.end() || !it->second.p) continue;

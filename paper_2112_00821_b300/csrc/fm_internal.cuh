@@ -130,6 +130,85 @@ struct Intr {
     float fx, fy, cx, cy;
 };
 
+#ifdef __CUDACC__
+// Sub-plane refinement of the winner (Sec. 2.3.4): the vertex of the parabola
+// through the costs (cm, c0, cp) at the plane distances (xm, x0, xp), clamped
+// to [min(xm, xp), max(xm, xp)]; x0 where the three are not convex.  Every
+// operation rounds on its own (no contraction into fused multiply-adds), so
+// every kernel that takes the winner gets the same bits.
+__device__ __forceinline__ float wta_vertex(float x0, float xm, float xp, float c0, float cm, float cp)
+{
+    const float A = __fmul_rn(__fsub_rn(x0, xm), __fsub_rn(c0, cp));
+    const float B = __fmul_rn(__fsub_rn(x0, xp), __fsub_rn(c0, cm));
+    const float den = __fsub_rn(A, B);
+    if (!(den > 0.0f)) return x0;
+    const float num = __fsub_rn(__fmul_rn(__fsub_rn(x0, xm), A), __fmul_rn(__fsub_rn(x0, xp), B));
+    const float xs = __fsub_rn(x0, __fdiv_rn(__fmul_rn(0.5f, num), den));
+    return fminf(fmaxf(xs, fminf(xm, xp)), fmaxf(xm, xp));
+}
+// Depth at pixel (x, y) of the plane n^T X + xs = 0 (Sec. 2.2.1): -xs over
+// n^T K^-1 (x, y, 1)^T, each operation rounded on its own.
+__device__ __forceinline__ float wta_depth(float xs, int x, int y, Intr K, float n0, float n1, float n2)
+{
+    const float u = __fdiv_rn(__fsub_rn((float)x, K.cx), K.fx);
+    const float v = __fdiv_rn(__fsub_rn((float)y, K.cy), K.fy);
+    const float ray = __fadd_rn(__fadd_rn(__fmul_rn(n0, u), __fmul_rn(n1, v)), n2);
+    return __fdiv_rn(-xs, ray);
+}
+#endif
+
+// ---------------------------------------------------------------- two-pass SGM
+// The aggregation and the winner-takes-all in two wavefront passes (sgm_wave.cu):
+// pass A runs the four paths that come from the left and from the row above,
+// top row first, and writes the sum of its paths (T1, the cost volume's
+// layout); pass B runs the other four from the bottom-right corner, adds T1 and
+// takes the winner, the parabola and the depth in place (and, for a debug
+// capture, writes the whole aggregate to Sbar).  A block of kWaveRows image rows
+// is one CTA, one warp per row; the previous row's path costs reach the next
+// warp through shared memory and the next block through a ring in global
+// memory (kWaveRing columns per block boundary, or a whole row).
+constexpr int kWaveRows = 8;
+constexpr int kWaveRing = 32;
+constexpr int kWaveBatch = 16;
+struct WaveFrame {
+    SgmArgs a;                    // S, lo, dI, img, sizes, layout, penalties (a.Sbar: debug aggregate or null)
+    uint16_t* T1;                 // pass A sums, the cost volume's layout
+    const float* delta;           // plane distances (winner-takes-all)
+    int G;                        // planes of the level list (entries of delta)
+    Intr K;
+    float n0, n1, n2;
+    float* depth;
+    int32_t* gwin;                // winning plane per pixel (may be null)
+    uint4* gring;                 // per block boundary: [ring][3][32] path costs
+    int4* gscal;                  // per block boundary: [ring][4] scalars
+    int ring;                     // columns of each ring (a power of two)
+    int* gflag;                   // per block boundary: producer columns done, consumer columns done
+    int nblocks;                  // ceil(H / kWaveRows)
+};
+struct WaveBatch {
+    WaveFrame f[kWaveBatch];
+    int nframes;
+    int item0[kWaveBatch + 1];    // first CTA item of each frame (items in frame order)
+    int* ticket;                  // item counter (zeroed before the launch)
+    int* err;                     // raised when a wait gives up
+};
+// blocks of kWaveRows rows of an H-row image
+int wave_blocks(int H);
+// per frame of a batch, the caller provides the rings between its row blocks
+// (wave_ring_cols columns each: kWaveRing when every block of the frame is
+// resident at once, i.e. wave_blocks(H) <= cap, else a whole row, so that no
+// block waits on the block below it) -- path costs first, the scalars at
+// *scal_off -- and zeroed flag words (wave_flag_bytes)
+int wave_ring_cols(int W, int H, int cap);
+size_t wave_ring_bytes(int W, int H, int cap, size_t* scal_off);
+size_t wave_flag_bytes(int H);
+// CTAs of the two-pass kernels resident at once on the device (0: no
+// cooperative launch)
+int wave_capacity(int device);
+// pass 0 or 1 with `ctas` persistent CTAs (at most wave_capacity), launched
+// cooperatively; b.ticket[pass] must be zero
+void launch_sgm_wave(const WaveBatch& b, int pass, int ctas, cudaStream_t st);
+
 // Sbar may hold nparts partial sums, part_stride elements apart (summed here);
 // pstride / bstride / bshift as in CostArgs (pstride 0: the [H][W][Ds] layout)
 void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds, int G,

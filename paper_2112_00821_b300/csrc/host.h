@@ -89,8 +89,15 @@ fassmvs_status stage_reserve(fassmvs_ctx* c, size_t bytes);
 // stage_reserve plus the device mirrors of `bytes` and the work counter
 fassmvs_status ctx_reserve(fassmvs_ctx* c, size_t bytes);
 
-// partial sums of the aggregation for a tuning
+// sgm_parts value of the two-pass wavefront aggregation
+constexpr int kSgmTwoPass = -1;
+// partial sums of the per-direction aggregation for a tuning
 int sgm_parts(const fassmvs_tuning& t, int paths);
+// what the aggregation of a batch runs as on `device`: 0 for the two-pass
+// wavefront form with the winner-takes-all fused (sgm_parts -1, where the
+// device launches cooperative kernels), else the partial sums of the
+// per-direction form
+int agg_parts(const fassmvs_tuning& t, int paths, int device);
 
 // The coarse-to-fine estimate of n frames sharing launches (Sec. 2.1 per
 // frame); pyrs, when not NULL, gives resident image pyramids per frame.
@@ -101,8 +108,9 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
 fm::DogWeights dog_weights();
 
 // Largest size over the levels of every per-frame scratch buffer run_batch
-// asks for (by name) when the pyramids are resident.
-void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0, int parts,
+// asks for (by name) when the pyramids are resident; parts as agg_parts
+// gives, wave_cap = fm::wave_capacity of the device.
+void frame_scratch_layout(const fassmvs_config& cfg, int W, int H, int V, int G0, int parts, int wave_cap,
                           std::vector<std::pair<std::string, size_t>>& out);
 
 }  // namespace fmh

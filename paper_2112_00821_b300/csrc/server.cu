@@ -441,7 +441,9 @@ fassmvs_status fassmvs_server_create(const fassmvs_config* cfg, const fassmvs_se
     if (scfg->mem_budget < 4096) return sfail(nullptr, FASSMVS_EINVAL, "mem_budget below 4 KiB");
     if (scfg->deadline_ms < 0) return sfail(nullptr, FASSMVS_EINVAL, "deadline_ms must be >= 0");
     if (scfg->overlap_queue < 0) return sfail(nullptr, FASSMVS_EINVAL, "overlap_queue must be >= 0");
-    if (sgm_parts(scfg->tuning, cfg->paths) != sgm_parts(scfg->tuning_overlap, cfg->paths))
+    // one scratch layout serves both tunings: the same aggregation form
+    if ((scfg->tuning.sgm_parts == kSgmTwoPass) != (scfg->tuning_overlap.sgm_parts == kSgmTwoPass) ||
+        sgm_parts(scfg->tuning, cfg->paths) != sgm_parts(scfg->tuning_overlap, cfg->paths))
         return sfail(nullptr, FASSMVS_EINVAL, "tuning and tuning_overlap must give the same sgm_parts");
     auto* s = new fassmvs_server();
     s->cfg = *cfg;
@@ -734,7 +736,8 @@ fassmvs_status fassmvs_server_submit(fassmvs_server* s, const fassmvs_request* r
         return sfail(s, FASSMVS_EINVAL, "request %lld: a depth map of that id is already kept", (long long)r->id);
     // scratch layout of the request
     std::vector<std::pair<std::string, size_t>> sizes;
-    frame_scratch_layout(s->cfg, F0->W, F0->H, (int)q->nb.size(), pl.G0, sgm_parts(s->scfg.tuning, s->cfg.paths), sizes);
+    frame_scratch_layout(s->cfg, F0->W, F0->H, (int)q->nb.size(), pl.G0,
+                         agg_parts(s->scfg.tuning, s->cfg.paths, s->device), fm::wave_capacity(s->device), sizes);
     if (r->host_outputs) {
         const size_t np = (size_t)F0->W * F0->H;
         sizes.push_back({"out:depth", 4 * np});

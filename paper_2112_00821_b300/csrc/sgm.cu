@@ -180,10 +180,9 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
                     }
                     const uint32_t lp0 = __shfl_sync(FULL, Lp[0], 0) & 0xFFFFu;
                     const int lastl = (D - 1) >> 3, lasti = (D - 1) & 7;
-                    uint32_t lsel = Lp[0];
-#pragma unroll
-                    for (int j = 1; j < 4; ++j)
-                        if ((lasti >> 1) == j) lsel = Lp[j];
+                    // Lp[lasti >> 1] by selects (an indexed read would go to local memory)
+                    const uint32_t l01 = (lasti & 2) ? Lp[1] : Lp[0], l23 = (lasti & 2) ? Lp[3] : Lp[2];
+                    const uint32_t lsel = (lasti & 4) ? l23 : l01;
                     const uint32_t lpw = __shfl_sync(FULL, lsel, lastl);
                     const uint32_t lpD = (lasti & 1) ? (lpw >> 16) : (lpw & 0xFFFFu);
                     if (lane == 0) {

@@ -108,19 +108,9 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
     const int g = min(max((lo ? lo[p] : 0) + s, 0), G - 1);
     const float x0 = delta[g];
     float xs = x0;
-    if (s > 0 && s < D - 1) {
-        const float xm = delta[max(g - 1, 0)], xp = delta[min(g + 1, G - 1)];
-        const float c0 = (float)(key >> 8), cm = (float)vm, cp = (float)vp;
-        const float A = (x0 - xm) * (c0 - cp);
-        const float B = (x0 - xp) * (c0 - cm);
-        const float den = A - B;
-        if (den > 0.0f) {
-            xs = x0 - 0.5f * ((x0 - xm) * A - (x0 - xp) * B) / den;
-            xs = fminf(fmaxf(xs, fminf(xm, xp)), fmaxf(xm, xp));
-        }
-    }
-    const float ray = n0 * ((x - K.cx) / K.fx) + n1 * ((y - K.cy) / K.fy) + n2;
-    depth[p] = -xs / ray;
+    if (s > 0 && s < D - 1)
+        xs = wta_vertex(x0, delta[max(g - 1, 0)], delta[min(g + 1, G - 1)], (float)(key >> 8), (float)vm, (float)vp);
+    depth[p] = wta_depth(xs, x, y, K, n0, n1, n2);
     if (gwin) gwin[p] = g;
 }
 

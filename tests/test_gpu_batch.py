@@ -151,13 +151,15 @@ def test_tuning_choices_do_not_change_results():
     items = [_item(sc) for sc in _frames()]
     ref = _single(cfg, items)
     ctx = fassmvs.Context(cfg)
-    for chunk, cps, parts in ((8, 1, 1), (256, 2, 2), (48, 2, 4), (0, 1, 8), (0, 2, 0), (32, 0, 8), (0, 0, 0)):
+    # sgm_parts -1 is the two-pass wavefront form (winner-takes-all fused)
+    for chunk, cps, parts in ((8, 1, 1), (256, 2, 2), (48, 2, 4), (0, 1, 8), (0, 2, 0), (32, 0, 8), (0, 0, 0),
+                              (0, 2, -1), (32, 0, -1)):
         ctx.set_tuning(chunk, cps, parts)
         got = ctx.estimate_batch(items)
         ctx.sync()
         _same(got, ref)
     chunk, cps, parts = ctx.autotune(items)
-    assert chunk in (0, 64) and cps in (0, 1, 2) and parts in (0, 2, 4, 8)
+    assert chunk in (0, 64) and cps in (0, 1, 2) and parts in (-1, 0, 2, 4, 8)
     got = ctx.estimate_batch(items)
     ctx.sync()
     _same(got, ref)

@@ -101,6 +101,20 @@ def test_served_results_match_the_plain_estimate(streams):
             assert torch.equal(x, y), key
 
 
+def test_two_pass_aggregation_serves_the_same_maps(streams):
+    """The two-pass wavefront aggregation (sgm_parts -1) on two lanes whose
+    batches overlap gives the maps of the plain per-direction estimate."""
+    from paper_2112_00821_b300 import fassmvs, serve
+    scfg = fassmvs.server_config(lanes=2, max_batch=3, mem_budget=4 << 30, tuning=(0, 2, -1),
+                                 tuning_overlap=(32, 0, -1), overlap_queue=1)
+    res, so = serve.run_server(streams, _cfg(), scfg, fps=None, keep=True)
+    assert res["server"]["completed"] == sum(len(s.reqs) for s in streams)
+    _, po = serve.run_plain(streams, _cfg(), fps=None, keep=True)
+    for key in so:
+        for x, y in zip(so[key], po[key]):
+            assert torch.equal(x, y), key
+
+
 def test_admission_keeps_memory_within_the_budget(streams):
     from paper_2112_00821_b300 import fassmvs, serve
     # room for the resident frames and about two requests of the larger stream
