@@ -6,10 +6,10 @@
 //      produced cooperatively -- each warp owns 7 or 8 sample rows, each
 //      lane two sample columns (coalesced neighbour-image reads); the
 //      homography's rows are stepped down the column in double-float
-//      arithmetic, the position's cell is the floor of an FP32 quotient and
-//      its offsets inside the cell come from the double-float residual
-//      N - cell * D, so they are accurate to ~1e-7 px; the value is the
-//      bilinear blend in lerp form in FP32, unrounded;
+//      arithmetic, the position's nearest pixel comes from an FP32 quotient
+//      q and its offset from the double-float residual N - q D, so it is
+//      accurate to ~1e-7 px; the value is the bilinear blend in lerp form
+//      about the nearest pixel in FP32, unrounded;
 //   2. one __syncthreads (the sample tile is double-buffered);
 //   3. census: warp w < 7 takes columns 8w .. 8w + 7 of the tile, lane l
 //      column 8w + l % 8 and rows 13 (l / 8) .. + 12 (every lane of the seven
@@ -67,6 +67,7 @@ struct SmemCost {
     int32_t lo[PH][PW];
     int32_t rlo[PH], rhi[PH];            // per pixel row: planes its windows need, [rlo, rhi)
     int glo, ghi;
+    int rskip;                           // tile rows the tile row above covers (computed, not stored)
 };
 
 struct df { float hi, lo; };
@@ -120,21 +121,25 @@ __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h +
 
 // One coordinate of a warped sample.  N / D is the position (D > 0, r ~ 1 / D;
 // r = 0 for a point behind the camera, which then reads pixel 0 with weight 0,
-// the clamped position of (-inf, -inf)).  The quotient q = N / D in FP32 and
-// its residual e = N - q D (formed with fused multiply-adds, exact to far
+// the clamped position of (-inf, -inf)).  The FP32 quotient q of N's high word
+// and its residual e = N - q D (formed with fused multiply-adds, exact to far
 // below an ulp of q) give the position as q + e / D in double-float; with c
-// the nearest integer, the offset f = (q - c) + e / D (the first difference
-// exact) is accurate to ~1.5e-8 px.  The bilinear blend weighs pixel c and
-// its neighbour c + s (s = the sign of f) with |f|; a position outside the
-// image reads the nearest image pixel with weight 0, its clamp.  in: the
-// position lies on [0, size - 1].
+// the integer nearest q, the offset f = (q - c) + e / D (the difference exact,
+// one rounding in the fused multiply-add) is accurate to ~1.5e-8 px.  Where
+// the position lies that close to a half integer, |f| may pass 1/2 by the
+// error of q.  The bilinear blend weighs pixel c and its neighbour c + s
+// (s = the sign of f) with |f| < 1, so it interpolates between them and never
+// extrapolates (a floor-based cell would, by up to that error times the
+// change of slope across the cell edge); a position outside the image reads
+// the nearest image pixel with weight 0, its clamp.  in: the position lies on
+// [0, size - 1].
 struct Coord { int i, s; float w; bool in; };
 __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 {
-    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
+    const float q = __fmul_rn(N.hi, r);
     const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
     const float c = rintf(fminf(fmaxf(q, -1.0f), maxf + 1.0f));     // NaN -> -1
-    const float f = __fadd_rn(__fsub_rn(q, c), __fmul_rn(e, r));
+    const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
     const bool neg = f < 0.0f;
     const float nb = neg ? __fsub_rn(c, 1.0f) : __fadd_rn(c, 1.0f);
     const float cc = fminf(fmaxf(c, 0.0f), maxf);
@@ -148,10 +153,10 @@ __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 // the same values as coord gives there, bit for bit.
 __device__ __forceinline__ Coord coord_in(df N, df D, float r)
 {
-    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
+    const float q = __fmul_rn(N.hi, r);
     const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
     const float c = rintf(q);
-    const float f = __fadd_rn(__fsub_rn(q, c), __fmul_rn(e, r));
+    const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
     return {__float_as_int(__fadd_rn(c, MAGIC)) - MAGIC_BITS, f < 0.0f ? -1 : 1, fabsf(f), true};
 }
 
@@ -257,39 +262,28 @@ __host__ __device__ constexpr int cbit(int k) { return 2 * (ccount(cword(k)) - 1
 constexpr uint32_t SIGN_BITS = 0xAAAAAAAAu;
 __host__ __device__ constexpr uint32_t big_bits(int w) { return (w & 1) ? 0x15555555u : 0x55555555u; }
 
-// The big-difference bits of the comparisons that a pixel on the image's left
-// (right) edge makes with itself: the window positions left (right) of the
-// centre in its row clamp back onto the pixel, ties in FP64 as in FP32.
-__host__ __device__ constexpr uint32_t self_bits(int w, int k0, int k1)
+// The big-difference bits (in word w) of the comparisons that a pixel on
+// image edges makes with itself: window position k = 9 (dy + 3) + dx + 4
+// clamps back onto the pixel when each offset is zero or points out of the
+// image across an edge the pixel lies on (L, R: left, right column; T, B: top,
+// bottom row).  Those comparisons are ties in FP64 as in FP32, so they are
+// left out of the near ties.
+__host__ __device__ constexpr uint32_t self_mask(int w, bool L, bool R, bool T, bool B)
 {
     uint32_t m = 0;
-    for (int k = k0; k <= k1; ++k)
-        if (k != 31 && cword(k) == w) m |= 1u << (cbit(k) - 1);
+    for (int k = 0; k < 63; ++k) {
+        if (k == 31 || cword(k) != w) continue;
+        const int dy = k / 9 - 3, dx = k % 9 - 4;
+        const bool xs = dx == 0 || (L && dx < 0) || (R && dx > 0);
+        const bool ys = dy == 0 || (T && dy < 0) || (B && dy > 0);
+        if (xs && ys) m |= 1u << (cbit(k) - 1);
+    }
     return m;
 }
-constexpr uint32_t kSelfLeft = self_bits(1, 27, 30);    // dy = 0, dx = -4 .. -1
-constexpr uint32_t kSelfRight = self_bits(2, 32, 35);   // dy = 0, dx = 1 .. 4
-
-// Whether a pixel on the top or bottom image row (sample row j0 + 3, column
-// c0 + 4, reference position (X, Y)) has a near tie that the census must
-// decide again, i.e. one that is not a tie of the pixel with itself (window
-// positions clamped back onto it) or of two plateaus.
-__device__ __noinline__ bool cen_border_near(const float (*vt)[SW], int j0, int c0, int jlast, int X, int Y, int W,
-                                             int H)
-{
-    const float vp = vt[min(j0 + 3, jlast)][c0 + 4];
-    const float cs = __fmul_rn(kCensusScale, vp);
-    for (int kk = 0; kk < 63; ++kk) {
-        if (kk == 31) continue;
-        const int dy = kk / 9, dx = kk - 9 * (kk / 9);
-        const float vq = vt[min(j0 + dy, jlast)][c0 + dx];
-        if (fabsf(__fmaf_rn(vq, kCensusScale, -cs)) >= 2.0f) continue;
-        const int xq = min(max(X - 4 + dx, 0), W - 1), yq = min(max(Y - 3 + dy, 0), H - 1);
-        if (vq == vp && ((xq == X && yq == Y) || vq == rintf(vq))) continue;
-        return true;
-    }
-    return false;
-}
+constexpr uint32_t kSelfLeft = self_mask(1, true, false, false, false);    // dy = 0, dx = -4 .. -1
+constexpr uint32_t kSelfRight = self_mask(2, false, true, false, false);   // dy = 0, dx = 1 .. 4
+static_assert(self_mask(0, false, false, false, false) == 0u && self_mask(3, true, true, false, false) == 0u,
+              "a pixel inside the image has no self comparisons");
 
 // canonical 9x7 census word -> the sign bits of the four comparison words
 __device__ __forceinline__ uint4 to_layout(uint64_t c)
@@ -413,13 +407,31 @@ __device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW],
     return __reduce_add_sync(0xFFFFFFFFu, delta);
 }
 
-// slr[r] += v for a run-time r (a register array indexed by constants only)
-template <int N>
-__device__ __forceinline__ void add_at(uint32_t (&slr)[N], int r, uint32_t v)
+// The near ties that the census's filter leaves (fmask: this lane's chunk
+// rows, pixel rows pr0 + r at column pc), decided exactly by cen_fix, one
+// pixel at a time for the whole warp; corr[r] gets the change of chunk row r's
+// Hamming distance (zero for the others).  Called by the whole warp, and out
+// of line: about one warp-pair in thirty has a pixel left here.
+__device__ __noinline__ void fix_ties(const CostArgs& a, const SmemCost& sm, int buf, int k, int tx0, int ty0,
+                                      int pr0, int pc, int jlast, uint32_t fmask, int lane, int* corr)
 {
+    const float(*vt)[SW] = sm.val[buf];
 #pragma unroll
-    for (int i = 0; i < N; ++i)
-        if (i == r) slr[i] += v;
+    for (int r = 0; r < CH; ++r) corr[r] = 0;
+    uint32_t pend = __ballot_sync(0xFFFFFFFFu, fmask != 0u);
+    while (pend) {
+        const int src = __ffs(pend) - 1;
+        const uint32_t fm = __shfl_sync(0xFFFFFFFFu, fmask, src);
+        const int r = __ffs(fm) - 1;
+        const int c0 = __shfl_sync(0xFFFFFFFFu, pc, src);
+        const int j0 = __shfl_sync(0xFFFFFFFFu, pr0, src) + r;
+        const int d = cen_fix(a, vt, sm.hdf[buf], k, tx0, ty0, j0, c0, jlast, sm.refl[j0][c0], lane);
+        if (lane == src) {
+            fmask &= fmask - 1u;
+            corr[r] += d;
+        }
+        pend = __ballot_sync(0xFFFFFFFFu, fmask != 0u);
+    }
 }
 
 // ---------------------------------------------------------------- staging
@@ -534,19 +546,20 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
 
 // One tile (bx, by) of one frame, plane chunk bz of nz, with the census (NCC
 // false) or NCC 5x5 cost.  Called by the single-frame grid kernel and by the
-// multi-frame kernel.  ROWSTEP: the volume stores step a 64-bit offset from
-// row to row (fewer instructions; the multi-frame kernel, whose arguments sit
-// in shared memory, has the registers for it, the single-frame one would
-// spill).
-template <bool NCC, bool ROWSTEP>
+// multi-frame kernel, both with their arguments in shared memory.
+template <bool NCC>
 __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int bz, int nz, SmemCost& sm,
                                           uint8_t* stg, uint32_t& phase)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tx0 = bx * PW, ty0 = by * PH;
+    // the last tile row ends on the image's last row (for an image at least a
+    // tile high), so that row is chunk row CH - 1 of the last chunk; its rows
+    // above by * PH, which the tile row above covers, are computed but not
+    // stored
+    const int tx0 = bx * PW, ty0 = a.H >= PH ? min(by * PH, a.H - PH) : 0;
     const int W = a.W, H = a.H;
 
-    if (tid == 0) { sm.glo = a.G; sm.ghi = 0; }
+    if (tid == 0) { sm.glo = a.G; sm.ghi = 0; sm.rskip = by * PH - ty0; }
     __syncthreads();
     for (int i = tid; i < PH * PW; i += THREADS) {
         const int r = i / PW, c = i % PW;
@@ -783,8 +796,9 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                         }
                     }
                     if (centre_row) {
-                        const uint32_t m0 = __ballot_sync(0xFFFFFFFFu, ok0);
-                        const uint32_t m1 = __ballot_sync(0xFFFFFFFFu, ok1);
+                        // every sample of an interior pair lies on the image
+                        const uint32_t m0 = IN ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, ok0);
+                        const uint32_t m1 = IN ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, ok1);
                         if (lane == 0) {
                             sm.okm[buf][j - 3][0] = (m0 >> 4) | (m1 << 28);
                             sm.okm[buf][j - 3][1] = m1 >> 4;
@@ -894,19 +908,36 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     const uint4 rf = sm.refl[pr0 + r][pc];
                     int hcost = __popc((w[r][0] ^ rf.x) & SIGN_BITS) + __popc((w[r][1] ^ rf.y) & SIGN_BITS) +
                                 __popc((w[r][2] ^ rf.z) & SIGN_BITS) + __popc((w[r][3] ^ rf.w) & SIGN_BITS);
-                    const uint32_t near = (~w[r][0] & big_bits(0)) | (~w[r][1] & keep1) | (~w[r][2] & keep2) |
-                                          (~w[r][3] & big_bits(3));
+                    uint32_t k0 = big_bits(0), k1 = keep1, k2 = keep2, k3 = big_bits(3);
+                    // a first chunk row on the image's top row, a last one on its
+                    // bottom row (always chunk row CH - 1, see the tile origin)
+                    const bool eL = tx0 + pc == 0, eR = tx0 + pc == W - 1;
+                    if (r == 0 && ty0 + pr0 == 0) {
+                        k0 &= ~(eL ? self_mask(0, true, false, true, false)
+                                   : (eR ? self_mask(0, false, true, true, false) : self_mask(0, false, false, true, false)));
+                        k1 &= ~(eL ? self_mask(1, true, false, true, false)
+                                   : (eR ? self_mask(1, false, true, true, false) : self_mask(1, false, false, true, false)));
+                    }
+                    if (r == CH - 1 && ty0 + pr0 + CH - 1 == H - 1) {
+                        k2 &= ~(eL ? self_mask(2, true, false, false, true)
+                                   : (eR ? self_mask(2, false, true, false, true) : self_mask(2, false, false, false, true)));
+                        k3 &= ~(eL ? self_mask(3, true, false, false, true)
+                                   : (eR ? self_mask(3, false, true, false, true) : self_mask(3, false, false, false, true)));
+                    }
+                    const uint32_t near = (~w[r][0] & k0) | (~w[r][1] & k1) | (~w[r][2] & k2) | (~w[r][3] & k3);
                     const bool ok = (sm.okm[buf][pr0 + r][pc >> 5] >> (pc & 31)) & 1u;
                     if (!ok) hcost = kCensusMax;
                     fmask |= (ok && near) ? (1u << r) : 0u;
                     slr[r] += (uint32_t)hcost << sh;
                 }
-                // near ties of pixels inside the image.  A pixel whose centre is
-                // an integer and whose window holds no risky sample has only
-                // plateau ties: its FP32 census is exact already.
+                // near ties of pixels inside the image.  A pixel whose centre is an
+                // integer and whose window holds no risky sample has only plateau
+                // ties: its FP32 census is exact already
                 {
                     const int m = tx0 + pc < W ? jlast - 3 - pr0 : -1;   // last chunk row inside the image
                     fmask &= m >= CH - 1 ? 0xFFFFFFFFu : (m < 0 ? 0u : (2u << m) - 1u);
+                    const int r0 = sm.rskip - pr0;                        // first chunk row this tile stores
+                    fmask &= r0 <= 0 ? 0xFFFFFFFFu : (r0 >= CH ? 0u : ~((1u << r0) - 1u));
                 }
                 if (fmask) {
                     uint64_t rows = 0;
@@ -920,26 +951,14 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                         const int r = __ffs(f) - 1;
                         f &= f - 1u;
                         const float vp = vt[min(pr0 + r + 3, jlast)][pc + 4];
-                        const int Y = ty0 + pr0 + r;
                         if (vp == rintf(vp) && !((rr >> r) & 0x7Fu)) fmask &= ~(1u << r);
-                        else if ((Y == 0 || Y == H - 1) &&
-                                 !cen_border_near(vt, pr0 + r, pc, jlast, tx0 + pc, Y, W, H))
-                            fmask &= ~(1u << r);
                     }
                 }
-                uint32_t pend = __ballot_sync(0xFFFFFFFFu, fmask != 0u);
-                while (pend) {
-                    const int src = __ffs(pend) - 1;
-                    const uint32_t fm = __shfl_sync(0xFFFFFFFFu, fmask, src);
-                    const int r = __ffs(fm) - 1;
-                    const int c0 = __shfl_sync(0xFFFFFFFFu, pc, src);
-                    const int j0 = __shfl_sync(0xFFFFFFFFu, pr0, src) + r;
-                    const int d = cen_fix(a, vt, sm.hdf[buf], k, tx0, ty0, j0, c0, jlast, sm.refl[j0][c0], lane);
-                    if (lane == src) {
-                        fmask &= fmask - 1u;
-                        if (d) add_at(slr, r, (uint32_t)(d * (1 << sh)));
-                    }
-                    pend = __ballot_sync(0xFFFFFFFFu, fmask != 0u);
+                if (__any_sync(0xFFFFFFFFu, fmask != 0u)) {
+                    int corr[CH];
+                    fix_ties(a, sm, buf, k, tx0, ty0, pr0, pc, jlast, fmask, lane, corr);
+#pragma unroll
+                    for (int r = 0; r < CH; ++r) slr[r] += (uint32_t)(corr[r] * (1 << sh));
                 }
             }
             buf ^= 1;
@@ -947,20 +966,19 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         // -------------------------------------------------------------- store
         if (do_cost && tx0 + pc < W) {
             // the chunk's pixels are W * pstride elements apart, row by row
-            size_t roff = ROWSTEP ? ((size_t)(ty0 + pr0) * W + tx0 + pc) * a.pstride : 0;
-            const size_t rstride = ROWSTEP ? (size_t)W * a.pstride : 0;
+            size_t roff = ((size_t)(ty0 + pr0) * W + tx0 + pc) * a.pstride;
+            const size_t rstride = (size_t)W * a.pstride;
 #pragma unroll
             for (int r = 0; r < CH; ++r) {
                 const int py = ty0 + pr0 + r;
                 const int s = g - sm.lo[pr0 + r][pc];
-                if (py < H && s >= 0 && s < a.D) {
+                if (py < H && pr0 + r >= sm.rskip && s >= 0 && s < a.D) {
                     const uint32_t sl = slr[r] & 0xFFFFu, sr = slr[r] >> 16;
                     uint32_t vl = 0xFFFFFFFFu, vr = 0xFFFFFFFFu;
                     // (x * ceil(2^32 / n)) >> 32 == x / n exactly for x < 2^16, n <= 16
                     if (a.nL > 0) vl = (uint32_t)(((uint64_t)(sl * a.nmax + (a.nL >> 1)) * a.mL) >> 32);
                     if (a.nR > 0) vr = (uint32_t)(((uint64_t)(sr * a.nmax + (a.nR >> 1)) * a.mR) >> 32);
-                    const size_t poff = ROWSTEP ? roff : ((size_t)py * W + tx0 + pc) * a.pstride;
-                    a.S[poff + (size_t)(s >> a.bshift) * a.bstride + (s & ((1 << a.bshift) - 1))] =
+                    a.S[roff + (size_t)(s >> a.bshift) * a.bstride + (s & ((1 << a.bshift) - 1))] =
                         (uint16_t)min(vl, vr);
                 }
                 roff += rstride;
@@ -970,13 +988,21 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
 }
 
 template <bool NCC>
-__global__ void __launch_bounds__(THREADS, 2) cost_kernel(const CostArgs a)
+__global__ void __launch_bounds__(THREADS, 2) cost_kernel(const __grid_constant__ CostArgs a)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     SmemCost& sm = *reinterpret_cast<SmemCost*>(smraw);
+    // the arguments in shared memory, as the batched form keeps them (the
+    // tile loop then has the registers for 64-bit row offsets)
+    __shared__ CostArgs sa;
+    {
+        const int* src = reinterpret_cast<const int*>(&a);
+        int* dst = reinterpret_cast<int*>(&sa);
+        for (int i = threadIdx.x; i < (int)(sizeof(CostArgs) / sizeof(int)); i += THREADS) dst[i] = src[i];
+    }
     stage_init(sm);
     uint32_t phase = 0;
-    cost_tile<NCC, false>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm, nullptr, phase);
+    cost_tile<NCC>(sa, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm, nullptr, phase);
 }
 
 // Batched form: work items (frame, tile x, tile y, chunk | chunks << 16) of
@@ -1012,7 +1038,7 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
             for (int i = threadIdx.x; i < (int)(sizeof(CostArgs) / sizeof(int)); i += THREADS) dst[i] = src[i];
         }
         __syncthreads();
-        cost_tile<NCC, true>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm, stg, phase);
+        cost_tile<NCC>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm, stg, phase);
         __syncthreads();
         if (!counter) break;
     }
