@@ -1,26 +1,30 @@
 // Plane-sweep census cost volume (Alg. 1 of FaSS-MVS) for sm_103a.
 //
-// A CTA of 8 warps owns a 56 x 52 tile of reference pixels and walks every
+// A CTA of 8 warps owns a 56 x 28 tile of reference pixels and walks every
 // plane its windows need, one (plane, view) pair per iteration:
-//   1. sampling: the 64 x 58 warped sample tile (tile + 9x7 census halo) is
-//      produced cooperatively -- each warp owns 7 or 8 sample rows, each
-//      lane two sample columns (coalesced neighbour-image reads); the
-//      homography's rows are stepped down the column in double-float
-//      arithmetic, the position's nearest pixel comes from an FP32 quotient
-//      q and its offset from the double-float residual N - q D, so it is
-//      accurate to ~1e-7 px; the value is the bilinear blend in lerp form
-//      about the nearest pixel in FP32, unrounded;
+//   1. sampling: the 64 x 34 warped sample tile (tile + 9x7 census halo) is
+//      produced cooperatively -- each warp owns 4 or 5 sample rows, each
+//      lane two sample columns, the view image's taps read from a box staged
+//      in shared memory by TMA; the homography's rows are stepped down the
+//      column in double-float arithmetic, the position's nearest pixel comes
+//      from an FP32 quotient q and its offset from the double-float residual
+//      N - q D, so it is accurate to ~1e-7 px; the value is the bilinear
+//      blend in lerp form about the nearest pixel in FP32, unrounded;
 //   2. one __syncthreads (the sample tile is double-buffered);
 //   3. census: warp w < 7 takes columns 8w .. 8w + 7 of the tile, lane l
-//      column 8w + l % 8 and rows 13 (l / 8) .. + 12 (every lane of the seven
+//      column 8w + l % 8 and rows 7 (l / 8) .. + 6 (every lane of the seven
 //      warps busy; rows 72 words apart so the four row chunks fall in
-//      different shared-memory banks); every comparison bit [V(q) < V(p)] is
-//      the sign of the FP32 difference V(q) - V(p) (exact: equal values give
-//      +0), funnel-shifted into two words per pixel; the XOR with the
-//      reference census (pre-arranged in the same bit order) and two
-//      popcounts give the Hamming distance; left / right sums accumulate in
-//      registers over the views and the plane's costs are stored after the
-//      last view.
+//      different shared-memory banks); each comparison [V(q) < V(p)] is
+//      decided on 2^15 (V(q) - V(p)) in FP32, whose sign and whether it
+//      reaches 2 are funnel-shifted into four words per pixel; the XOR of the
+//      sign bits with the reference census (pre-arranged in the same bit
+//      order) and four popcounts give the Hamming distance, and the near ties
+//      are decided exactly (see the exact census below); left / right sums
+//      accumulate in registers over the views and the plane's costs are
+//      stored after the last view.
+// Seven-row chunks keep the census loop's unrolled code small enough for the
+// instruction cache (13-row chunks on 56 x 52 tiles, with fewer halo samples,
+// measured 8-14 % slower).
 // Sampling reading (Alg. 1, shared with the oracle): the value of the
 // neighbour image at the unrounded position H q, bilinear in lerp form,
 // positions clamped to the image.
@@ -32,13 +36,14 @@ namespace fm {
 
 namespace {
 
-constexpr int PW = 56, PH = 52;          // pixel tile
+constexpr int PW = 56, PH = 28;          // pixel tile
 constexpr int SW = 72, SH = PH + 6;      // sample tile rows: 64 samples (PW + 8) in a 72-word stride
 constexpr int NWARP = 8, THREADS = 256;
-constexpr int CH = 13;                   // pixel rows per census chunk (PH / 4)
-constexpr int kCensusWarps = PW / 8;     // 7 warps x (8 columns x 4 chunks of 13 rows)
+constexpr int CH = 7;                    // pixel rows per census chunk (PH / 4)
+static_assert(PH == 4 * CH, "four census chunks per tile column");
+constexpr int kCensusWarps = PW / 8;     // 7 warps x (8 columns x 4 chunks of 7 rows)
 constexpr int kPlanWarp = NWARP - 1;     // plans and issues the staging copies
-// first sample row of warp w's share (7 or 8 rows each)
+// first sample row of warp w's share (4 or 5 rows each)
 __host__ __device__ constexpr int row_start(int w) { return (SH * w) / NWARP; }
 constexpr int kMaxRows = 8;              // the largest share
 static_assert(row_start(NWARP) - row_start(NWARP - 1) <= kMaxRows, "row shares");
@@ -499,7 +504,7 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
 #pragma unroll
         for (int i = 0; i < 9; ++i) hh[i] = __ldg(h + i) + __ldg(h + 9 + i);
         const float x = (float)((lane & 1) ? min(max(tx0 + 59, 0), a.W - 1) : min(max(tx0 - 4, 0), a.W - 1));
-        const float y = (float)((lane & 2) ? min(max(ty0 + 54, 0), a.H - 1) : min(max(ty0 - 3, 0), a.H - 1));
+        const float y = (float)((lane & 2) ? min(max(ty0 + PH + 2, 0), a.H - 1) : min(max(ty0 - 3, 0), a.H - 1));
         const float nu = hh[0] * x + hh[1] * y + hh[2];
         const float nv = hh[3] * x + hh[4] * y + hh[5];
         const float dn = hh[6] * x + hh[7] * y + hh[8];
@@ -634,7 +639,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     __syncthreads();
 
     // census role (warps 0-6): column 8 * warp + lane % 8, rows
-    // 13 * (lane / 8) .. + 12; warp 7 has none
+    // CH * (lane / 8) .. + CH - 1; warp 7 has none
     const int pc = warp * 8 + (lane & 7);
     const int pr0 = (lane >> 3) * CH;
     const bool cact = warp < kCensusWarps;
