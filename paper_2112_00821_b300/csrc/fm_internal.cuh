@@ -167,7 +167,7 @@ __device__ __forceinline__ float wta_depth(float xs, int x, int y, Intr K, float
 // is one CTA, one warp per row; the previous row's path costs reach the next
 // warp through shared memory and the next block through a ring in global
 // memory (kWaveRing columns per block boundary, or a whole row).
-constexpr int kWaveRows = 8;
+constexpr int kWaveRows = 4;
 constexpr int kWaveRing = 32;
 constexpr int kWaveBatch = 16;
 struct WaveFrame {

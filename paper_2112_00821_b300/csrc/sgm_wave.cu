@@ -5,18 +5,19 @@
 // runs the four paths whose predecessor lies to the left or in the row above:
 // (1,0), (0,1), (1,1) and (-1,1).  Pass B walks the image rotated by half a
 // turn -- rows bottom to top, right to left -- and runs the other four:
-// (-1,0), (0,-1), (-1,-1), (1,-1).  One warp owns one row; lane l holds
-// hypotheses 8l .. 8l+7 of the current pixel, two per register.  The
-// horizontal path keeps its predecessor in registers.  The three paths that
-// come from the row above read the predecessor's costs, minimum and winning
-// planes from the warp of that row through a ring of kWaveNs columns in shared
-// memory; the first warp of a block of kWaveRows rows reads them from the last
-// warp of the block above through a ring in global memory.  A warp starts a
-// column once the row above has published the column to its right, and
-// publishes a column once the warp below has read the column kWaveNs places
-// before it (bounded waits; a wait that gives up raises an error word and
-// makes every later wait return at once).  Blocks take tickets in launch order,
-// so the block above always runs first and every wait ends.
+// (-1,0), (0,-1), (-1,-1), (1,-1).  One warp owns one row and steps its
+// paths together (one batched step per column); lane l holds hypotheses
+// 8l .. 8l+7 of the current pixel, two per register.  The horizontal path
+// keeps its predecessor in registers.  The three paths that come from the row
+// above read the predecessor's costs, minimum and winning planes from the warp
+// of that row through a ring of NS columns in shared memory; the first warp of
+// a block of kWaveRows rows reads them from the last warp of the block above
+// through a ring in global memory.  A warp starts a column once the row above
+// has published the column to its right, and publishes a column once the warp
+// below has read the column NS places before it (bounded waits; a wait that
+// gives up raises an error word and makes every later wait return at once).
+// Blocks take tickets in launch order, so the block above always runs first
+// and every wait ends.
 //
 // Pass A writes the sum of its four paths (T1, 16 bits per hypothesis).  Pass
 // B adds its own four and T1: the whole aggregate S_bar of Eq. sgm-aggr,
@@ -29,6 +30,15 @@
 // normalised form with windows); the sum is exact (every total stays below
 // 2^16, checked on the host), so the results equal the per-direction kernels'
 // bit for bit.
+//
+// Measured on a single frame it is latency-bound: the wavefront walks
+// 2 H + W columns in sequence (a row starts two columns behind the row above)
+// where a path line walks at most max(W, H), and one column step of a row
+// costs about one line step per path (with every wait between rows removed,
+// 2.4 us per column at 160 x 120).  At 1080p x 256 planes (four levels) it
+// takes 52 ms against 5.6 ms for the per-direction kernels and the separate
+// winner-takes-all, so it is the explicit form sgm_parts = -1, not the
+// default.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -58,7 +68,7 @@ __device__ __forceinline__ uint32_t dup2(uint32_t v) { return v | (v << 16); }
 struct WaveSmem {
     uint4 L[R][NS][3][32];
     int4 sc[R][NS][4];
-    uint16_t buf[R][kMaxSlots + 4];        // per warp: the window shift
+    uint16_t buf[R][4 * (kMaxSlots + 4)];  // per warp and path: the window shift
     int prog[R];                           // columns each warp has published
     int cons[R];                           // columns each warp has consumed from the row above
     int item;
@@ -121,93 +131,124 @@ __device__ __forceinline__ int wait_at_least(const int* flag, int need, int* err
     return v;
 }
 
-// One step of one path recurrence (Eq. xsgm in the normalised form, the
-// penalties of Eq. sgm-smooth-* and p2-grad, windows), for the warp's pixel:
-// Lp the predecessor's costs (two slots per register, INF16 outside its
-// window), Mp its minimum, sigma the slot shift lo_p - lo_pred + di.  first:
-// the path starts here (L = S).  Returns the pixel's costs in L, their minimum
-// in M and, for the path-gradient variant, the winning slot (lowest on ties).
+// One step of the NP path recurrences of a pass (Eq. xsgm in the normalised
+// form, the penalties of Eq. sgm-smooth-* and p2-grad, windows) for the
+// warp's pixel, in phases over the paths -- neighbour shuffles and
+// transitions, one shift round through the warp's buffers, the new costs, NP
+// independent minimum reductions -- so that the paths' dependency chains
+// overlap.  Per path p: Lp the predecessor's costs (two slots per register,
+// INF16 outside its window), Mp its minimum, sigma the slot shift
+// lo_p - lo_pred + di, P2 the large penalty; first: the path starts here
+// (L = S).  Returns the pixel's costs in L, their minimum in M and, for the
+// path-gradient variant, the winning slot (lowest on ties).  The arithmetic of
+// each path is that of sgm.cu's line walk, so the sums agree bit for bit.
 struct PathIn {
     int D, s0, lane, variant, p1;
     uint32_t vmask[4];
 };
+constexpr int kBufLen = kMaxSlots + 4;     // one shift buffer per path and warp
 
-__device__ __forceinline__ void path_step(const PathIn& q, const uint32_t (&Sv)[4], const uint32_t (&Lp)[4],
-                                          uint32_t Mp, bool first, int sigma, int P2, uint16_t* buf,
-                                          uint32_t (&L)[4], uint32_t& M, int& wslot)
+template <int NP>
+__device__ __forceinline__ void paths_step(const PathIn& q, const uint32_t (&Sv)[4], const uint32_t (&Lp)[NP][4],
+                                           const uint32_t (&Mp)[NP], const bool (&first)[NP],
+                                           const int (&sigma)[NP], const int (&P2)[NP], uint16_t* buf,
+                                           uint32_t (&L)[NP][4], uint32_t (&M)[NP], int (&wslot)[NP])
 {
-    if (first) {
+    const uint32_t P1 = (uint32_t)q.p1, P1P1 = dup2(P1);
+    uint32_t T[NP][4], cap[NP];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) L[j] = (Sv[j] & q.vmask[j]) | (INF2 & ~q.vmask[j]);
-    } else {
-        uint32_t left = __shfl_up_sync(FULL, Lp[3], 1), right = __shfl_down_sync(FULL, Lp[0], 1);
+    for (int p = 0; p < NP; ++p) {
+        uint32_t left = __shfl_up_sync(FULL, Lp[p][3], 1), right = __shfl_down_sync(FULL, Lp[p][0], 1);
         if (q.lane == 0) left = INF2;
         if (q.lane == 31) right = INF2;
-        const uint32_t P1 = (uint32_t)q.p1, P1P1 = dup2(P1);
-        const uint32_t cap = Mp + (uint32_t)max(P2, q.p1), cap2 = dup2(cap);
+        cap[p] = Mp[p] + (uint32_t)max(P2[p], q.p1);
+        const uint32_t cap2 = dup2(cap[p]);
         // T(s') = min(L'(s'), L'(s'-1) + P1, L'(s'+1) + P1, M' + P2), packed
-        uint32_t T[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const uint32_t pv = __byte_perm(j == 0 ? left : Lp[j - 1], Lp[j], 0x5432);
-            const uint32_t nv = __byte_perm(Lp[j], j == 3 ? right : Lp[j + 1], 0x5432);
-            T[j] = __vimin3_u16x2(Lp[j], cap2, __viaddmin_u16x2(pv, P1P1, nv + P1P1));
+            const uint32_t pv = __byte_perm(j == 0 ? left : Lp[p][j - 1], Lp[p][j], 0x5432);
+            const uint32_t nv = __byte_perm(Lp[p][j], j == 3 ? right : Lp[p][j + 1], 0x5432);
+            T[p][j] = __vimin3_u16x2(Lp[p][j], cap2, __viaddmin_u16x2(pv, P1P1, nv + P1P1));
         }
-        if (sigma != 0) {
-            // shift by sigma slots through the warp's buffer: index k + 2 holds
-            // T(k) for k in [-2, D+1]; beyond the predecessor's window the
-            // transition costs M' + P2 (k = -2, D + 1 and clamped indices)
-            const int D = q.D, s0 = q.s0;
-            uint32_t* b32 = reinterpret_cast<uint32_t*>(buf);
+    }
+    bool shift[NP], any = false;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        shift[p] = !first[p] && sigma[p] != 0;     // warp-uniform
+        any |= shift[p];
+    }
+    if (any) {
+        // shift by sigma slots through the path's buffer: index k + 2 holds
+        // T(k) for k in [-2, D+1]; beyond the predecessor's window the
+        // transition costs M' + P2 (k = -2, D + 1 and clamped indices)
+        const int D = q.D, s0 = q.s0;
+        const int lastl = (D - 1) >> 3, lasti = (D - 1) & 7;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (!shift[p]) continue;
+            uint16_t* bp = buf + p * kBufLen;
+            uint32_t* b32 = reinterpret_cast<uint32_t*>(bp);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                if (s0 + 2 * j + 1 < D) b32[1 + (s0 >> 1) + j] = T[j];
-                else if (s0 + 2 * j < D) buf[2 + s0 + 2 * j] = (uint16_t)(T[j] & 0xFFFFu);
+                if (s0 + 2 * j + 1 < D) b32[1 + (s0 >> 1) + j] = T[p][j];
+                else if (s0 + 2 * j < D) bp[2 + s0 + 2 * j] = (uint16_t)(T[p][j] & 0xFFFFu);
             }
-            const uint32_t lp0 = __shfl_sync(FULL, Lp[0], 0) & 0xFFFFu;
-            const int lastl = (D - 1) >> 3, lasti = (D - 1) & 7;
+            const uint32_t lp0 = __shfl_sync(FULL, Lp[p][0], 0) & 0xFFFFu;
             // Lp[lasti >> 1] by selects (an indexed read would go to local memory)
-            const uint32_t l01 = (lasti & 2) ? Lp[1] : Lp[0], l23 = (lasti & 2) ? Lp[3] : Lp[2];
+            const uint32_t l01 = (lasti & 2) ? Lp[p][1] : Lp[p][0], l23 = (lasti & 2) ? Lp[p][3] : Lp[p][2];
             const uint32_t lsel = (lasti & 4) ? l23 : l01;
             const uint32_t lpw = __shfl_sync(FULL, lsel, lastl);
             const uint32_t lpD = (lasti & 1) ? (lpw >> 16) : (lpw & 0xFFFFu);
             if (q.lane == 0) {
-                buf[0] = (uint16_t)cap;
-                buf[1] = (uint16_t)min(lp0 + P1, cap);
-                buf[D + 2] = (uint16_t)min(lpD + P1, cap);
-                buf[D + 3] = (uint16_t)cap;
+                bp[0] = (uint16_t)cap[p];
+                bp[1] = (uint16_t)min(lp0 + P1, cap[p]);
+                bp[D + 2] = (uint16_t)min(lpD + P1, cap[p]);
+                bp[D + 3] = (uint16_t)cap[p];
             }
-            __syncwarp();
+        }
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (!shift[p]) continue;
+            const uint16_t* bp = buf + p * kBufLen;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int q0 = min(max(s0 + 2 * j + sigma, -2), D + 1) + 2;
-                const int q1 = min(max(s0 + 2 * j + 1 + sigma, -2), D + 1) + 2;
-                T[j] = (uint32_t)buf[q0] | ((uint32_t)buf[q1] << 16);
+                const int q0 = min(max(s0 + 2 * j + sigma[p], -2), D + 1) + 2;
+                const int q1 = min(max(s0 + 2 * j + 1 + sigma[p], -2), D + 1) + 2;
+                T[p][j] = (uint32_t)bp[q0] | ((uint32_t)bp[q1] << 16);
             }
-            __syncwarp();
         }
-        const uint32_t M2 = dup2(Mp);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) L[j] = ((Sv[j] + T[j] - M2) & q.vmask[j]) | (INF2 & ~q.vmask[j]);
+        __syncwarp();
     }
-    if (q.variant == 2) {
-        // key = cost << 8 | slot, one byte permutation per slot
-        uint32_t key = 0xFFFFFFFFu;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const uint32_t M2 = dup2(Mp[p]);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            key = min(key, __byte_perm(L[j], (uint32_t)(q.s0 + 2 * j), 0x5104));
-            key = min(key, __byte_perm(L[j], (uint32_t)(q.s0 + 2 * j + 1), 0x5324));
+            const uint32_t v = first[p] ? Sv[j] : Sv[j] + T[p][j] - M2;
+            L[p][j] = (v & q.vmask[j]) | (INF2 & ~q.vmask[j]);
         }
-        key = __reduce_min_sync(FULL, key);
-        M = key >> 8;
-        wslot = (int)(key & 255u);
-    } else {
-        const uint32_t mm = __vimin3_u16x2(__vimin3_u16x2(L[0], L[1], L[2]), L[3], L[3]);
-        M = __reduce_min_sync(FULL, min(mm & 0xFFFFu, mm >> 16));
-        wslot = 0;
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        if (q.variant == 2) {
+            // key = cost << 8 | slot, one byte permutation per slot
+            uint32_t key = 0xFFFFFFFFu;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                key = min(key, __byte_perm(L[p][j], (uint32_t)(q.s0 + 2 * j), 0x5104));
+                key = min(key, __byte_perm(L[p][j], (uint32_t)(q.s0 + 2 * j + 1), 0x5324));
+            }
+            key = __reduce_min_sync(FULL, key);
+            M[p] = key >> 8;
+            wslot[p] = (int)(key & 255u);
+        } else {
+            const uint32_t mm = __vimin3_u16x2(__vimin3_u16x2(L[p][0], L[p][1], L[p][2]), L[p][3], L[p][3]);
+            M[p] = __reduce_min_sync(FULL, min(mm & 0xFFFFu, mm >> 16));
+            wslot[p] = 0;
+        }
     }
 }
-
 
 // The path directions of a pass, as indices of the direction order of
 // sgm.cu ((1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1)): horizontal,
@@ -305,7 +346,7 @@ __device__ __forceinline__ void load_pix(const WaveFrame& F, size_t pix, int x, 
 
 // One row of one pass, run by one warp.  Pass coordinates (xp, yp): pass A is
 // the image, pass B the image turned by half a turn (x = W-1-xp, y = H-1-yp).
-template <int PASS>
+template <int PASS, bool EIGHT>
 __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, int lane, WaveSmem& sm, int* err)
 {
     const SgmArgs& a = F.a;
@@ -313,7 +354,6 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
     const int yp = blk * R + warp;
     if (yp >= H) return;                   // warp-uniform; no row below waits on it
     const int y = PASS ? H - 1 - yp : yp;
-    const bool eight = a.paths == 8;
     // the row above is the previous warp of this CTA, or the last warp of the
     // CTA of the block above through the global ring; the row below likewise
     const bool up = yp > 0, up_global = up && warp == 0;
@@ -391,7 +431,7 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
                 return o;
             };
             pv = fetch(xp, 0);
-            if (eight) {
+            if (EIGHT) {
                 if (xp > 0) pd = fetch(xp - 1, 1);
                 if (xp + 1 < W) pa = fetch(xp + 1, 2);
             }
@@ -406,7 +446,7 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
                                       : wait_at_least<false>(&sm.cons[warp + 1], need, err, lane);
         }
 
-        // ---- the four paths (Eq. xsgm), each added to the running total
+        // ---- the paths (Eq. xsgm), each added to the running total
         auto di_of = [&](int w, int g1, int g2, int step) {
             int di = 0;
             if (a.variant == 1) di = (int)(int8_t)(cur.dsn >> (8 * w));
@@ -424,39 +464,56 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
         } else {
             tot[0] = tot[1] = tot[2] = tot[3] = 0u;
         }
-        // horizontal: the previous column of this row
-        {
-            uint32_t L[4], M;
-            int ws;
-            const bool first = xp == 0;
-            const int sigma = first ? 0 : lo_p - lo_prev + di_of(0, g1h, g2h, xp);
-            path_step(q, Sv, Lh, Mh, first, sigma, first ? 0 : p2_of(ip_prev), buf, L, M, ws);
+        // the pass's paths in one batched step: p = 0 horizontal (the previous
+        // column of this row), then the paths from the row above (vertical,
+        // diagonal, anti-diagonal), whose steps from the path's start are yp,
+        // min(xp, yp) and min(W-1-xp, yp)
+        constexpr int NP = EIGHT ? 4 : 2;
+        uint32_t Lp[NP][4], Mp[NP];
+        bool first[NP];
+        int sig[NP], p2v[NP], g1c[NP];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                tot[j] += L[j] & q.vmask[j];
-                Lh[j] = L[j];
-            }
-            Mh = M;
-            g2h = g1h;
-            g1h = lo_p + ws;
+        for (int j = 0; j < 4; ++j) Lp[0][j] = Lh[j];
+        Mp[0] = Mh;
+        first[0] = xp == 0;
+        sig[0] = first[0] ? 0 : lo_p - lo_prev + di_of(0, g1h, g2h, xp);
+        p2v[0] = first[0] ? 0 : p2_of(ip_prev);
+        g1c[0] = 0;
+#pragma unroll
+        for (int p = 1; p < NP; ++p) {
+            const Pred& P = p == 1 ? pv : (p == 2 ? pd : pa);
+            const bool have = p == 1 ? up : (p == 2 ? up && xp > 0 : up && xp + 1 < W);
+            const int step = p == 1 ? yp : (p == 2 ? min(xp, yp) : min(W - 1 - xp, yp));
+            first[p] = !have;
+            const int g1 = have ? P.sc.y : 0, g2 = have ? P.sc.z : 0;
+            g1c[p] = g1;
+            Lp[p][0] = P.L.x; Lp[p][1] = P.L.y; Lp[p][2] = P.L.z; Lp[p][3] = P.L.w;
+            Mp[p] = have ? (uint32_t)P.sc.x : 0u;
+            sig[p] = have ? lo_p - P.lo + di_of(p, g1, g2, step) : 0;
+            p2v[p] = have ? p2_of(P.ip) : 0;
         }
-        // the paths from the row above, each published at once for the row
-        // below: the lane's costs and {minimum, winning plane, the
-        // predecessor's winning plane}
-        const int pslot = xp & ((down_global ? NR : NS) - 1);
-        auto cross = [&](int w, bool have_pred, const Pred& P, int step) {
-            uint32_t L[4], M;
-            int ws;
-            const bool first = !have_pred;
-            const int g1 = first ? 0 : P.sc.y, g2 = first ? 0 : P.sc.z;
-            const int sigma = first ? 0 : lo_p - P.lo + di_of(w + 1, g1, g2, step);
-            const uint32_t Lp[4] = {P.L.x, P.L.y, P.L.z, P.L.w};
-            path_step(q, Sv, Lp, first ? 0u : (uint32_t)P.sc.x, first, sigma, first ? 0 : p2_of(P.ip), buf, L, M, ws);
+        uint32_t L[NP][4], M[NP];
+        int ws[NP];
+        paths_step<NP>(q, Sv, Lp, Mp, first, sig, p2v, buf, L, M, ws);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) tot[j] += L[j] & q.vmask[j];
-            if (down) {
-                const uint4 lv = make_uint4(L[0], L[1], L[2], L[3]);
-                const int4 sc = make_int4((int)M, lo_p + ws, g1, 0);
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) tot[j] += L[p][j] & q.vmask[j];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Lh[j] = L[0][j];
+        Mh = M[0];
+        g2h = g1h;
+        g1h = lo_p + ws[0];
+        // the paths from the row above are published for the row below: the
+        // lane's costs and {minimum, winning plane, the predecessor's winning
+        // plane}
+        const int pslot = xp & ((down_global ? NR : NS) - 1);
+        if (down) {
+#pragma unroll
+            for (int p = 1; p < NP; ++p) {
+                const int w = p - 1;
+                const uint4 lv = make_uint4(L[p][0], L[p][1], L[p][2], L[p][3]);
+                const int4 sc = make_int4((int)M[p], lo_p + ws[p], g1c[p], 0);
                 if (down_global) {
                     if (act) __stcg(gL_dn + ((size_t)pslot * 3 + w) * 32 + lane, lv);
                     if (lane == 0) __stcg(gS_dn + (size_t)pslot * 4 + w, sc);
@@ -465,13 +522,6 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
                     if (lane == 0) sm.sc[warp][pslot][w] = sc;
                 }
             }
-        };
-        // steps from the start of each path: vertical yp, diagonal
-        // min(xp, yp), anti-diagonal min(W-1-xp, yp)
-        cross(0, up, pv, yp);
-        if (eight) {
-            cross(1, up && xp > 0, pd, min(xp, yp));
-            cross(2, up && xp + 1 < W, pa, min(W - 1 - xp, yp));
         }
         lo_prev = lo_p;
         ip_prev = ip;
@@ -513,8 +563,8 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
 // launch is cooperative (every CTA resident), so with a frame's blocks no
 // more than the CTAs the successor an item waits on is always taken; a frame
 // with more blocks gets whole-row rings and never waits downwards.
-template <int PASS>
-__global__ void __launch_bounds__(R * 32, 2) sgm_wave_kernel(const __grid_constant__ WaveBatch b)
+template <int PASS, bool EIGHT>
+__global__ void __launch_bounds__(R * 32, 4) sgm_wave_kernel(const __grid_constant__ WaveBatch b)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     WaveSmem& sm = *reinterpret_cast<WaveSmem*>(smraw);
@@ -531,9 +581,17 @@ __global__ void __launch_bounds__(R * 32, 2) sgm_wave_kernel(const __grid_consta
         if (item >= total) break;
         int f = 0;
         while (f + 1 < b.nframes && b.item0[f + 1] <= item) ++f;
-        wave_row<PASS>(b.f[f], item - b.item0[f], warp, lane, sm, b.err);
+        wave_row<PASS, EIGHT>(b.f[f], item - b.item0[f], warp, lane, sm, b.err);
         __syncthreads();
     }
+}
+
+// the kernel of a pass and path count
+using WaveKernel = void (*)(const WaveBatch);
+WaveKernel wave_kernel(int pass, bool eight)
+{
+    return pass ? (eight ? sgm_wave_kernel<1, true> : sgm_wave_kernel<1, false>)
+                : (eight ? sgm_wave_kernel<0, true> : sgm_wave_kernel<0, false>);
 }
 
 }  // namespace
@@ -565,19 +623,20 @@ int wave_capacity(int device)
     std::lock_guard<std::mutex> lk(mu);
     auto it = cap.find(device);
     if (it != cap.end()) return it->second;
-    int coop = 0, nsm = 0, occ0 = 0, occ1 = 0;
+    int coop = 0, nsm = 0, occ = 1 << 30;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
     const int smem = (int)sizeof(WaveSmem);
-    bool ok = coop != 0 &&
-              cudaFuncSetAttribute(sgm_wave_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-                  cudaSuccess &&
-              cudaFuncSetAttribute(sgm_wave_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
-                  cudaSuccess &&
-              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, sgm_wave_kernel<0>, R * 32, smem) == cudaSuccess &&
-              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, sgm_wave_kernel<1>, R * 32, smem) == cudaSuccess;
+    bool ok = coop != 0;
+    for (int i = 0; i < 4 && ok; ++i) {
+        const WaveKernel k = wave_kernel(i & 1, i >> 1);
+        int o = 0;
+        ok = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, R * 32, smem) == cudaSuccess;
+        occ = std::min(occ, o);
+    }
     cudaGetLastError();
-    const int c = ok ? nsm * std::min(occ0, occ1) : 0;
+    const int c = ok ? nsm * occ : 0;
     cap[device] = c;
     return c;
 }
@@ -594,8 +653,8 @@ void launch_sgm_wave(const WaveBatch& b, int pass, int ctas, cudaStream_t st)
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    if (pass == 0) cudaLaunchKernelEx(&cfg, sgm_wave_kernel<0>, b);
-    else cudaLaunchKernelEx(&cfg, sgm_wave_kernel<1>, b);
+    // the frames of a batch share the configuration, so its path count
+    cudaLaunchKernelEx(&cfg, wave_kernel(pass, b.f[0].a.paths == 8), b);
     count_launch();
 }
 
