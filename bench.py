@@ -356,13 +356,13 @@ def run_ours(a):
     cost_ms, cost_n = stages["cost"]
     sgm_ms, sgm_n = stages["sgm"]
     voxel_views = sum(w * h * d for w, h, d in lv) * views * a.steps
-    # cost kernel: per voxel and view the warp (1.27 bilinear samples of the
-    # 64x58 sample tile per 56x52 pixel tile, ~20 FP32 ops each = 26 ops) and
-    # the census-Hamming of the warped 9x7 window (62 compare-and-insert bit
-    # steps at 2 ops + XOR, popcount, accumulate = 127 ops): 153 ops; peak =
-    # SMs x 128 lanes x max SM clock (issue bound), the clock from the
-    # measured-peaks record (else the nominal maximum)
-    cost_ops = 153.0 * voxel_views
+    # cost kernel, algorithmic work per voxel and view: one warped bilinear
+    # sample (~20 FP32 ops; the halo samples a tile adds are the design's
+    # overhead, not counted) and the census-Hamming of the warped 9x7 window
+    # (62 compare-and-insert bit steps at 2 ops + XOR, popcount, accumulate =
+    # 127 ops): 147 ops; peak = SMs x 128 lanes x max SM clock (issue bound),
+    # the clock from the measured-peaks record (else the nominal maximum)
+    cost_ops = 147.0 * voxel_views
     alu_peak = n_sm * 128 * clk * 1e6 / 1e12        # T int-ops/s
     cost_ach = cost_ops / (cost_ms * 1e-3) / 1e12 if cost_ms > 0 else 0.0
     # one launch of each per level: `achieved` and `traffic` are per average

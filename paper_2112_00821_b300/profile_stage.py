@@ -2,7 +2,7 @@
 profiling a single kernel (ncu -k ...) or timing it with CUDA events.
 
   python -m paper_2112_00821_b300.profile_stage --stage cost|sgm|both|estimate \
-      [--W 960 --H 540 --planes 256 --views 5 --reps 2 --variant 2]
+      [--W 960 --H 540 --planes 256 --views 5 --reps 2 --variant 2 --sgm-parts 0]
 
 cost / sgm: the single-level stage entry points (cost_kernel, sgm_dir_kernel).
 estimate: the full 4-level estimate (the kernels the benchmark runs:
@@ -36,6 +36,8 @@ def main():
     p.add_argument("--reps", type=int, default=2)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--cost", type=int, default=0, help="0 census 9x7, 1 NCC 5x5 (estimate stage)")
+    p.add_argument("--sgm-parts", type=int, default=0,
+                   help="aggregation form of the estimate stage: 0 automatic, -1 two-pass, 1/2/4/8 partial sums")
     a = p.parse_args()
 
     import numpy as np
@@ -49,6 +51,7 @@ def main():
         cfg = fassmvs.default_config(levels=4, D=[256] * 4, paths=a.paths, variant=a.variant,
                                      p1=100 if a.cost else 24, p2=0, adaptive_p2=1, cost=a.cost)
         ctx = fassmvs.Context(cfg)
+        ctx.set_tuning(0, 2, a.sgm_parts)
         ctx.set_cameras(sc.K, sc.R, sc.t, sc.side)
         ref = torch.from_numpy(sc.ref).cuda()
         nbrs = [torch.from_numpy(x).cuda() for x in sc.nbrs]
