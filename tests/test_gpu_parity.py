@@ -263,6 +263,29 @@ def test_sgm_on_oracle_cost_volume(ctx, orc):
         assert np.array_equal(got, exp)
 
 
+def test_sgm_path_gradient_fhd_band_vs_oracle(ctx, orc):
+    """The benchmark's aggregation on 1080p-wide paths: path-gradient SGM,
+    8 paths, the adaptive P2 table of the estimate (P1 = 24 n_max), on a
+    1920 x 128 band of the finest level's cost volume (256 planes, 5 views)
+    -- 1920-step horizontal lines and 128-step vertical and diagonal ones --
+    against the oracle's aggregation of the same band: bit-exact."""
+    from paper_2112_00821_b300 import synth
+    sc, cfg = synth.workload("fhd_1920x1080_g256_l4", 0, want_gt=False)
+    S = ctx.cost_volume(dev(sc.ref), [dev(x) for x in sc.nbrs], sc.side, sc.K, sc.R, sc.t,
+                        sc.plane_n, sc.rho_far, sc.drho, 256)
+    y0, y1 = 476, 604
+    band = np.ascontiguousarray(host(S[y0:y1], np.uint16)[..., :256])
+    del S
+    nmax = max(sum(1 for s in sc.side if s < 0), sum(1 for s in sc.side if s > 0))
+    p1 = cfg["p1"] * nmax
+    img = np.ascontiguousarray(sc.ref[y0:y1])
+    got, exp = _sgm_case(ctx, orc, band, 256, 256, p1, lut=orc.p2_table(p1), img=img, paths=8,
+                         variant=2, dmax=8)
+    diff = int(np.count_nonzero(got != exp))
+    print("PARITY sgm path-gradient 1920x128x256 band: %d of %d voxels differ" % (diff, got.size))
+    assert diff == 0
+
+
 def test_sgm_zero_penalties_full_size(ctx):
     """P1 = P2 = 0 gives paths * S exactly, at 1920 x 1080 x 256."""
     g = torch.Generator(device="cuda").manual_seed(0)
