@@ -217,8 +217,14 @@ __device__ __forceinline__ float blend(int i0, int iu, int iv, int iuv, float a,
 }
 
 // the taps from global memory
-__device__ __forceinline__ float taps_global(const uint8_t* __restrict__ img, int pitch, SPos p, bool& pl)
+__device__ __forceinline__ float taps_global(const uint8_t* __restrict__ img, int pitch, int W, int H, SPos p,
+                                             bool& pl)
 {
+    if (!FM_IN(p.iu, W, 0x102) || !FM_IN(p.iu + p.su, W, 0x102) || !FM_IN(p.iv, H, 0x102) ||
+        !FM_IN(p.iv + p.sv, H, 0x102)) {
+        pl = false;
+        return 0.0f;
+    }
     const uint8_t* r0 = img + (size_t)p.iv * pitch + p.iu;
     const int dv = p.sv * pitch;
     return blend(__ldg(r0), __ldg(r0 + p.su), __ldg(r0 + dv), __ldg(r0 + dv + p.su), p.a, p.b, pl);
@@ -227,8 +233,14 @@ __device__ __forceinline__ float taps_global(const uint8_t* __restrict__ img, in
 // the taps from the staged box whose origin is (sx0, sy0) (in_box true)
 __device__ __forceinline__ float taps_staged(const uint8_t* stg, int sx0, int sy0, SPos p, bool& pl)
 {
-    const uint8_t* r0 = stg + (p.iv - sy0) * kStageBX + (p.iu - sx0);
+    const int o = (p.iv - sy0) * kStageBX + (p.iu - sx0);
     const int dv = p.sv * kStageBX;
+    if (!FM_IN(o + min(p.su, 0) + min(dv, 0), kStageBX * kStageBY, 0x101) ||
+        !FM_IN(o + max(p.su, 0) + max(dv, 0), kStageBX * kStageBY, 0x101)) {
+        pl = false;
+        return 0.0f;
+    }
+    const uint8_t* r0 = stg + o;
     return blend(r0[0], r0[p.su], r0[dv], r0[dv + p.su], p.a, p.b, pl);
 }
 
@@ -360,6 +372,7 @@ __device__ __forceinline__ df sample_exact(const CostArgs& a, const float* h, in
         iu = df_cell(df_div(N, D), a.W - 2, au);
         iv = df_cell(df_div(M, D), a.H - 2, av);
     }
+    if (!FM_IN(iu, a.W - 1, 0x107) || !FM_IN(iv, a.H - 1, 0x107)) return {0.0f, 0.0f};
     const uint8_t* r0 = a.views.img[k] + (size_t)iv * a.pitch + iu;
     const float i00 = (float)__ldg(r0) - 128.0f, i01 = (float)__ldg(r0 + 1) - 128.0f;
     const float i10 = (float)__ldg(r0 + a.pitch) - 128.0f, i11 = (float)__ldg(r0 + a.pitch + 1) - 128.0f;
@@ -391,6 +404,7 @@ __device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW],
         const int kk = lane + 32 * t;
         if (kk == 31 || kk >= 63) continue;
         const int dy = kk / 9, dx = kk - 9 * (kk / 9);
+        if (!FM_IN(min(j0 + dy, jlast) * SW + c0 + dx, SH * SW, 0x10a)) continue;
         const float vq = vt[min(j0 + dy, jlast)][c0 + dx];
         const float x = __fmaf_rn(vq, kCensusScale, -cs);
         if (fabsf(x) >= 2.0f) continue;
@@ -711,7 +725,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             if (do_sample) {
                 const uint8_t* sp = ready ? stg + buf * kStageBX * kStageBY : nullptr;
                 const int sx0 = ready ? sm.stg_x0[buf] : -(1 << 20), sy0 = ready ? sm.stg_y0[buf] : -(1 << 20);
-                const float* h = a.htab + ((size_t)g * a.V + k) * 18;
+                const float* h = a.htab + ((size_t)(FM_IN(g, a.G, 0x108) ? g : 0) * a.V + k) * 18;
                 const uint8_t* img = a.views.img[k];
                 if (!NCC && lane < 18) sm.hdf[buf][lane] = __ldg(h + lane);
                 const df h0 = load_df(h, 0), h1 = load_df(h, 1), h2 = load_df(h, 2);
@@ -777,12 +791,14 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                             f0 = taps_staged(sp, sx0, sy0, p0, pl0);
                             f1 = taps_staged(sp, sx0, sy0, p1, pl1);
                         } else {
-                            f0 = b0 ? taps_staged(sp, sx0, sy0, p0, pl0) : taps_global(img, a.pitch, p0, pl0);
-                            f1 = b1 ? taps_staged(sp, sx0, sy0, p1, pl1) : taps_global(img, a.pitch, p1, pl1);
+                            f0 = b0 ? taps_staged(sp, sx0, sy0, p0, pl0) : taps_global(img, a.pitch, W, H, p0, pl0);
+                            f1 = b1 ? taps_staged(sp, sx0, sy0, p1, pl1) : taps_global(img, a.pitch, W, H, p1, pl1);
                         }
                     }
-                    vrow[j][lane] = f0;
-                    vrow[j][32 + lane] = f1;
+                    if (FM_IN(j, SH, 0x103)) {
+                        vrow[j][lane] = f0;
+                        vrow[j][32 + lane] = f1;
+                    }
                     if constexpr (!NCC) {
                         // risky samples: not a plateau but within 2^-13 of an
                         // integer; per pixel column, whether its 9 window columns
@@ -832,10 +848,12 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     const int sh = a.views.side[k] < 0 ? 0 : 16;
 #pragma unroll
                     for (int jr = 0; jr < CH + 4; ++jr) {
+                        const bool rok = FM_IN(min(pr0 + 1 + jr, jlast), SH, 0x109) &&
+                                         FM_IN(pr0 + 1 + jr, SH, 0x109) && FM_IN(pc + 6, SW, 0x109);
 #pragma unroll
                         for (int c = 0; c < 5; ++c) {
-                            rb[jr % 5][c] = bp[min(pr0 + 1 + jr, jlast) * SW + c];
-                            ra[jr % 5][c] = ap[jr * SW + c];
+                            rb[jr % 5][c] = rok ? bp[min(pr0 + 1 + jr, jlast) * SW + c] : 0.0f;
+                            ra[jr % 5][c] = rok ? ap[jr * SW + c] : 0.0f;
                         }
                         if (jr >= 4) {
                             const int r = jr - 4;
@@ -889,8 +907,9 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 for (int jr = 0; jr < CH + 6; ++jr) {
                     float wv[9];
                     const float* rowp = base + (pr0 + min(jr, jl)) * SW;
+                    const bool rok = FM_IN(pr0 + min(jr, jl), SH, 0x104) && FM_IN(pc + 8, SW, 0x104);
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) wv[c] = rowp[c];
+                    for (int c = 0; c < 9; ++c) wv[c] = rok ? rowp[c] : 0.0f;
 #pragma unroll
                     for (int r = 0; r < CH; ++r) {
                         const int dy = jr - r;
@@ -910,7 +929,8 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 uint32_t fmask = 0u;
 #pragma unroll
                 for (int r = 0; r < CH; ++r) {
-                    const uint4 rf = sm.refl[pr0 + r][pc];
+                    const uint4 rf = FM_IN((pr0 + r) * PW + pc, PH * PW, 0x105) ? sm.refl[pr0 + r][pc]
+                                                                                 : make_uint4(0, 0, 0, 0);
                     int hcost = __popc((w[r][0] ^ rf.x) & SIGN_BITS) + __popc((w[r][1] ^ rf.y) & SIGN_BITS) +
                                 __popc((w[r][2] ^ rf.z) & SIGN_BITS) + __popc((w[r][3] ^ rf.w) & SIGN_BITS);
                     uint32_t k0 = big_bits(0), k1 = keep1, k2 = keep2, k3 = big_bits(3);
@@ -983,8 +1003,8 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     // (x * ceil(2^32 / n)) >> 32 == x / n exactly for x < 2^16, n <= 16
                     if (a.nL > 0) vl = (uint32_t)(((uint64_t)(sl * a.nmax + (a.nL >> 1)) * a.mL) >> 32);
                     if (a.nR > 0) vr = (uint32_t)(((uint64_t)(sr * a.nmax + (a.nR >> 1)) * a.mR) >> 32);
-                    a.S[roff + (size_t)(s >> a.bshift) * a.bstride + (s & ((1 << a.bshift) - 1))] =
-                        (uint16_t)min(vl, vr);
+                    const size_t e = roff + (size_t)(s >> a.bshift) * a.bstride + (s & ((1 << a.bshift) - 1));
+                    if (FM_IN(e, (size_t)W * H * a.Ds, 0x106)) a.S[e] = (uint16_t)min(vl, vr);
                 }
                 roff += rstride;
             }
@@ -1052,6 +1072,7 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
 }  // namespace
 
 int cost_tiles_x(int W) { return (W + PW - 1) / PW; }
+FM_CHECK_TAKE(check_take_cost)
 int cost_tiles_y(int H) { return (H + PH - 1) / PH; }
 
 namespace {

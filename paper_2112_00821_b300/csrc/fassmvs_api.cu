@@ -1513,6 +1513,11 @@ fassmvs_status fassmvs_sync(fassmvs_ctx* c)
         {"sgm_err", FASSMVS_ETIMEOUT,
          "a row of the two-pass aggregation waited past its bound on a neighbouring row (the depth maps of that "
          "estimate are not valid)"}};
+    // the checked build's bounds checks (always 0 in the default build)
+    const unsigned sites[4] = {fm::check_take_cost(), fm::check_take_sgm(), fm::check_take_wave(),
+                               fm::check_take_stages()};
+    for (unsigned site : sites)
+        if (site) return fail(c, FASSMVS_EINTERNAL, "bounds check failed at site 0x%x (checked build)", site);
     for (const Flag& fl : flags) {
         auto it = c->bufs.find(fl.buf);
         if (it == c->bufs.end() || !it->second.p) continue;

@@ -6,6 +6,44 @@
 
 namespace fm {
 
+// ---------------------------------------------------------------- checked build
+// With -DFASSMVS_CHECKED (libfassmvs_checked.so) the kernels test the indices
+// they form into shared and global memory before each access: FM_IN(i, n,
+// site) is true for 0 <= i < n; otherwise it records `site` in the
+// translation unit's check word (the first failure wins) and the access is
+// skipped, so nothing outside a buffer is read or written and no kernel traps.
+// fassmvs_sync turns a recorded site into FASSMVS_EINTERNAL.  Sites: 0x1nn
+// cost.cu, 0x2nn sgm.cu, 0x3nn sgm_wave.cu, 0x4nn stages.cu.  In the default
+// build every check is the constant true.
+#if defined(FASSMVS_CHECKED) && defined(__CUDACC__)
+static __device__ unsigned int fm_check_word;
+__device__ __forceinline__ bool fm_in(long long i, long long n, unsigned site)
+{
+    if (i >= 0 && i < n) return true;
+    atomicCAS(&fm_check_word, 0u, site);
+    return false;
+}
+#define FM_IN(i, n, site) ::fm::fm_in((long long)(i), (long long)(n), (site))
+// the translation unit's recorded site (0: none), cleared once read
+#define FM_CHECK_TAKE(fn)                                                          \
+    unsigned fn()                                                                  \
+    {                                                                              \
+        unsigned v = 0, z = 0;                                                     \
+        cudaMemcpyFromSymbol(&v, fm_check_word, sizeof v);                         \
+        if (v) cudaMemcpyToSymbol(fm_check_word, &z, sizeof z);                    \
+        return v;                                                                  \
+    }
+#else
+#define FM_IN(i, n, site) true
+#define FM_CHECK_TAKE(fn) \
+    unsigned fn() { return 0u; }
+#endif
+// per translation unit
+unsigned check_take_cost();
+unsigned check_take_sgm();
+unsigned check_take_wave();
+unsigned check_take_stages();
+
 constexpr int kMaxViews = 16;     // neighbour views per reference frame
 constexpr int kMaxSlots = 256;    // planes per pixel window (32 lanes x 8 slots)
 constexpr int kCensusMax = 62;    // informative bits of a 9x7 census string

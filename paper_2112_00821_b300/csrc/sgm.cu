@@ -49,6 +49,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __device__ __forceinline__ void load_scal(const SgmArgs& a, int r, int x, int y, StepScal& o)
 {
     const size_t pix = (size_t)y * a.W + x;
+    if (!FM_IN(x, a.W, 0x205) || !FM_IN(y, a.H, 0x205)) { o.lo = o.ipix = o.dsn = 0; return; }
     o.lo = a.lo ? __ldg(a.lo + pix) : 0;
     o.ipix = a.use_lut ? (int)__ldg(a.img + (size_t)y * a.img_pitch + x) : 0;
     o.dsn = (a.variant == 1 && a.dI) ? (int)a.dI[(size_t)r * a.W * a.H + pix] : 0;
@@ -108,7 +109,7 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
         if (u < n) {
             const int xx = x0 + u * dx, yy = y0 + u * dy;
             const size_t pp = ((size_t)yy * W + xx) * a.pstride + soff;
-            if (act) {
+            if (act && FM_IN(pp + 7, (size_t)W * H * a.pstride, 0x201)) {
                 cp_async16(&rg[u][0][lane], a.S + pp);
                 if (!first) cp_async16(&rg[u][1][lane], Sb + pp);
             }
@@ -136,7 +137,7 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
             const uint4 sraw = rg[u][0][lane];
             const uint4 acc = rg[u][1][lane];
             __syncwarp();
-            if (step + PF < n && act) {
+            if (step + PF < n && act && FM_IN(pf_off + 7, (size_t)W * H * a.pstride, 0x201)) {
                 cp_async16(&rg[u][0][lane], a.S + pf_off);
                 if (!first) cp_async16(&rg[u][1][lane], Sb + pf_off);
             }
@@ -155,7 +156,7 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
                 int P2 = a.p2;
                 if (a.use_lut) {
                     int d = cur_ipix - ipix_prev;
-                    P2 = a.lut[d < 0 ? -d : d];
+                    P2 = FM_IN(d < 0 ? -d : d, 256, 0x204) ? a.lut[d < 0 ? -d : d] : 0;
                 }
                 P2 = max(P2, a.p1);
                 const uint32_t cap = M + (uint32_t)P2, cap2 = dup2(cap);
@@ -196,7 +197,8 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
                     for (int j = 0; j < 4; ++j) {
                         const int q0 = min(max(s0 + 2 * j + sigma, -2), D + 1) + 2;
                         const int q1 = min(max(s0 + 2 * j + 1 + sigma, -2), D + 1) + 2;
-                        T[j] = (uint32_t)buf[q0] | ((uint32_t)buf[q1] << 16);
+                        T[j] = FM_IN(q0, D + 4, 0x202) && FM_IN(q1, D + 4, 0x202)
+                                   ? (uint32_t)buf[q0] | ((uint32_t)buf[q1] << 16) : 0u;
                     }
                     __syncwarp();
                 }
@@ -236,7 +238,7 @@ __device__ __forceinline__ void sgm_line(const SgmArgs& a, uint16_t* __restrict_
                     o = make_uint4(acc.x + (L[0] & vmask[0]), acc.y + (L[1] & vmask[1]),
                                    acc.z + (L[2] & vmask[2]), acc.w + (L[3] & vmask[3]));
                 }
-                *reinterpret_cast<uint4*>(Sb + off) = o;
+                if (FM_IN(off + 7, (size_t)W * H * a.pstride, 0x203)) *reinterpret_cast<uint4*>(Sb + off) = o;
             }
             off += dstep;
             pf_off += dstep;
@@ -296,6 +298,8 @@ int sgm_lines(int W, int H, int r)
     const int n = dy == 0 ? H : (dx == 0 ? W : W + H - 1);
     return (n + WARPS - 1) / WARPS * WARPS;     // whole CTAs per frame
 }
+
+FM_CHECK_TAKE(check_take_sgm)
 
 void sgm_dir_of(int r, int* dx, int* dy)
 {

@@ -215,7 +215,8 @@ __device__ __forceinline__ void paths_step(const PathIn& q, const uint32_t (&Sv)
             for (int j = 0; j < 4; ++j) {
                 const int q0 = min(max(s0 + 2 * j + sigma[p], -2), D + 1) + 2;
                 const int q1 = min(max(s0 + 2 * j + 1 + sigma[p], -2), D + 1) + 2;
-                T[p][j] = (uint32_t)bp[q0] | ((uint32_t)bp[q1] << 16);
+                T[p][j] = FM_IN(q0, D + 4, 0x301) && FM_IN(q1, D + 4, 0x301)
+                              ? (uint32_t)bp[q0] | ((uint32_t)bp[q1] << 16) : 0u;
             }
         }
         __syncwarp();
@@ -301,7 +302,7 @@ __device__ __forceinline__ void wave_wta(const WaveFrame& F, size_t pix, int x, 
     if (s > 0 && s < D - 1)
         xs = wta_vertex(x0, __ldg(F.delta + max(g - 1, 0)), __ldg(F.delta + min(g + 1, G - 1)), (float)(key >> 8),
                         (float)vm, (float)vp);
-    F.depth[pix] = wta_depth(xs, x, y, F.K, F.n0, F.n1, F.n2);
+    if (FM_IN(pix, (size_t)F.a.W * F.a.H, 0x302)) F.depth[pix] = wta_depth(xs, x, y, F.K, F.n0, F.n1, F.n2);
     if (F.gwin) F.gwin[pix] = g;
 }
 
@@ -329,7 +330,7 @@ __device__ __forceinline__ void load_pix(const WaveFrame& F, size_t pix, int x, 
                                          PixIn& o)
 {
     const SgmArgs& a = F.a;
-    if (act) {
+    if (act && FM_IN(pix * a.pstride + soff + 7, (size_t)a.W * a.H * a.pstride, 0x303)) {
         o.s = ld_slots(a.S, pix * a.pstride + soff);
         if (PASS) o.t = ld_slots(F.T1, pix * a.pstride + soff);
     }
@@ -353,6 +354,7 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
     const int W = a.W, H = a.H, D = a.D;
     const int yp = blk * R + warp;
     if (yp >= H) return;                   // warp-uniform; no row below waits on it
+    if (!FM_IN(blk, F.nblocks, 0x305)) return;
     const int y = PASS ? H - 1 - yp : yp;
     // the row above is the previous warp of this CTA, or the last warp of the
     // CTA of the block above through the global ring; the row below likewise
@@ -456,7 +458,7 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
         auto p2_of = [&](int ipred) {
             if (!a.use_lut) return a.p2;
             const int d = ip - ipred;
-            return (int)a.lut[d < 0 ? -d : d];
+            return FM_IN(d < 0 ? -d : d, 256, 0x304) ? (int)a.lut[d < 0 ? -d : d] : 0;
         };
         uint32_t tot[4];
         if (PASS) {
@@ -548,10 +550,12 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
 
         // ---- pass A: the sum of its paths; pass B: the aggregate and the winner
         const size_t off = pix * a.pstride + soff;
+        const bool oin = FM_IN(off + 7, (size_t)W * H * a.pstride, 0x306);
         if (!PASS) {
-            if (act) *reinterpret_cast<uint4*>(F.T1 + off) = make_uint4(tot[0], tot[1], tot[2], tot[3]);
+            if (act && oin) *reinterpret_cast<uint4*>(F.T1 + off) = make_uint4(tot[0], tot[1], tot[2], tot[3]);
         } else {
-            if (a.Sbar && act) *reinterpret_cast<uint4*>(a.Sbar + off) = make_uint4(tot[0], tot[1], tot[2], tot[3]);
+            if (a.Sbar && act && oin)
+                *reinterpret_cast<uint4*>(a.Sbar + off) = make_uint4(tot[0], tot[1], tot[2], tot[3]);
             wave_wta(F, pix, x, y, lo_p, tot, D, q.s0, lane);
         }
     }
@@ -595,6 +599,8 @@ WaveKernel wave_kernel(int pass, bool eight)
 }
 
 }  // namespace
+
+FM_CHECK_TAKE(check_take_wave)
 
 int wave_blocks(int H) { return (H + R - 1) / R; }
 int wave_ring_cols(int W, int H, int cap)

@@ -71,7 +71,8 @@ __global__ void wta_kernel(const uint16_t* __restrict__ Sbar, const int32_t* __r
     if (p >= (size_t)W * H) return;
     const int s0 = lane * 8;
     uint32_t v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (s0 < D) {
+    if (s0 < D && FM_IN(p * pstride + (size_t)(s0 >> bshift) * bstride + (s0 & ((1 << bshift) - 1)) + 7,
+                        (size_t)W * H * Ds, 0x401)) {
         const size_t off = p * pstride + (size_t)(s0 >> bshift) * bstride + (s0 & ((1 << bshift) - 1));
         const uint4* src = reinterpret_cast<const uint4*>(Sbar + off);
         uint4 raw = __ldg(src);
@@ -141,13 +142,14 @@ __global__ void __launch_bounds__(256) relayout16_kernel(const uint16_t* __restr
     const int nb = Ds / 16, per = 2 * nb;      // uint4 per pixel
     for (int i = threadIdx.x; i < nb * 2 * kRelPix; i += blockDim.x) {
         const int b = i / (2 * kRelPix), j = (i >> 1) & (kRelPix - 1), h = i & 1;
-        if (j < npx) sm[b][2 * j + h] = __ldcs(reinterpret_cast<const uint4*>(src + ((size_t)b * np + p0 + j) * 16) + h);
+        if (j < npx && FM_IN(b, kMaxSlots / 16, 0x402) && FM_IN(((size_t)b * np + p0 + j) * 16 + 15, np * Ds, 0x402))
+            sm[b][2 * j + h] = __ldcs(reinterpret_cast<const uint4*>(src + ((size_t)b * np + p0 + j) * 16) + h);
     }
     __syncthreads();
     uint4* d = reinterpret_cast<uint4*>(dst + p0 * (size_t)Ds);
     for (int i = threadIdx.x; i < npx * per; i += blockDim.x) {
         const int j = i / per, k = i - j * per;
-        d[i] = sm[k >> 1][2 * j + (k & 1)];
+        if (FM_IN((p0 + j) * (size_t)Ds + 8 * k + 7, np * Ds, 0x403)) d[i] = sm[k >> 1][2 * j + (k & 1)];
     }
 }
 
@@ -341,6 +343,8 @@ void launch_census(const uint8_t* img, int W, int H, int pitch, uint64_t* out, c
     census_kernel<<<grid2(W, H, b), b, 0, st>>>(img, W, H, pitch, out);
     count_launch();
 }
+
+FM_CHECK_TAKE(check_take_stages)
 
 void launch_wta_refine(const uint16_t* Sbar, const int32_t* lo, int W, int H, int D, int Ds, int G,
                        const float* delta, Intr K, const float n[3], float* depth, int32_t* gwin,

@@ -13,7 +13,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfassmvs.so")
+# FASSMVS_CHECKED=1 loads the bounds-checked build (same ABI; a failed check
+# makes fassmvs_sync return FASSMVS_EINTERNAL)
+LIB_PATH = os.path.join(_HERE, "libfassmvs_checked.so" if os.environ.get("FASSMVS_CHECKED") == "1"
+                        else "libfassmvs.so")
 _lib = None
 
 OK, EINVAL, ENOMEM, EBUSY, ETIMEOUT, ECUDA, EINTERNAL, ECANCELED = range(8)
@@ -150,7 +153,8 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libfassmvs.so is not built; run paper_2112_00821_b300/build.py")
+            raise ImportError("%s is not built; run paper_2112_00821_b300/build.py"
+                              % os.path.basename(LIB_PATH))
         L = C.CDLL(LIB_PATH)
         for name, args in _SIGS.items():
             f = getattr(L, name)
