@@ -550,7 +550,8 @@ __device__ __forceinline__ void wave_row(const WaveFrame& F, int blk, int warp, 
 
         // ---- pass A: the sum of its paths; pass B: the aggregate and the winner
         const size_t off = pix * a.pstride + soff;
-        const bool oin = FM_IN(off + 7, (size_t)W * H * a.pstride, 0x306);
+        // a lane that holds no hypothesis stores nothing (its offset is not checked)
+        const bool oin = act && FM_IN(off + 7, (size_t)W * H * a.pstride, 0x306);
         if (!PASS) {
             if (act && oin) *reinterpret_cast<uint4*>(F.T1 + off) = make_uint4(tot[0], tot[1], tot[2], tot[3]);
         } else {

@@ -41,7 +41,7 @@ def main(out_path):
         ("pg8", dict(levels=3, D=[16, 16, 16], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1), (0, 2, 0)),
         ("sn4", dict(levels=2, D=[24, 24], paths=4, variant=1, p1=24, p2=0, adaptive_p2=1), (8, 1, 2)),
         ("pw8_fixed_p2", dict(levels=1, D=[32], paths=8, variant=0, p1=10, p2=120, adaptive_p2=0), (0, 0, 4)),
-        ("ncc_pg8", dict(levels=2, D=[16, 16], paths=8, variant=2, p1=100, p2=0, adaptive_p2=1, cost=1),
+        ("ncc_pg8", dict(levels=2, D=[16, 16], paths=8, variant=2, p1=40, p2=0, adaptive_p2=1, cost=1),
          (0, 2, 0)),
         ("twopass_pg8", dict(levels=3, D=[16, 16, 16], paths=8, variant=2, p1=24, p2=0, adaptive_p2=1),
          (0, 2, -1)),
