@@ -377,7 +377,14 @@ FASSMVS_API fassmvs_status fassmvs_debug_inject(fassmvs_ctx* ctx, int mode);
 #define FASSMVS_DUMP_DEPTH_RAW 5  /* float [H][W]: refined depth before the median */
 #define FASSMVS_DUMP_DEPTH 6      /* float [H][W]: depth after the 5x5 median */
 #define FASSMVS_DUMP_NORMAL 7     /* float [H][W][3]: smoothed unit normals */
+#define FASSMVS_DUMP_WARP 8       /* float [H][W]: warped values minus 128 of the (plane, view)
+                                     pair set by fassmvs_debug_capture_warp, as the census reads
+                                     them (Alg. 1 patch warping); NaN at pixels whose tile did not
+                                     sweep that plane */
 FASSMVS_API fassmvs_status fassmvs_debug_capture(fassmvs_ctx* ctx, int level);
+/* Which (plane of the level's list, neighbour view) the next captures keep
+ * the warped values of (FASSMVS_DUMP_WARP); -1, -1: none. */
+FASSMVS_API fassmvs_status fassmvs_debug_capture_warp(fassmvs_ctx* ctx, int plane, int view);
 FASSMVS_API fassmvs_status fassmvs_debug_dump(fassmvs_ctx* ctx, int level, int what, void* dst, size_t cap,
                                               size_t* bytes, int32_t dims[5]);
 
@@ -469,8 +476,13 @@ FASSMVS_API fassmvs_status fassmvs_census(fassmvs_ctx* ctx, const uint8_t* img, 
  * left and the right views, each sum rescaled to max(n_left, n_right) images
  * (round half up), S = min of the two.  A view whose centre sample leaves the
  * image costs 62.  With the context's cost set to NCC the per-view cost is
- * the NCC 5x5 cost instead (255 for an invalid view or a flat window).  Samples are bilinear on a 1/256-pixel grid with 8-bit
- * weights.  K, R, t, n are host arrays.  Slots D..Ds-1 are left untouched. */
+ * the NCC 5x5 cost instead (255 for an invalid view or a flat window).  A
+ * sample is the bilinear value (lerp form) of the neighbour image at the
+ * exact warped position, clamped to the image, not rounded; the census
+ * decides every comparison as the FP64 values would (comparisons closer than
+ * 2^-14 grey levels are decided again in double-float), so the census cost
+ * equals the FP64 reading's.  K, R, t, n are host arrays.  Slots D..Ds-1 are
+ * left untouched. */
 FASSMVS_API fassmvs_status fassmvs_cost_volume(fassmvs_ctx* ctx, const uint8_t* ref, const uint8_t* const* nbrs,
                                    int n_nb, const int8_t* side, int W, int H, const double K[9],
                                    const double* R, const double* t, const double n[3], double rho0,

@@ -126,13 +126,14 @@ __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h +
 
 // One coordinate of a warped sample.  N / D is the position (D > 0, r ~ 1 / D;
 // r = 0 for a point behind the camera, which then reads pixel 0 with weight 0,
-// the clamped position of (-inf, -inf)).  The FP32 quotient q of N's high word
-// and its residual e = N - q D (formed with fused multiply-adds, exact to far
-// below an ulp of q) give the position as q + e / D in double-float; with c
-// the integer nearest q, the offset f = (q - c) + e / D (the difference exact,
-// one rounding in the fused multiply-add) is accurate to ~1.5e-8 px.  Where
-// the position lies that close to a half integer, |f| may pass 1/2 by the
-// error of q.  The bilinear blend weighs pixel c and its neighbour c + s
+// the clamped position of (-inf, -inf)).  The FP32 quotient q = N / D and its
+// residual e = N - q D (formed with fused multiply-adds, exact to far below an
+// ulp of q) give the position as q + e / D in double-float; with c the integer
+// nearest q, the offset f = (q - c) + e / D (the difference exact, one
+// rounding in the fused multiply-add) is accurate to half an ulp of f: 1.5e-8
+// px, 3e-8 where the position lies within half an ulp of q of a half integer
+// and |f| passes 1/2 (q keeps N's low word so that this stays that rare).
+// The bilinear blend weighs pixel c and its neighbour c + s
 // (s = the sign of f) with |f| < 1, so it interpolates between them and never
 // extrapolates (a floor-based cell would, by up to that error times the
 // change of slope across the cell edge); a position outside the image reads
@@ -141,7 +142,7 @@ __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h +
 struct Coord { int i, s; float w; bool in; };
 __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 {
-    const float q = __fmul_rn(N.hi, r);
+    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
     const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
     const float c = rintf(fminf(fmaxf(q, -1.0f), maxf + 1.0f));     // NaN -> -1
     const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
@@ -158,7 +159,7 @@ __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 // the same values as coord gives there, bit for bit.
 __device__ __forceinline__ Coord coord_in(df N, df D, float r)
 {
-    const float q = __fmul_rn(N.hi, r);
+    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
     const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
     const float c = rintf(q);
     const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
@@ -255,11 +256,14 @@ __device__ __forceinline__ bool in_box(int sx0, int sy0, SPos p)
 // A census comparison [V(q) < V(p)] is decided on the FP32 values (V = warped
 // value - 128) by the sign of x = 2^15 (V(q) - V(p)), one rounding of an
 // exact difference; bit 30 of x records |x| >= 2, i.e. |V(q) - V(p)| >= 2^-14,
-// and a funnel shift by two keeps both bits.  An FP32 value lies within 2.1e-5
-// of the FP64 value of the sampling reading (the weights within 1.5e-8 of the
-// double-float offsets, times tap differences of at most 255, plus the
-// blend's roundings and the FP32 value itself), so a comparison whose FP32
-// difference reaches 2^-14 = 6.1e-5 has the FP64 comparison's sign.  The
+// and a funnel shift by two keeps both bits.  An FP32 value lies within
+// 2.7e-5 of the FP64 value of the sampling reading: each lerp's weight error
+// (at most 3e-8 px) times a tap difference of at most 255, plus half an ulp of
+// the top and bottom lerps (|value| < 128: 3.8e-6), of their difference
+// (< 256: 7.6e-6, times the weight <= 1/2) and of the value, 1.14e-5 +
+// 3.8e-6 + 7.6e-6 + 3.8e-6 (measured on whole 1080p pairs: at most 2.2e-5).
+// Below 2^-15 = 3.05e-5, so a comparison whose FP32 difference reaches
+// 2^-14 = 6.1e-5 has the FP64 comparison's sign.  The
 // others -- near ties -- are decided again: equal values of one reference
 // position or of two plateaus of equal pixels are ties in FP64 as well; the
 // rest are recomputed in double-float from the homography and the image
@@ -832,6 +836,20 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 if constexpr (!NCC) {
                     sm.rkcol[buf][warp][lane] = (uint8_t)rk_lo;
                     sm.rkcol[buf][warp][32 + lane] = (uint8_t)rk_hi;
+                }
+                // debug capture: this warp's sample rows that are pixel rows the
+                // tile stores (each lane its own two columns, read back from
+                // where it wrote them)
+                if (a.dbg_warp && g == a.dbg_g && k == a.dbg_k) {
+                    for (int j = rs; j < re; ++j) {
+                        const int Y = ty0 - 3 + j;
+                        if (j < 3 || j >= 3 + PH || Y > H - 1 || j - 3 < sm.rskip) continue;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int col = lane + 32 * h, X = tx0 - 4 + col;
+                            if (col >= 4 && col < 4 + PW && X < W) a.dbg_warp[(size_t)Y * W + X] = vrow[j][col];
+                        }
+                    }
                 }
             }
             if (staged) phase ^= 1u << buf;

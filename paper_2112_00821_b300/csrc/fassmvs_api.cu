@@ -938,6 +938,15 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
             }
             a.err = (int*)cost_err;
             a.stage_test = c->inject == 1;
+            if (f == 0 && l == c->dbg_level && c->dbg_warp_g >= 0) {
+                // the warped values of one (plane, view) pair; NaN where no tile sampled it
+                void* p;
+                FM_TRY(ensure(c, "dbg:warp", sizeof(float) * np, &p));
+                FM_TRY(cuda_check(c, cudaMemsetAsync(p, 0xFF, sizeof(float) * np, st), "capture"));
+                a.dbg_warp = (float*)p;
+                a.dbg_g = c->dbg_warp_g;
+                a.dbg_k = c->dbg_warp_k;
+            }
             // aggregation arguments
             fm::SgmArgs& g = sargs[f];
             memset(&g, 0, sizeof g);
@@ -1574,17 +1583,27 @@ fassmvs_status fassmvs_debug_capture(fassmvs_ctx* c, int level)
     return FASSMVS_OK;
 }
 
+fassmvs_status fassmvs_debug_capture_warp(fassmvs_ctx* c, int plane, int view)
+{
+    if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
+    if (plane < -1 || view < -1 || view >= fm::kMaxViews || (plane < 0) != (view < 0))
+        return fail(c, FASSMVS_EINVAL, "plane and view both -1 (off) or both >= 0");
+    c->dbg_warp_g = plane;
+    c->dbg_warp_k = view;
+    return FASSMVS_OK;
+}
+
 fassmvs_status fassmvs_debug_dump(fassmvs_ctx* c, int level, int what, void* dst, size_t cap, size_t* bytes,
                                   int32_t dims[5])
 {
     if (!c) return fail(nullptr, FASSMVS_EINVAL, "ctx is NULL");
     if (level != c->dbg_level || c->dbg_dims[0] == 0)
         return fail(c, FASSMVS_EINVAL, "level %d was not captured by the last estimate", level);
-    static const char* const names[8] = {"dbg:S",    "dbg:lo",   "dbg:dI",   "dbg:agg",
-                                         "dbg:gwin", "dbg:draw", "dbg:dmed", "dbg:nrm"};
-    if (what < 0 || what > 7) return fail(c, FASSMVS_EINVAL, "what 0..7");
+    static const char* const names[9] = {"dbg:S",    "dbg:lo",   "dbg:dI",   "dbg:agg", "dbg:gwin",
+                                         "dbg:draw", "dbg:dmed", "dbg:nrm", "dbg:warp"};
+    if (what < 0 || what > 8) return fail(c, FASSMVS_EINVAL, "what 0..8");
     const size_t np = (size_t)c->dbg_dims[0] * c->dbg_dims[1], nv = np * c->dbg_dims[3];
-    const size_t need[8] = {2 * nv, 4 * np, 8 * np, 2 * nv, 4 * np, 4 * np, 4 * np, 12 * np};
+    const size_t need[9] = {2 * nv, 4 * np, 8 * np, 2 * nv, 4 * np, 4 * np, 4 * np, 12 * np, 4 * np};
     if (bytes) *bytes = need[what];
     if (dims) memcpy(dims, c->dbg_dims, sizeof c->dbg_dims);
     if (!dst) return FASSMVS_OK;

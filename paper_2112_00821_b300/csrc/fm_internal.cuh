@@ -107,6 +107,11 @@ struct CostArgs {
     // test hook: plan the staging boxes but issue no copies, with a wait
     // bound of about a millisecond, so that every staged wait gives up
     int stage_test;
+    // debug capture (may be null): the warped values minus 128 of plane
+    // dbg_g, view dbg_k at every pixel whose tile sampled that pair, float
+    // [H][W], exactly as the census reads them
+    float* dbg_warp;
+    int dbg_g, dbg_k;
 };
 constexpr int kStageBX = 128, kStageBY = 80;
 void launch_cost(const CostArgs& a, cudaStream_t st);

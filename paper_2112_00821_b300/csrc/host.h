@@ -32,6 +32,7 @@ struct fassmvs_ctx {
     int inject = 0;                      // test hook (fassmvs_debug_inject)
     int dbg_level = -1;                  // level captured by the next estimate (fassmvs_debug_capture)
     int dbg_dims[5] = {0, 0, 0, 0, 0};  // W, H, D, Ds, G of the captured level
+    int dbg_warp_g = -1, dbg_warp_k = -1;   // (plane, view) whose warped values the capture keeps
     struct Rec { cudaEvent_t a, b; int stage; };
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> pending;

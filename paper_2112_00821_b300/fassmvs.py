@@ -132,6 +132,7 @@ _SIGS = {
     "fassmvs_server_last_error": [_VP],
     "fassmvs_debug_inject": [_VP, C.c_int],
     "fassmvs_debug_capture": [_VP, C.c_int],
+    "fassmvs_debug_capture_warp": [_VP, C.c_int, C.c_int],
     "fassmvs_debug_dump": [_VP, C.c_int, C.c_int, _VP, C.c_size_t, _VP, _VP],
     "fassmvs_plane_bounds": [_VP, C.c_int, C.c_int, _VP, C.c_double, C.c_double, _VP, _VP],
     "fassmvs_cross_ratio_planes": [_VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int,
@@ -376,18 +377,23 @@ class Context:
 
     STAGES = ("pyramid", "census", "cost", "sgm", "wta", "median", "normals", "window", "relayout")
 
-    DUMPS = ("cost", "window", "dsn", "agg", "argmin", "depth_raw", "depth", "normal")
+    DUMPS = ("cost", "window", "dsn", "agg", "argmin", "depth_raw", "depth", "normal", "warp")
 
     def debug_capture(self, level):
         """The next estimates keep the intermediates of pyramid level `level`
         (frame 0); -1 turns capturing off."""
         self._check(lib().fassmvs_debug_capture(self._h, int(level)))
 
+    def debug_capture_warp(self, plane, view):
+        """The captures keep the warped values (minus 128) of this (plane of
+        the level's list, neighbour view) pair, dumped as "warp"; -1, -1: none."""
+        self._check(lib().fassmvs_debug_capture_warp(self._h, int(plane), int(view)))
+
     def debug_dump(self, level, what):
         """One captured intermediate (a name of DUMPS) as a CUDA tensor:
         cost / agg uint16 (H, W, Ds) viewed as int16, window / argmin int32
         (H, W), dsn int8 (8, H, W), depth_raw / depth float32 (H, W), normal
-        float32 (H, W, 3)."""
+        float32 (H, W, 3), warp float32 (H, W)."""
         import torch
         w = self.DUMPS.index(what)
         dims = (C.c_int32 * 5)()
@@ -396,7 +402,7 @@ class Context:
         W, H, D, Ds, G = list(dims)
         shape, dt = {0: ((H, W, Ds), torch.int16), 1: ((H, W), torch.int32), 2: ((8, H, W), torch.int8),
                      3: ((H, W, Ds), torch.int16), 4: ((H, W), torch.int32), 5: ((H, W), torch.float32),
-                     6: ((H, W), torch.float32), 7: ((H, W, 3), torch.float32)}[w]
+                     6: ((H, W), torch.float32), 7: ((H, W, 3), torch.float32), 8: ((H, W), torch.float32)}[w]
         out = torch.empty(shape, dtype=dt, device="cuda")
         self._check(lib().fassmvs_debug_dump(self._h, int(level), w, _ptr(out), nb.value, None, None))
         return out, dict(W=W, H=H, D=D, Ds=Ds, G=G)
