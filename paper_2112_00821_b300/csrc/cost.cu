@@ -60,6 +60,7 @@ struct SmemCost {
     float val[2][SH][SW];                // warped values minus 128 (FP32, unrounded)
     uint32_t okm[2][PH][2];              // centre-in-image bit per pixel column
     float hdf[2][18];                    // census: the pair's homography (high, low words), for near ties
+    uint32_t rkb[2][SH][2];              // census: risky samples, one bit per sample (columns 0-31, 32-63)
     uint8_t rkcol[2][NWARP][64];         // census: per sampling warp and pixel column, its rows whose
                                          // window columns hold a risky sample (one bit per row)
     union {
@@ -126,13 +127,14 @@ __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h +
 
 // One coordinate of a warped sample.  N / D is the position (D > 0, r ~ 1 / D;
 // r = 0 for a point behind the camera, which then reads pixel 0 with weight 0,
-// the clamped position of (-inf, -inf)).  The FP32 quotient q = N / D and its
-// residual e = N - q D (formed with fused multiply-adds, exact to far below an
-// ulp of q) give the position as q + e / D in double-float; with c the integer
-// nearest q, the offset f = (q - c) + e / D (the difference exact, one
-// rounding in the fused multiply-add) is accurate to half an ulp of f: 1.5e-8
-// px, 3e-8 where the position lies within half an ulp of q of a half integer
-// and |f| passes 1/2 (q keeps N's low word so that this stays that rare).
+// the clamped position of (-inf, -inf)).  The FP32 quotient q = N.hi / D and
+// the residual e = N - q D of the whole numerator (formed with fused
+// multiply-adds, exact to far below an ulp of q) give the position as
+// q + e / D in double-float; with c the integer nearest q, the offset
+// f = (q - c) + e / D (the difference exact, one rounding in the fused
+// multiply-add) is accurate to half an ulp of f: 1.5e-8 px, 3e-8 where the
+// position lies within |N.lo / D| plus an ulp of q of a half integer and
+// |f| passes 1/2.
 // The bilinear blend weighs pixel c and its neighbour c + s
 // (s = the sign of f) with |f| < 1, so it interpolates between them and never
 // extrapolates (a floor-based cell would, by up to that error times the
@@ -142,7 +144,7 @@ __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h +
 struct Coord { int i, s; float w; bool in; };
 __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 {
-    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
+    const float q = __fmul_rn(N.hi, r);
     const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
     const float c = rintf(fminf(fmaxf(q, -1.0f), maxf + 1.0f));     // NaN -> -1
     const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
@@ -159,7 +161,7 @@ __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
 // the same values as coord gives there, bit for bit.
 __device__ __forceinline__ Coord coord_in(df N, df D, float r)
 {
-    const float q = __fmul_rn(__fadd_rn(N.hi, N.lo), r);
+    const float q = __fmul_rn(N.hi, r);
     const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
     const float c = rintf(q);
     const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
@@ -265,11 +267,11 @@ __device__ __forceinline__ bool in_box(int sx0, int sy0, SPos p)
 // Below 2^-15 = 3.05e-5, so a comparison whose FP32 difference reaches
 // 2^-14 = 6.1e-5 has the FP64 comparison's sign.  The
 // others -- near ties -- are decided again: equal values of one reference
-// position or of two plateaus of equal pixels are ties in FP64 as well; the
-// rest are recomputed in double-float from the homography and the image
-// (cen_fix).  Pixels whose centre is an integer and whose window holds no
-// risky sample (a non-plateau value within 2^-13 of an integer) can only
-// have plateau ties and skip that step.
+// position are ties in FP64 as well; a pixel whose centre is an integer and
+// whose window holds no risky sample (a non-plateau value within 2^-13 of an
+// integer) has only ties between plateaus of equal pixels, which are exact
+// integers in FP64 too, and skips the step; the rest are recomputed in
+// double-float from the homography and the image (cen_fix).
 constexpr float kCensusScale = 32768.0f;
 constexpr float kRiskyBound = 0x1p-13f;
 //
@@ -336,8 +338,15 @@ __device__ __forceinline__ df df_div(df N, df D)
     return two_sum(qh, __fmul_rn(rem, r));
 }
 
-// the cell (clamped to [0, cmax]) and offset (clamped to [0, 1]) of a position
-// u in double-float
+// (hi, lo) with |lo| <= half an ulp of hi.  The products below drop the
+// low-times-low term, which is negligible only for normalised operands: the
+// offset left by subtracting the floor keeps few significant bits in its high
+// word, and its unnormalised low word times that of a tap difference reached
+// 2e-8 grey levels, enough to misorder a near tie.
+__device__ __forceinline__ df df_norm(df a) { return two_sum(a.hi, a.lo); }
+
+// the cell (clamped to [0, cmax]) and offset (clamped to [0, 1], normalised)
+// of a position u in double-float
 __device__ __forceinline__ int df_cell(df u, int cmax, df& a)
 {
     float fl = floorf(u.hi);
@@ -346,23 +355,25 @@ __device__ __forceinline__ int df_cell(df u, int cmax, df& a)
     else if (__fadd_rn(f.hi, f.lo) >= 1.0f) { fl = __fadd_rn(fl, 1.0f); f.hi = __fsub_rn(f.hi, 1.0f); }
     if (fl < 0.0f) { a = {0.0f, 0.0f}; return 0; }
     if (fl > (float)cmax) { a = {1.0f, 0.0f}; return cmax; }
-    a = f;
+    a = df_norm(f);
     return (int)fl;
 }
 
-// t0 + a (t1 - t0) for taps t0, t1 and a double-float offset a
+// t0 + a (t1 - t0) for taps t0, t1 and a normalised double-float offset a
+// (normalised result)
 __device__ __forceinline__ df df_lerp_taps(float t0, float t1, df a)
 {
     const float d = __fsub_rn(t1, t0);
     const df p = two_prod(a.hi, d);
     const df s = two_sum(t0, p.hi);
-    return {s.hi, __fadd_rn(s.lo, __fadd_rn(p.lo, __fmul_rn(a.lo, d)))};
+    return df_norm({s.hi, __fadd_rn(s.lo, __fadd_rn(p.lo, __fmul_rn(a.lo, d)))});
 }
 
 // value - 128 of the warped neighbour k at reference pixel (X, Y) under the
 // homography h (18 floats: the high then the low words of the nine entries),
-// in double-float arithmetic: the reading of the sampling evaluated to ~1e-11
-// grey levels
+// in double-float arithmetic: the position to ~1e-11 px, every product taken
+// on normalised operands, so the value of the sampling reading to ~1e-11 grey
+// levels
 __device__ __forceinline__ df sample_exact(const CostArgs& a, const float* h, int k, int X, int Y)
 {
     const float fx = (float)X, fy = (float)Y;
@@ -382,7 +393,7 @@ __device__ __forceinline__ df sample_exact(const CostArgs& a, const float* h, in
     const float i10 = (float)__ldg(r0 + a.pitch) - 128.0f, i11 = (float)__ldg(r0 + a.pitch + 1) - 128.0f;
     const df top = df_lerp_taps(i00, i01, au), bot = df_lerp_taps(i10, i11, au);
     // top + b (bot - top)
-    const df dd = df_add(bot, {-top.hi, -top.lo});
+    const df dd = df_norm(df_add(bot, {-top.hi, -top.lo}));
     const df p = two_prod(av.hi, dd.hi);
     const float pl = __fadd_rn(p.lo, __fadd_rn(__fmul_rn(av.hi, dd.lo), __fmul_rn(av.lo, dd.hi)));
     return df_add(top, {p.hi, pl});
@@ -393,13 +404,17 @@ __device__ __forceinline__ df sample_exact(const CostArgs& a, const float* h, in
 // stays below 2^-14 -- are decided exactly, computed by the whole warp (lane l
 // takes window positions l and l + 32; the same value returned in every
 // lane).  Equal values of one reference position (a window clamped at the
-// image border) or of two plateaus of equal pixels are ties in FP64 as well;
-// the rest are recomputed in double-float.  Sample rows past jlast (below the
-// image) read row jlast, as the census does.
-__device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW], const float* h, int k, int tx0, int ty0,
-                                       int j0, int c0, int jlast, uint4 rf, int lane)
+// image border) are ties in FP64 as well, and so are equal integers of two
+// samples that are not risky (rkb: an integer-valued sample that is not
+// risky is a plateau); the rest are recomputed in double-float (a non-plateau
+// value close to an integer can come out as that integer in FP32).  Sample
+// rows past jlast (below the image) read row jlast, as the census does.
+__device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW], const uint32_t (*rkb)[2],
+                                       const float* h, int k, int tx0, int ty0, int j0, int c0, int jlast, uint4 rf,
+                                       int lane)
 {
     const float vp = vt[min(j0 + 3, jlast)][c0 + 4];
+    const bool rp = (rkb[min(j0 + 3, jlast)][(c0 + 4) >> 5] >> ((c0 + 4) & 31)) & 1u;
     const float cs = __fmul_rn(kCensusScale, vp);
     const int xp = min(max(tx0 + c0, 0), a.W - 1), yp = min(max(ty0 + j0, 0), a.H - 1);
     int delta = 0;
@@ -413,7 +428,8 @@ __device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW],
         const float x = __fmaf_rn(vq, kCensusScale, -cs);
         if (fabsf(x) >= 2.0f) continue;
         const int xq = min(max(tx0 - 4 + c0 + dx, 0), a.W - 1), yq = min(max(ty0 - 3 + j0 + dy, 0), a.H - 1);
-        if (vq == vp && ((xq == xp && yq == yp) || vq == rintf(vq))) continue;
+        const bool rq = (rkb[min(j0 + dy, jlast)][(c0 + dx) >> 5] >> ((c0 + dx) & 31)) & 1u;
+        if (vq == vp && ((xq == xp && yq == yp) || (vq == rintf(vq) && !rq && !rp))) continue;
         const df ep = sample_exact(a, h, k, xp, yp);
         const df eq = sample_exact(a, h, k, xq, yq);
         const df d = two_sum(eq.hi, -ep.hi);
@@ -448,7 +464,7 @@ __device__ __noinline__ void fix_ties(const CostArgs& a, const SmemCost& sm, int
         const int r = __ffs(fm) - 1;
         const int c0 = __shfl_sync(0xFFFFFFFFu, pc, src);
         const int j0 = __shfl_sync(0xFFFFFFFFu, pr0, src) + r;
-        const int d = cen_fix(a, vt, sm.hdf[buf], k, tx0, ty0, j0, c0, jlast, sm.refl[j0][c0], lane);
+        const int d = cen_fix(a, vt, sm.rkb[buf], sm.hdf[buf], k, tx0, ty0, j0, c0, jlast, sm.refl[j0][c0], lane);
         if (lane == src) {
             fmask &= fmask - 1u;
             corr[r] += d;
@@ -570,7 +586,7 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
 // One tile (bx, by) of one frame, plane chunk bz of nz, with the census (NCC
 // false) or NCC 5x5 cost.  Called by the single-frame grid kernel and by the
 // multi-frame kernel, both with their arguments in shared memory.
-template <bool NCC>
+template <bool NCC, bool DBG>
 __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int bz, int nz, SmemCost& sm,
                                           uint8_t* stg, uint32_t& phase)
 {
@@ -637,6 +653,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     }
     for (int i = tid; i < 2 * SH * SW; i += THREADS) (&sm.val[0][0][0])[i] = 0.0f;
     for (int i = tid; i < 2 * PH * 2; i += THREADS) (&sm.okm[0][0][0])[i] = 0u;
+    for (int i = tid; i < 2 * SH * 2; i += THREADS) (&sm.rkb[0][0][0])[i] = 0u;
     // planes of this tile (guarded against an out-of-range window map), split
     // into nz consecutive chunks
     const int tlo = max(sm.glo, 0), thi = min(sm.ghi, a.G);
@@ -810,6 +827,10 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                         const bool rk0 = !pl0 && fabsf(__fsub_rn(f0, rintf(f0))) < kRiskyBound;
                         const bool rk1 = !pl1 && fabsf(__fsub_rn(f1, rintf(f1))) < kRiskyBound;
                         const uint32_t q0 = __ballot_sync(0xFFFFFFFFu, rk0), q1 = __ballot_sync(0xFFFFFFFFu, rk1);
+                        if (lane == 0 && FM_IN(j, SH, 0x103)) {
+                            sm.rkb[buf][j][0] = q0;
+                            sm.rkb[buf][j][1] = q1;
+                        }
                         if (q0 | q1) {
                             const uint64_t M = ((uint64_t)q1 << 32) | q0;
                             uint64_t t = M | (M >> 1);
@@ -840,7 +861,7 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 // debug capture: this warp's sample rows that are pixel rows the
                 // tile stores (each lane its own two columns, read back from
                 // where it wrote them)
-                if (a.dbg_warp && g == a.dbg_g && k == a.dbg_k) {
+                if (DBG && a.dbg_warp && g == a.dbg_g && k == a.dbg_k) {
                     for (int j = rs; j < re; ++j) {
                         const int Y = ty0 - 3 + j;
                         if (j < 3 || j >= 3 + PH || Y > H - 1 || j - 3 < sm.rskip) continue;
@@ -913,33 +934,47 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 const float(*vt)[SW] = sm.val[buf];
                 const float* base = &vt[0][pc];
                 const int jl = jlast - pr0;
-                float cs[CH];
+                // -2^15 V(p) of each pixel, twice: columns c and c + 1 of a
+                // window row go through one packed fused multiply-add (each
+                // half rounded as the scalar one)
+                const float2 S2 = make_float2(kCensusScale, kCensusScale);
+                float2 ncs[CH];
                 uint32_t w[CH][4];
 #pragma unroll
                 for (int r = 0; r < CH; ++r) {
-                    cs[r] = __fmul_rn(kCensusScale, base[(pr0 + min(r + 3, jl)) * SW + 4]);
+                    const float c = __fmul_rn(-kCensusScale, base[(pr0 + min(r + 3, jl)) * SW + 4]);
+                    ncs[r] = make_float2(c, c);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) w[r][q] = 0u;
                 }
 #pragma unroll
                 for (int jr = 0; jr < CH + 6; ++jr) {
-                    float wv[9];
+                    float2 wv2[4];
                     const float* rowp = base + (pr0 + min(jr, jl)) * SW;
                     const bool rok = FM_IN(pr0 + min(jr, jl), SH, 0x104) && FM_IN(pc + 8, SW, 0x104);
 #pragma unroll
-                    for (int c = 0; c < 9; ++c) wv[c] = rok ? rowp[c] : 0.0f;
+                    for (int i = 0; i < 4; ++i)
+                        wv2[i] = rok ? make_float2(rowp[2 * i], rowp[2 * i + 1]) : make_float2(0.0f, 0.0f);
+                    const float wv8 = rok ? rowp[8] : 0.0f;
 #pragma unroll
                     for (int r = 0; r < CH; ++r) {
                         const int dy = jr - r;
                         if (dy < 0 || dy > 6) continue;
+                        // 2^15 (V(q) - V(p)): sign = [V(q) < V(p)], bit 30 = the
+                        // difference reaches 2^-14
+                        float x[9];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float2 x2 = __ffma2_rn(wv2[i], S2, ncs[r]);
+                            x[2 * i] = x2.x;
+                            x[2 * i + 1] = x2.y;
+                        }
+                        x[8] = __fmaf_rn(wv8, kCensusScale, ncs[r].x);
 #pragma unroll
                         for (int c = 0; c < 9; ++c) {
                             const int kb = dy * 9 + c;
                             if (kb == 31) continue;
-                            // 2^15 (V(q) - V(p)): sign = [V(q) < V(p)], bit 30 = the
-                            // difference reaches 2^-14
-                            const float x = __fmaf_rn(wv[c], kCensusScale, -cs[r]);
-                            w[r][cword(kb)] = __funnelshift_l(__float_as_uint(x), w[r][cword(kb)], 2);
+                            w[r][cword(kb)] = __funnelshift_l(__float_as_uint(x[c]), w[r][cword(kb)], 2);
                         }
                     }
                 }
@@ -1045,15 +1080,16 @@ __global__ void __launch_bounds__(THREADS, 2) cost_kernel(const __grid_constant_
     }
     stage_init(sm);
     uint32_t phase = 0;
-    cost_tile<NCC>(sa, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm, nullptr, phase);
+    cost_tile<NCC, false>(sa, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.z, sm, nullptr, phase);
 }
 
 // Batched form: work items (frame, tile x, tile y, chunk | chunks << 16) of
 // any number of frames.  With a counter the CTAs are persistent and pull items
 // from it; without one, CTA i runs item i alone (short-lived CTAs, so that a
 // higher-priority stream can take SMs over at CTA granularity).  The frame's
-// arguments are staged in shared memory for the item.
-template <bool NCC>
+// arguments are staged in shared memory for the item.  DBG: the capture of a
+// chosen pair's warped tile (dbg_warp) is compiled in.
+template <bool NCC, bool DBG>
 __global__ void __launch_bounds__(THREADS, 2)
 cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ items, int n_items, int* counter)
 {
@@ -1081,7 +1117,7 @@ cost_batch_kernel(const CostArgs* __restrict__ args, const int4* __restrict__ it
             for (int i = threadIdx.x; i < (int)(sizeof(CostArgs) / sizeof(int)); i += THREADS) dst[i] = src[i];
         }
         __syncthreads();
-        cost_tile<NCC>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm, stg, phase);
+        cost_tile<NCC, DBG>(sa, w.y, w.z, w.w & 0xFFFF, w.w >> 16, sm, stg, phase);
         __syncthreads();
         if (!counter) break;
     }
@@ -1106,8 +1142,10 @@ void cost_smem_optin()
     const int smem = (int)sizeof(SmemCost);
     cudaFuncSetAttribute(cost_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(cost_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(cost_batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
-    cudaFuncSetAttribute(cost_batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    cudaFuncSetAttribute(cost_batch_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    cudaFuncSetAttribute(cost_batch_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    cudaFuncSetAttribute(cost_batch_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    cudaFuncSetAttribute(cost_batch_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
     done[dev] = true;
 }
 }  // namespace
@@ -1125,11 +1163,12 @@ void launch_cost(const CostArgs& a, cudaStream_t st)
 }
 
 void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas, bool ncc,
-                       cudaStream_t st)
+                       bool dbg, cudaStream_t st)
 {
     cost_smem_optin();
     if (n_items <= 0) return;
-    auto kern = ncc ? cost_batch_kernel<true> : cost_batch_kernel<false>;
+    auto kern = ncc ? (dbg ? cost_batch_kernel<true, true> : cost_batch_kernel<true, false>)
+                    : (dbg ? cost_batch_kernel<false, true> : cost_batch_kernel<false, false>);
     if (ctas > 0) {
         cudaMemsetAsync(counter, 0, sizeof(int), st);
         kern<<<ctas, THREADS, kBatchSmem, st>>>(args, items, n_items, counter);

@@ -1011,8 +1011,10 @@ fassmvs_status run_batch(fassmvs_ctx* c, const fassmvs_frame* frames, int n, cud
                           "staging copy"));
         {
             StageTimer tm(c, FASSMVS_STAGE_COST, st);
+            // the kernel that copies the warped tile out only while a pair is chosen
+            const bool dbg = l == c->dbg_level && c->dbg_warp_g >= 0;
             fm::launch_cost_batch((const fm::CostArgs*)(sg.dev + at_cargs), (const int4*)(sg.dev + at_items),
-                                  (int)items.size(), (int*)counter, ctas, cfg.cost != 0, st);
+                                  (int)items.size(), (int*)counter, ctas, cfg.cost != 0, dbg, st);
         }
         {
             StageTimer tm(c, FASSMVS_STAGE_RELAYOUT, st);

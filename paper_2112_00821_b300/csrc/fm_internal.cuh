@@ -117,9 +117,11 @@ constexpr int kStageBX = 128, kStageBY = 80;
 void launch_cost(const CostArgs& a, cudaStream_t st);
 // multi-frame form: items[i] = (frame, tile x, tile y, chunk | chunks << 16);
 // ctas > 0 persistent CTAs pulling items from *counter, else one CTA per item;
-// ncc: every frame's args use the NCC cost (else the census)
+// ncc: every frame's args use the NCC cost (else the census); dbg: the kernel
+// that copies a chosen pair's warped tile to dbg_warp (a separate
+// instantiation, so the usual one holds none of that code)
 void launch_cost_batch(const CostArgs* args, const int4* items, int n_items, int* counter, int ctas, bool ncc,
-                       cudaStream_t st);
+                       bool dbg, cudaStream_t st);
 int cost_tiles_x(int W);
 int cost_tiles_y(int H);
 
