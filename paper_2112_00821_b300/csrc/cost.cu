@@ -95,7 +95,8 @@ __device__ __forceinline__ df df_add(df a, df b)
 }
 
 // Values whose high word lies on the 2^-10 grid with magnitude below 2^12
-// add exactly in FP32, so stepping down a column costs two additions: the
+// add exactly in FP32, so stepping down a column costs two additions
+// (grid_add2: one packed addition per word for a lane's two columns): the
 // homography is scaled (prep_level_kernel) so that |N|, |D| stay below 2^12
 // over and well around the image, and the step's high words are on the grid.
 constexpr float GRID_MAGIC = 12288.0f;   // 1.5 * 2^13: rounds |x| < 2^12 to the 2^-10 grid
@@ -104,7 +105,6 @@ __device__ __forceinline__ df to_grid(df a)
     float h = __fsub_rn(__fadd_rn(a.hi, GRID_MAGIC), GRID_MAGIC);
     return {h, __fadd_rn(a.lo, __fsub_rn(a.hi, h))};
 }
-__device__ __forceinline__ df grid_add(df a, df b) { return {__fadd_rn(a.hi, b.hi), __fadd_rn(a.lo, b.lo)}; }
 
 // a * b for an integer-valued b (|b| < 2^24)
 __device__ __forceinline__ df df_mul_int(df a, float b)
@@ -125,16 +125,18 @@ __device__ __forceinline__ float rcp_approx(float x)
 
 __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h + i), __ldg(h + 9 + i)}; }
 
-// One coordinate of a warped sample.  N / D is the position (D > 0, r ~ 1 / D;
-// r = 0 for a point behind the camera, which then reads pixel 0 with weight 0,
-// the clamped position of (-inf, -inf)).  The FP32 quotient q = N.hi / D and
-// the residual e = N - q D of the whole numerator (formed with fused
-// multiply-adds, exact to far below an ulp of q) give the position as
-// q + e / D in double-float; with c the integer nearest q, the offset
-// f = (q - c) + e / D (the difference exact, one rounding in the fused
-// multiply-add) is accurate to half an ulp of f: 1.5e-8 px, 3e-8 where the
-// position lies within |N.lo / D| plus an ulp of q of a half integer and
-// |f| passes 1/2.
+// One coordinate of a warped sample.  N / D is the position (D > 0); the
+// arithmetic carries nr ~ -1 / D (nr = 0 for a point behind the camera, which
+// then reads pixel 0 with weight 0, the clamped position of (-inf, -inf)), so
+// that the packed form below needs no negated operand: nq = N.hi nr is minus
+// the FP32 quotient q = N.hi / D, and the residual e = N - q D of the whole
+// numerator (formed with fused multiply-adds, exact to far below an ulp of q)
+// gives the position as q + e / D in double-float.  With c the integer
+// nearest q, the offset f = (q - c) + e / D (the difference exact, one
+// rounding in the fused multiply-add) is accurate to half an ulp of f: 1.5e-8
+// px, 3e-8 where the position lies within |N.lo / D| plus an ulp of q of a
+// half integer and |f| passes 1/2.  Every value here is the exact negation of
+// the one the positive form would round (round-to-nearest is symmetric).
 // The bilinear blend weighs pixel c and its neighbour c + s
 // (s = the sign of f) with |f| < 1, so it interpolates between them and never
 // extrapolates (a floor-based cell would, by up to that error times the
@@ -142,12 +144,13 @@ __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h +
 // the nearest image pixel with weight 0, its clamp.  in: the position lies on
 // [0, size - 1].
 struct Coord { int i, s; float w; bool in; };
-__device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
+__device__ __forceinline__ Coord coord(df N, df D, float nr, float maxf)
 {
-    const float q = __fmul_rn(N.hi, r);
-    const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
+    const float nq = __fmul_rn(N.hi, nr);
+    const float e = __fmaf_rn(nq, D.lo, __fadd_rn(__fmaf_rn(nq, D.hi, N.hi), N.lo));
+    const float q = -nq;
     const float c = rintf(fminf(fmaxf(q, -1.0f), maxf + 1.0f));     // NaN -> -1
-    const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
+    const float f = __fmaf_rn(e, -nr, __fsub_rn(q, c));
     const bool neg = f < 0.0f;
     const float nb = neg ? __fsub_rn(c, 1.0f) : __fadd_rn(c, 1.0f);
     const float cc = fminf(fmaxf(c, 0.0f), maxf);
@@ -156,31 +159,15 @@ __device__ __forceinline__ Coord coord(df N, df D, float r, float maxf)
     return {__float_as_int(__fadd_rn(cc, MAGIC)) - MAGIC_BITS, edge ? 0 : (neg ? -1 : 1), edge ? 0.0f : fabsf(f), in};
 }
 
-// The same for a position known to lie 2 px or more inside the image (a pair
-// whose whole sample tile maps there): no clamping, the same arithmetic, so
-// the same values as coord gives there, bit for bit.
-__device__ __forceinline__ Coord coord_in(df N, df D, float r)
-{
-    const float q = __fmul_rn(N.hi, r);
-    const float e = __fmaf_rn(-q, D.lo, __fadd_rn(__fmaf_rn(-q, D.hi, N.hi), N.lo));
-    const float c = rintf(q);
-    const float f = __fmaf_rn(e, r, __fsub_rn(q, c));
-    return {__float_as_int(__fadd_rn(c, MAGIC)) - MAGIC_BITS, f < 0.0f ? -1 : 1, fabsf(f), true};
-}
-
 // The nearest pixel, neighbour steps and weights of one warped sample, and
 // whether its position lies on the image grid.
 struct SPos { int iu, iv, su, sv; float a, b; };
 
-// a sample of a pair whose whole tile maps 2 px or more inside the image
-__device__ __forceinline__ SPos sample_pos_in(df Nu, df Nv, df Dn)
+// -1 / D to about half an ulp (one Newton step on the approximation of the
+// reciprocal of -D; the approximation's sign is that of its argument)
+__device__ __forceinline__ float neg_recip(float dsum, float nr0)
 {
-    const float dsum = __fadd_rn(Dn.hi, Dn.lo);
-    const float r0 = rcp_approx(dsum);
-    const float r = __fmaf_rn(r0, __fmaf_rn(-dsum, r0, 1.0f), r0);
-    const Coord cu = coord_in(Nu, Dn, r);
-    const Coord cv = coord_in(Nv, Dn, r);
-    return {cu.i, cv.i, cu.s, cv.s, cu.w, cv.w};
+    return __fmaf_rn(nr0, __fmaf_rn(dsum, nr0, 1.0f), nr0);
 }
 
 template <bool WANT_OK>
@@ -188,13 +175,47 @@ __device__ __forceinline__ SPos sample_pos(float wm1, float hm1, df Nu, df Nv, d
 {
     const float dsum = __fadd_rn(Dn.hi, Dn.lo);
     const bool front = dsum > 0.0f;
-    // 1 / D to about half an ulp (one Newton step on the approximation)
-    const float r0 = rcp_approx(dsum);
-    const float r = front ? __fmaf_rn(r0, __fmaf_rn(-dsum, r0, 1.0f), r0) : 0.0f;
-    const Coord cu = coord(Nu, Dn, r, wm1);
-    const Coord cv = coord(Nv, Dn, r, hm1);
+    const float nr = front ? neg_recip(dsum, rcp_approx(-dsum)) : 0.0f;
+    const Coord cu = coord(Nu, Dn, nr, wm1);
+    const Coord cv = coord(Nv, Dn, nr, hm1);
     if (WANT_OK) ok = front && cu.in && cv.in;
     return {cu.i, cv.i, cu.s, cv.s, cu.w, cv.w};
+}
+
+// ---- the two samples of a lane (columns lane and 32 + lane) at once, for a
+// pair whose whole tile maps 2 px or more inside the image: no clamping, and
+// each FP32 operation of the form above done as one packed FP32x2 operation
+// (each half rounded as the scalar one), so the values equal the scalar
+// path's bit for bit
+struct df2 { float2 hi, lo; };
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ df2 pack(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+__device__ __forceinline__ df lo_half(df2 a) { return {a.hi.x, a.lo.x}; }
+__device__ __forceinline__ df hi_half(df2 a) { return {a.hi.y, a.lo.y}; }
+__device__ __forceinline__ df2 grid_add2(df2 a, df2 b) { return {__fadd2_rn(a.hi, b.hi), __fadd2_rn(a.lo, b.lo)}; }
+
+struct Coord2 { int i0, i1, s0, s1; float2 w; };
+__device__ __forceinline__ Coord2 coord2_in(df2 N, df2 D, float2 nr)
+{
+    const float2 nq = __fmul2_rn(N.hi, nr);
+    const float2 e = __ffma2_rn(nq, D.lo, __fadd2_rn(__ffma2_rn(nq, D.hi, N.hi), N.lo));
+    // -c = rint(-q); -f = e nr + (-q - (-c))
+    const float2 nc = make_float2(rintf(nq.x), rintf(nq.y));
+    const float2 nf = __ffma2_rn(e, nr, __ffma2_rn(nc, f2(-1.0f), nq));
+    const float2 cm = __fadd2_rn(nc, f2(MAGIC));
+    return {MAGIC_BITS - __float_as_int(cm.x), MAGIC_BITS - __float_as_int(cm.y), nf.x > 0.0f ? -1 : 1,
+            nf.y > 0.0f ? -1 : 1, make_float2(fabsf(nf.x), fabsf(nf.y))};
+}
+
+struct SPos2 { int iu0, iv0, su0, sv0, iu1, iv1, su1, sv1; float2 a, b; };
+__device__ __forceinline__ SPos2 sample_pos2_in(df2 Nu, df2 Nv, df2 Dn)
+{
+    const float2 dsum = __fadd2_rn(Dn.hi, Dn.lo);
+    const float2 nr0 = make_float2(rcp_approx(-dsum.x), rcp_approx(-dsum.y));
+    const float2 nr = __ffma2_rn(nr0, __ffma2_rn(dsum, nr0, f2(1.0f)), nr0);
+    const Coord2 cu = coord2_in(Nu, Dn, nr);
+    const Coord2 cv = coord2_in(Nv, Dn, nr);
+    return {cu.i0, cv.i0, cu.s0, cv.s0, cu.i1, cv.i1, cu.s1, cv.s1, cu.w, cv.w};
 }
 
 // 2^23 + b as a float for a byte b (exact)
@@ -245,6 +266,35 @@ __device__ __forceinline__ float taps_staged(const uint8_t* stg, int sx0, int sy
     }
     const uint8_t* r0 = stg + o;
     return blend(r0[0], r0[p.su], r0[dv], r0[dv + p.su], p.a, p.b, pl);
+}
+
+// the two samples of a lane from the staged box (interior pairs: the
+// footprints lie in it), blended as blend() does, as FP32x2 pairs: the tap
+// differences and the lerps are single roundings of the same operands
+__device__ __forceinline__ float2 taps2_staged(const uint8_t* stg, int sx0, int sy0, const SPos2& p, bool& pl0,
+                                               bool& pl1)
+{
+    const int o0 = (p.iv0 - sy0) * kStageBX + (p.iu0 - sx0), dv0 = p.sv0 * kStageBX;
+    const int o1 = (p.iv1 - sy0) * kStageBX + (p.iu1 - sx0), dv1 = p.sv1 * kStageBX;
+    if (!FM_IN(o0 + min(p.su0, 0) + min(dv0, 0), kStageBX * kStageBY, 0x101) ||
+        !FM_IN(o0 + max(p.su0, 0) + max(dv0, 0), kStageBX * kStageBY, 0x101) ||
+        !FM_IN(o1 + min(p.su1, 0) + min(dv1, 0), kStageBX * kStageBY, 0x101) ||
+        !FM_IN(o1 + max(p.su1, 0) + max(dv1, 0), kStageBX * kStageBY, 0x101)) {
+        pl0 = pl1 = false;
+        return make_float2(0.0f, 0.0f);
+    }
+    const uint8_t* r0 = stg + o0;
+    const uint8_t* r1 = stg + o1;
+    const int a0 = r0[0], au = r0[p.su0], av = r0[dv0], auv = r0[dv0 + p.su0];
+    const int b0 = r1[0], bu = r1[p.su1], bv = r1[dv1], buv = r1[dv1 + p.su1];
+    pl0 = ((a0 ^ au) | (av ^ auv) | (a0 ^ av)) == 0;
+    pl1 = ((b0 ^ bu) | (bv ^ buv) | (b0 ^ bv)) == 0;
+    const float2 t0 = make_float2(bf(a0), bf(b0)), tv = make_float2(bf(av), bf(bv));
+    const float2 d0 = __ffma2_rn(t0, f2(-1.0f), make_float2(bf(au), bf(bu)));
+    const float2 d1 = __ffma2_rn(tv, f2(-1.0f), make_float2(bf(auv), bf(buv)));
+    const float2 top = __ffma2_rn(p.a, d0, __fadd2_rn(t0, f2(-VBIAS)));
+    const float2 bot = __ffma2_rn(p.a, d1, __fadd2_rn(tv, f2(-VBIAS)));
+    return __ffma2_rn(p.b, __ffma2_rn(top, f2(-1.0f), bot), top);
 }
 
 // the 2x2 footprint lies in the staged box
@@ -757,11 +807,12 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 const df by_u = df_add(df_mul_int(h1, fy), h2);
                 const df by_v = df_add(df_mul_int(h4, fy), h5);
                 const df by_d = df_add(df_mul_int(h7, fy), h8);
-                df u0 = to_grid(df_add(df_mul_int(h0, fx0), by_u)), v0 = to_grid(df_add(df_mul_int(h3, fx0), by_v));
-                df d0 = to_grid(df_add(df_mul_int(h6, fx0), by_d));
-                df u1 = to_grid(df_add(df_mul_int(h0, fx1), by_u)), v1 = to_grid(df_add(df_mul_int(h3, fx1), by_v));
-                df d1 = to_grid(df_add(df_mul_int(h6, fx1), by_d));
+                // numerators and denominator of the lane's two columns, as pairs
+                df2 U = pack(to_grid(df_add(df_mul_int(h0, fx0), by_u)), to_grid(df_add(df_mul_int(h0, fx1), by_u)));
+                df2 Vn = pack(to_grid(df_add(df_mul_int(h3, fx0), by_v)), to_grid(df_add(df_mul_int(h3, fx1), by_v)));
+                df2 Dn = pack(to_grid(df_add(df_mul_int(h6, fx0), by_d)), to_grid(df_add(df_mul_int(h6, fx1), by_d)));
                 const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
+                const df2 S1 = pack(s1, s1), S4 = pack(s4, s4), S7 = pack(s7, s7);
                 float(*vrow)[SW] = sm.val[buf];
                 uint32_t rk_lo = 0u, rk_hi = 0u;
                 // the row loop in two variants, chosen once per (plane, view):
@@ -781,29 +832,26 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                     // as the clamped reading makes them equal)
                     if (Y > H - 1) break;
                     if (jj > 0 && Y >= 1 && Y <= H - 1) {
-                        u0 = grid_add(u0, s1); v0 = grid_add(v0, s4); d0 = grid_add(d0, s7);
-                        u1 = grid_add(u1, s1); v1 = grid_add(v1, s4); d1 = grid_add(d1, s7);
+                        U = grid_add2(U, S1); Vn = grid_add2(Vn, S4); Dn = grid_add2(Dn, S7);
                     }
                     bool ok0 = false, ok1 = false;
                     const bool centre_row = j >= 3 && j < 3 + PH;
-                    SPos p0, p1;
-                    if constexpr (IN) {
-                        p0 = sample_pos_in(u0, v0, d0);
-                        p1 = sample_pos_in(u1, v1, d1);
-                        ok0 = ok1 = true;
-                    } else if (centre_row) {
-                        p0 = sample_pos<true>(wm1, hm1, u0, v0, d0, ok0);
-                        p1 = sample_pos<true>(wm1, hm1, u1, v1, d1, ok1);
-                    } else {
-                        p0 = sample_pos<false>(wm1, hm1, u0, v0, d0, ok0);
-                        p1 = sample_pos<false>(wm1, hm1, u1, v1, d1, ok1);
-                    }
                     float f0, f1;
                     bool pl0, pl1;
                     if constexpr (IN) {
-                        f0 = taps_staged(sp, sx0, sy0, p0, pl0);
-                        f1 = taps_staged(sp, sx0, sy0, p1, pl1);
+                        const float2 fv = taps2_staged(sp, sx0, sy0, sample_pos2_in(U, Vn, Dn), pl0, pl1);
+                        f0 = fv.x;
+                        f1 = fv.y;
+                        ok0 = ok1 = true;
                     } else {
+                        SPos p0, p1;
+                        if (centre_row) {
+                            p0 = sample_pos<true>(wm1, hm1, lo_half(U), lo_half(Vn), lo_half(Dn), ok0);
+                            p1 = sample_pos<true>(wm1, hm1, hi_half(U), hi_half(Vn), hi_half(Dn), ok1);
+                        } else {
+                            p0 = sample_pos<false>(wm1, hm1, lo_half(U), lo_half(Vn), lo_half(Dn), ok0);
+                            p1 = sample_pos<false>(wm1, hm1, hi_half(U), hi_half(Vn), hi_half(Dn), ok1);
+                        }
                         // a row whose taps all lie in the box (the usual case)
                         // takes one straight shared-memory path; without a box
                         // (sp null, origin far away) every tap reads global memory
