@@ -125,75 +125,37 @@ __device__ __forceinline__ float rcp_approx(float x)
 
 __device__ __forceinline__ df load_df(const float* h, int i) { return {__ldg(h + i), __ldg(h + 9 + i)}; }
 
-// One coordinate of a warped sample.  N / D is the position (D > 0); the
-// arithmetic carries nr ~ -1 / D (nr = 0 for a point behind the camera, which
-// then reads pixel 0 with weight 0, the clamped position of (-inf, -inf)), so
-// that the packed form below needs no negated operand: nq = N.hi nr is minus
-// the FP32 quotient q = N.hi / D, and the residual e = N - q D of the whole
-// numerator (formed with fused multiply-adds, exact to far below an ulp of q)
-// gives the position as q + e / D in double-float.  With c the integer
-// nearest q, the offset f = (q - c) + e / D (the difference exact, one
-// rounding in the fused multiply-add) is accurate to half an ulp of f: 1.5e-8
-// px, 3e-8 where the position lies within |N.lo / D| plus an ulp of q of a
-// half integer and |f| passes 1/2.  Every value here is the exact negation of
-// the one the positive form would round (round-to-nearest is symmetric).
-// The bilinear blend weighs pixel c and its neighbour c + s
-// (s = the sign of f) with |f| < 1, so it interpolates between them and never
-// extrapolates (a floor-based cell would, by up to that error times the
-// change of slope across the cell edge); a position outside the image reads
-// the nearest image pixel with weight 0, its clamp.  in: the position lies on
-// [0, size - 1].
-struct Coord { int i, s; float w; bool in; };
-__device__ __forceinline__ Coord coord(df N, df D, float nr, float maxf)
-{
-    const float nq = __fmul_rn(N.hi, nr);
-    const float e = __fmaf_rn(nq, D.lo, __fadd_rn(__fmaf_rn(nq, D.hi, N.hi), N.lo));
-    const float q = -nq;
-    const float c = rintf(fminf(fmaxf(q, -1.0f), maxf + 1.0f));     // NaN -> -1
-    const float f = __fmaf_rn(e, -nr, __fsub_rn(q, c));
-    const bool neg = f < 0.0f;
-    const float nb = neg ? __fsub_rn(c, 1.0f) : __fadd_rn(c, 1.0f);
-    const float cc = fminf(fmaxf(c, 0.0f), maxf);
-    const bool edge = cc != c || nb < 0.0f || nb > maxf;
-    const bool in = c >= 0.0f && c <= maxf && !(c == 0.0f && neg) && !(c == maxf && f > 0.0f);
-    return {__float_as_int(__fadd_rn(cc, MAGIC)) - MAGIC_BITS, edge ? 0 : (neg ? -1 : 1), edge ? 0.0f : fabsf(f), in};
-}
-
-// The nearest pixel, neighbour steps and weights of one warped sample, and
-// whether its position lies on the image grid.
+// The coordinates of a lane's two warped samples (columns lane and
+// 32 + lane), each FP32 operation done once for both as a packed FP32x2
+// operation (each half rounded as the scalar operation would round it).  For
+// one coordinate, N / D is the position (D > 0); the arithmetic carries
+// nr ~ -1 / D (one Newton step on the approximate reciprocal of -D, whose sign
+// is that of its argument; nr = 0 for a point behind the camera, which then
+// reads pixel 0 with weight 0, the clamped position of (-inf, -inf)), so that
+// no packed operand is negated: nq = N.hi nr is minus the FP32 quotient
+// q = N.hi / D, and the residual e = N - q D of the whole numerator (formed
+// with fused multiply-adds, exact to far below an ulp of q) gives the
+// position as q + e / D in double-float.  With c the integer nearest q, the
+// offset f = (q - c) + e / D (the difference exact, one rounding in the fused
+// multiply-add) is accurate to half an ulp of f: 1.5e-8 px, 3e-8 where the
+// position lies within |N.lo / D| plus an ulp of q of a half integer and |f|
+// passes 1/2.  Every value is the exact negation of the one the positive form
+// would round (round-to-nearest is symmetric).  The bilinear blend weighs
+// pixel c and its neighbour c + s (s = the sign of f) with |f| < 1, so it
+// interpolates between them and never extrapolates (a floor-based cell
+// would, by up to that error times the change of slope across the cell
+// edge); a position outside the image reads the nearest image pixel with
+// weight 0, its clamp.
+//
+// The nearest pixel, neighbour steps and weights of one warped sample.
 struct SPos { int iu, iv, su, sv; float a, b; };
 
-// -1 / D to about half an ulp (one Newton step on the approximation of the
-// reciprocal of -D; the approximation's sign is that of its argument)
-__device__ __forceinline__ float neg_recip(float dsum, float nr0)
-{
-    return __fmaf_rn(nr0, __fmaf_rn(dsum, nr0, 1.0f), nr0);
-}
-
-template <bool WANT_OK>
-__device__ __forceinline__ SPos sample_pos(float wm1, float hm1, df Nu, df Nv, df Dn, bool& ok)
-{
-    const float dsum = __fadd_rn(Dn.hi, Dn.lo);
-    const bool front = dsum > 0.0f;
-    const float nr = front ? neg_recip(dsum, rcp_approx(-dsum)) : 0.0f;
-    const Coord cu = coord(Nu, Dn, nr, wm1);
-    const Coord cv = coord(Nv, Dn, nr, hm1);
-    if (WANT_OK) ok = front && cu.in && cv.in;
-    return {cu.i, cv.i, cu.s, cv.s, cu.w, cv.w};
-}
-
-// ---- the two samples of a lane (columns lane and 32 + lane) at once, for a
-// pair whose whole tile maps 2 px or more inside the image: no clamping, and
-// each FP32 operation of the form above done as one packed FP32x2 operation
-// (each half rounded as the scalar one), so the values equal the scalar
-// path's bit for bit
 struct df2 { float2 hi, lo; };
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 __device__ __forceinline__ df2 pack(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
-__device__ __forceinline__ df lo_half(df2 a) { return {a.hi.x, a.lo.x}; }
-__device__ __forceinline__ df hi_half(df2 a) { return {a.hi.y, a.lo.y}; }
 __device__ __forceinline__ df2 grid_add2(df2 a, df2 b) { return {__fadd2_rn(a.hi, b.hi), __fadd2_rn(a.lo, b.lo)}; }
 
+// a pair whose whole tile maps 2 px or more inside the image: no clamping
 struct Coord2 { int i0, i1, s0, s1; float2 w; };
 __device__ __forceinline__ Coord2 coord2_in(df2 N, df2 D, float2 nr)
 {
@@ -215,6 +177,52 @@ __device__ __forceinline__ SPos2 sample_pos2_in(df2 Nu, df2 Nv, df2 Dn)
     const float2 nr = __ffma2_rn(nr0, __ffma2_rn(dsum, nr0, f2(1.0f)), nr0);
     const Coord2 cu = coord2_in(Nu, Dn, nr);
     const Coord2 cv = coord2_in(Nv, Dn, nr);
+    return {cu.i0, cv.i0, cu.s0, cv.s0, cu.i1, cv.i1, cu.s1, cv.s1, cu.w, cv.w};
+}
+
+// Any pair (the clamped reading): -q is clamped to [-size, 1] before the
+// rounding (so q to [-1, size], a NaN to -1), and per half: the nearest pixel
+// clamped to the image, no neighbour step (weight 0) where the pixel or its
+// neighbour leaves the image, and in = the position lies on [0, size - 1].
+// For a position 2 px or more inside the image it gives what coord2_in
+// gives.
+__device__ __forceinline__ void coord_fix(int ci, float nf, int maxi, int& i, int& s, float& w, bool& in)
+{
+    const bool neg = nf > 0.0f;                           // f < 0
+    const int nb = neg ? ci - 1 : ci + 1;
+    const int cc = min(max(ci, 0), maxi);
+    const bool edge = cc != ci || (unsigned)nb > (unsigned)maxi;
+    in = (unsigned)ci <= (unsigned)maxi && !(ci == 0 && neg) && !(ci == maxi && nf < 0.0f);
+    i = cc;
+    s = edge ? 0 : (neg ? -1 : 1);
+    w = edge ? 0.0f : fabsf(nf);
+}
+__device__ __forceinline__ Coord2 coord2_clamped(df2 N, df2 D, float2 nr, float maxf, int maxi, bool& in0, bool& in1)
+{
+    const float2 nq = __fmul2_rn(N.hi, nr);
+    const float2 e = __ffma2_rn(nq, D.lo, __fadd2_rn(__ffma2_rn(nq, D.hi, N.hi), N.lo));
+    const float lo = -(maxf + 1.0f);
+    const float2 nc = make_float2(rintf(fmaxf(fminf(nq.x, 1.0f), lo)), rintf(fmaxf(fminf(nq.y, 1.0f), lo)));
+    const float2 nf = __ffma2_rn(e, nr, __ffma2_rn(nc, f2(-1.0f), nq));
+    const float2 cm = __fadd2_rn(nc, f2(MAGIC));
+    Coord2 o;
+    coord_fix(MAGIC_BITS - __float_as_int(cm.x), nf.x, maxi, o.i0, o.s0, o.w.x, in0);
+    coord_fix(MAGIC_BITS - __float_as_int(cm.y), nf.y, maxi, o.i1, o.s1, o.w.y, in1);
+    return o;
+}
+// ok0 / ok1: the sample's position lies on the image grid (and in front)
+__device__ __forceinline__ SPos2 sample_pos2(float wm1, float hm1, df2 Nu, df2 Nv, df2 Dn, bool& ok0, bool& ok1)
+{
+    const float2 dsum = __fadd2_rn(Dn.hi, Dn.lo);
+    const float2 nr0 = make_float2(rcp_approx(-dsum.x), rcp_approx(-dsum.y));
+    float2 nr = __ffma2_rn(nr0, __ffma2_rn(dsum, nr0, f2(1.0f)), nr0);
+    const bool f0 = dsum.x > 0.0f, f1 = dsum.y > 0.0f;
+    nr = make_float2(f0 ? nr.x : 0.0f, f1 ? nr.y : 0.0f);
+    bool iu0, iu1, iv0, iv1;
+    const Coord2 cu = coord2_clamped(Nu, Dn, nr, wm1, (int)wm1, iu0, iu1);
+    const Coord2 cv = coord2_clamped(Nv, Dn, nr, hm1, (int)hm1, iv0, iv1);
+    ok0 = f0 && iu0 && iv0;
+    ok1 = f1 && iu1 && iv1;
     return {cu.i0, cv.i0, cu.s0, cv.s0, cu.i1, cv.i1, cu.s1, cv.s1, cu.w, cv.w};
 }
 
@@ -844,21 +852,17 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                         f1 = fv.y;
                         ok0 = ok1 = true;
                     } else {
-                        SPos p0, p1;
-                        if (centre_row) {
-                            p0 = sample_pos<true>(wm1, hm1, lo_half(U), lo_half(Vn), lo_half(Dn), ok0);
-                            p1 = sample_pos<true>(wm1, hm1, hi_half(U), hi_half(Vn), hi_half(Dn), ok1);
-                        } else {
-                            p0 = sample_pos<false>(wm1, hm1, lo_half(U), lo_half(Vn), lo_half(Dn), ok0);
-                            p1 = sample_pos<false>(wm1, hm1, hi_half(U), hi_half(Vn), hi_half(Dn), ok1);
-                        }
+                        const SPos2 q = sample_pos2(wm1, hm1, U, Vn, Dn, ok0, ok1);
+                        const SPos p0{q.iu0, q.iv0, q.su0, q.sv0, q.a.x, q.b.x};
+                        const SPos p1{q.iu1, q.iv1, q.su1, q.sv1, q.a.y, q.b.y};
                         // a row whose taps all lie in the box (the usual case)
                         // takes one straight shared-memory path; without a box
                         // (sp null, origin far away) every tap reads global memory
                         const bool b0 = in_box(sx0, sy0, p0), b1 = in_box(sx0, sy0, p1);
                         if (__all_sync(0xFFFFFFFFu, b0 && b1)) {
-                            f0 = taps_staged(sp, sx0, sy0, p0, pl0);
-                            f1 = taps_staged(sp, sx0, sy0, p1, pl1);
+                            const float2 fv = taps2_staged(sp, sx0, sy0, q, pl0, pl1);
+                            f0 = fv.x;
+                            f1 = fv.y;
                         } else {
                             f0 = b0 ? taps_staged(sp, sx0, sy0, p0, pl0) : taps_global(img, a.pitch, W, H, p0, pl0);
                             f1 = b1 ? taps_staged(sp, sx0, sy0, p1, pl1) : taps_global(img, a.pitch, W, H, p1, pl1);
