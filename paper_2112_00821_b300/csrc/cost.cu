@@ -155,6 +155,35 @@ __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 __device__ __forceinline__ df2 pack(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
 __device__ __forceinline__ df2 grid_add2(df2 a, df2 b) { return {__fadd2_rn(a.hi, b.hi), __fadd2_rn(a.lo, b.lo)}; }
 
+// The per-warp set-up of the stepping for the lane's two columns, packed as
+// above: df_mul_int, df_add with a term shared by both columns, and to_grid,
+// each half equal to the scalar function's result bit for bit (y - x is
+// formed as fma(x, -1, y), one rounding of the exact difference; -a.hi is
+// passed in so that no packed operand is negated).
+__device__ __forceinline__ df2 df_mul_int2(df a, float na_hi, float2 b)
+{
+    const float2 np = __fmul2_rn(f2(na_hi), b);                    // -p
+    const float2 e = __ffma2_rn(f2(a.hi), b, np);
+    const float2 lo = __ffma2_rn(f2(a.lo), b, e);
+    const float2 h = __ffma2_rn(np, f2(-1.0f), lo);                // p + lo
+    const float2 t = __fadd2_rn(h, np);                            // h - p
+    return {h, __ffma2_rn(t, f2(-1.0f), lo)};
+}
+__device__ __forceinline__ df2 df_add2(df2 a, df b)
+{
+    const float2 bh = f2(b.hi);
+    const float2 s = __fadd2_rn(a.hi, bh);
+    const float2 bb = __ffma2_rn(a.hi, f2(-1.0f), s);              // s - a
+    const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, f2(-1.0f), s), f2(-1.0f), a.hi),
+                                __ffma2_rn(bb, f2(-1.0f), bh));    // (a - (s - bb)) + (b - bb)
+    return {s, __fadd2_rn(e, __fadd2_rn(a.lo, f2(b.lo)))};
+}
+__device__ __forceinline__ df2 to_grid2(df2 a)
+{
+    const float2 h = __fadd2_rn(__fadd2_rn(a.hi, f2(GRID_MAGIC)), f2(-GRID_MAGIC));
+    return {h, __fadd2_rn(a.lo, __ffma2_rn(h, f2(-1.0f), a.hi))};
+}
+
 // a pair whose whole tile maps 2 px or more inside the image: no clamping
 struct Coord2 { int i0, i1, s0, s1; float2 w; };
 __device__ __forceinline__ Coord2 coord2_in(df2 N, df2 D, float2 nr)
@@ -816,9 +845,10 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
                 const df by_v = df_add(df_mul_int(h4, fy), h5);
                 const df by_d = df_add(df_mul_int(h7, fy), h8);
                 // numerators and denominator of the lane's two columns, as pairs
-                df2 U = pack(to_grid(df_add(df_mul_int(h0, fx0), by_u)), to_grid(df_add(df_mul_int(h0, fx1), by_u)));
-                df2 Vn = pack(to_grid(df_add(df_mul_int(h3, fx0), by_v)), to_grid(df_add(df_mul_int(h3, fx1), by_v)));
-                df2 Dn = pack(to_grid(df_add(df_mul_int(h6, fx0), by_d)), to_grid(df_add(df_mul_int(h6, fx1), by_d)));
+                const float2 fx = make_float2(fx0, fx1);
+                df2 U = to_grid2(df_add2(df_mul_int2(h0, -h0.hi, fx), by_u));
+                df2 Vn = to_grid2(df_add2(df_mul_int2(h3, -h3.hi, fx), by_v));
+                df2 Dn = to_grid2(df_add2(df_mul_int2(h6, -h6.hi, fx), by_d));
                 const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
                 const df2 S1 = pack(s1, s1), S4 = pack(s4, s4), S7 = pack(s7, s7);
                 float(*vrow)[SW] = sm.val[buf];
