@@ -60,6 +60,13 @@ struct SmemCost {
     float val[2][SH][SW];                // warped values minus 128 (FP32, unrounded)
     uint32_t okm[2][PH][2];              // centre-in-image bit per pixel column
     float hdf[2][18];                    // census: the pair's homography (high, low words), for near ties
+    // the pair's set-up of the stepping, written by the planning warp two
+    // pairs ahead: per lane the column terms h x of its two columns (U, V, D
+    // as packed high / low words), per sampling warp the row term of its first
+    // row, and the row steps
+    float4 xt[2][3][32];
+    float2 yt[2][NWARP][3];
+    float2 st[2][3];
     uint32_t rkb[2][SH][2];              // census: risky samples, one bit per sample (columns 0-31, 32-63)
     uint8_t rkcol[2][NWARP][64];         // census: per sampling warp and pixel column, its rows whose
                                          // window columns hold a risky sample (one bit per row)
@@ -152,7 +159,6 @@ struct SPos { int iu, iv, su, sv; float a, b; };
 
 struct df2 { float2 hi, lo; };
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
-__device__ __forceinline__ df2 pack(df a, df b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
 __device__ __forceinline__ df2 grid_add2(df2 a, df2 b) { return {__fadd2_rn(a.hi, b.hi), __fadd2_rn(a.lo, b.lo)}; }
 
 // The per-warp set-up of the stepping for the lane's two columns, packed as
@@ -670,6 +676,37 @@ __device__ __forceinline__ void stage_plan(const CostArgs& a, SmemCost& sm, uint
     }
 }
 
+// The planning warp: the set-up of pair (g, k)'s stepping into `slot` (see
+// SmemCost::xt), which the sampling warps combine exactly as they would
+// compute it themselves.  (The pair's homography for the near-tie recompute,
+// hdf, is read during the census while this runs for the pair two ahead: the
+// sampling warps keep storing it.)
+__device__ __forceinline__ void stage_setup(const CostArgs& a, SmemCost& sm, int tx0, int ty0, int g, int k,
+                                            int slot, int lane)
+{
+    const float* h = a.htab + ((size_t)(FM_IN(g, a.G, 0x108) ? g : 0) * a.V + k) * 18;
+    // column terms of columns lane and 32 + lane
+    const int W = a.W, H = a.H;
+    const float2 fx = make_float2((float)min(max(tx0 - 4 + lane, 0), W - 1), (float)min(max(tx0 + 28 + lane, 0), W - 1));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const df hc = load_df(h, 3 * c);
+        const df2 x = df_mul_int2(hc, -hc.hi, fx);
+        sm.xt[slot][c][lane] = make_float4(x.hi.x, x.hi.y, x.lo.x, x.lo.y);
+    }
+    // row term of warp w's first row (lane 3 w + c), and the row steps
+    if (lane < 3 * NWARP) {
+        const int w = lane / 3, c = lane - 3 * w;
+        const float fy = (float)min(max(ty0 - 3 + row_start(w), 0), H - 1);
+        const df y = df_add(df_mul_int(load_df(h, 3 * c + 1), fy), load_df(h, 3 * c + 2));
+        sm.yt[slot][w][c] = make_float2(y.hi, y.lo);
+    }
+    if (lane < 3) {
+        const df s = to_grid(load_df(h, 3 * lane + 1));
+        sm.st[slot][lane] = make_float2(s.hi, s.lo);
+    }
+}
+
 // One tile (bx, by) of one frame, plane chunk bz of nz, with the census (NCC
 // false) or NCC 5x5 cost.  Called by the single-frame grid kernel and by the
 // multi-frame kernel, both with their arguments in shared memory.
@@ -758,6 +795,13 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
         __syncwarp();
         stage_plan(a, sm, stg, tx0, ty0, glo, 0, 0, lane);
     }
+    // the set-up of the first two pairs; each later pair's comes from the
+    // planning warp two pairs ahead, after the barrier of the pair between
+    if (warp == kPlanWarp && ghi > glo) {
+        stage_setup(a, sm, tx0, ty0, glo, 0, 0, lane);
+        const int g1 = a.V > 1 ? glo : glo + 1, k1 = a.V > 1 ? 1 : 0;
+        if (g1 < ghi) stage_setup(a, sm, tx0, ty0, g1, k1, 1, lane);
+    }
     __syncthreads();
 
     // census role (warps 0-6): column 8 * warp + lane % 8, rows
@@ -767,8 +811,6 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
     const bool cact = warp < kCensusWarps;
     // sampling role: sample rows [rs, re), sample columns lane and 32 + lane
     const int rs = row_start(warp), re = row_start(warp + 1);
-    const int X0 = min(max(tx0 - 4 + lane, 0), W - 1);
-    const int X1 = min(max(tx0 + 28 + lane, 0), W - 1);
     const float wm1 = (float)(W - 1), hm1 = (float)(H - 1);
     // tile-relative sample row of the image's last row: rows past it are read
     // from it (computing them anew would round differently from the row that
@@ -833,24 +875,22 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
             if (do_sample) {
                 const uint8_t* sp = ready ? stg + buf * kStageBX * kStageBY : nullptr;
                 const int sx0 = ready ? sm.stg_x0[buf] : -(1 << 20), sy0 = ready ? sm.stg_y0[buf] : -(1 << 20);
-                const float* h = a.htab + ((size_t)(FM_IN(g, a.G, 0x108) ? g : 0) * a.V + k) * 18;
                 const uint8_t* img = a.views.img[k];
-                if (!NCC && lane < 18) sm.hdf[buf][lane] = __ldg(h + lane);
-                const df h0 = load_df(h, 0), h1 = load_df(h, 1), h2 = load_df(h, 2);
-                const df h3 = load_df(h, 3), h4 = load_df(h, 4), h5 = load_df(h, 5);
-                const df h6 = load_df(h, 6), h7 = load_df(h, 7), h8 = load_df(h, 8);
-                const float fy = (float)min(max(ty0 - 3 + rs, 0), H - 1);
-                const float fx0 = (float)X0, fx1 = (float)X1;
-                const df by_u = df_add(df_mul_int(h1, fy), h2);
-                const df by_v = df_add(df_mul_int(h4, fy), h5);
-                const df by_d = df_add(df_mul_int(h7, fy), h8);
-                // numerators and denominator of the lane's two columns, as pairs
-                const float2 fx = make_float2(fx0, fx1);
-                df2 U = to_grid2(df_add2(df_mul_int2(h0, -h0.hi, fx), by_u));
-                df2 Vn = to_grid2(df_add2(df_mul_int2(h3, -h3.hi, fx), by_v));
-                df2 Dn = to_grid2(df_add2(df_mul_int2(h6, -h6.hi, fx), by_d));
-                const df s1 = to_grid(h1), s4 = to_grid(h4), s7 = to_grid(h7);
-                const df2 S1 = pack(s1, s1), S4 = pack(s4, s4), S7 = pack(s7, s7);
+                if (!NCC && lane < 18)
+                    sm.hdf[buf][lane] = __ldg(a.htab + ((size_t)(FM_IN(g, a.G, 0x108) ? g : 0) * a.V + k) * 18 + lane);
+                // numerators and denominator of the lane's two columns, as
+                // pairs: column terms + the row term of the warp's first row
+                auto start = [&](int c) {
+                    const float4 x = sm.xt[buf][c][lane];
+                    const float2 y = sm.yt[buf][warp][c];
+                    return to_grid2(df_add2(df2{make_float2(x.x, x.y), make_float2(x.z, x.w)}, df{y.x, y.y}));
+                };
+                auto step = [&](int c) {
+                    const float2 t = sm.st[buf][c];
+                    return df2{f2(t.x), f2(t.y)};
+                };
+                df2 U = start(0), Vn = start(1), Dn = start(2);
+                const df2 S1 = step(0), S4 = step(1), S7 = step(2);
                 float(*vrow)[SW] = sm.val[buf];
                 uint32_t rk_lo = 0u, rk_hi = 0u;
                 // the row loop in two variants, chosen once per (plane, view):
@@ -1120,6 +1160,13 @@ __device__ __forceinline__ void cost_tile(const CostArgs& a, int bx, int by, int
 #pragma unroll
                     for (int r = 0; r < CH; ++r) slr[r] += (uint32_t)(corr[r] * (1 << sh));
                 }
+            }
+            // the planning warp has no census: the set-up of the pair two
+            // ahead, into the slot this pair's sampling has finished with
+            if (warp == kPlanWarp) {
+                int g2 = g, k2 = k + 2;
+                while (k2 >= a.V) { k2 -= a.V; ++g2; }
+                if (g2 < ghi) stage_setup(a, sm, tx0, ty0, g2, k2, buf, lane);
             }
             buf ^= 1;
         }
