@@ -110,6 +110,50 @@ def test_cost_volume_tiny_scene_vs_fp64(ctx, orc):
     assert diff <= 1e-4, diff
 
 
+def _blocky(g, H, W):
+    """Piecewise-constant 6x6 blocks of a few grey levels (two of them one
+    apart), saturated areas and one-pixel stripes: nearly every warped
+    sample is a plateau or sits on an edge between equal-looking regions."""
+    bs = 6
+    levels = np.array([0, 0, 37, 100, 101, 180, 255, 255], np.uint8)
+    blk = levels[g.integers(0, len(levels), ((H + bs - 1) // bs, (W + bs - 1) // bs))]
+    img = np.kron(blk, np.ones((bs, bs), np.uint8))[:H, :W].copy()
+    img[:, 3::17] = 101
+    img[10:40, 20:90] = 255
+    img[H - 30:H - 5, W - 80:W - 10] = 0
+    return np.ascontiguousarray(img)
+
+
+def test_cost_volume_plateau_rich_images_vs_fp64(ctx, orc):
+    """Near ties everywhere: blocky images under general-position homographies
+    give plateau ties, ties across saturated areas, and non-plateau samples
+    near an integer at every block edge.  The census decides each comparison
+    with the FP64 order (FP32 where the difference reaches 2^-14, else the
+    plateau rules or the double-float recompute): the stage entry point's
+    volume (global taps) and the estimate's level-0 volume (staged taps,
+    packed interior path) against the oracle, at most 1e-4 differing."""
+    from paper_2112_00821_b300 import fassmvs, synth
+    sc = synth.make_frame("planes", 77, W=240, H=160, G0=64, n_left=2, n_right=2, want_gt=False)
+    g = np.random.default_rng(77)
+    sc.ref = _blocky(g, 160, 240)
+    sc.nbrs = [_blocky(g, 160, 240) for _ in sc.nbrs]
+    got, exp = _scene_cost(ctx, orc, sc, 64)
+    frac = float(np.mean(got != exp))
+    print("PARITY cost plateau-rich 240x160x64: differing %.3g (%d voxels)" % (frac, int(np.sum(got != exp))))
+    assert frac <= 1e-4, frac
+    c = fassmvs.Context(fassmvs.default_config(levels=1, D=[64], paths=8, variant=0, p1=24))
+    c.set_cameras(sc.K, sc.R, sc.t, sc.side)
+    c.debug_capture(0)
+    c.estimate(dev(sc.ref), [dev(x) for x in sc.nbrs], fassmvs.planes_of(sc))
+    vol, _ = c.debug_dump(0, "cost")
+    c.sync()
+    est = host(vol, np.uint16)[..., :64]
+    c.close()
+    frac = float(np.mean(est != exp))
+    print("PARITY cost plateau-rich, estimate level 0: differing %.3g" % frac)
+    assert frac <= 1e-4, frac
+
+
 def test_cost_volume_points_behind_a_neighbour(ctx, orc):
     """A neighbour turned 75 degrees about the vertical axis sees part of
     every plane behind it (homogeneous w <= 0): those samples take the
