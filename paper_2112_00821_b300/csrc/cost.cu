@@ -9,7 +9,10 @@
 //      column in double-float arithmetic, the position's nearest pixel comes
 //      from an FP32 quotient q and its offset from the double-float residual
 //      N - q D, so it is accurate to ~1e-7 px; the value is the bilinear
-//      blend in lerp form about the nearest pixel in FP32, unrounded;
+//      blend in lerp form about the nearest pixel in FP32, unrounded; a
+//      lane's two columns go through packed FP32x2 operations, and the
+//      stepping's set-up comes from the planning warp (warp 7), which has no
+//      census and computes it for the pair two ahead while the others count;
 //   2. one __syncthreads (the sample tile is double-buffered);
 //   3. census: warp w < 7 takes columns 8w .. 8w + 7 of the tile, lane l
 //      column 8w + l % 8 and rows 7 (l / 8) .. + 6 (every lane of the seven
