@@ -474,6 +474,31 @@ def test_estimate_end_to_end(orc, variant, levels):
     assert np.mean(cdiff[vis]) < 2e-3
 
 
+def test_estimate_benchmark_frame_end_to_end(orc):
+    """The benchmark's whole estimate (1920x1080, 5 views, 256 planes, 4
+    levels with their windows, path-gradient SGM with the adaptive P2,
+    winner-takes-all, median, normals, confidence) against the FP64 oracle's
+    on non-occluded pixels: the same bars as at small sizes."""
+    from paper_2112_00821_b300 import fassmvs, synth
+    sc, base = synth.workload("fhd_1920x1080_g256_l4", 0, want_gt=True)
+    kw = dict(levels=base["levels"], D=base["D"], paths=base["paths"], variant=base["variant"], p1=base["p1"],
+              p2=base["p2"], adaptive_p2=base["adaptive_p2"])
+    d, n, conf = _run_estimate(fassmvs.default_config(**kw), sc)
+    d_e, n_e, c_e = orc.estimate(sc, orc.make_config(**kw))
+    rel = np.abs(d - d_e) / d_e
+    vis = _erode(synth.visibility_mask(sc), 3) & (np.linalg.norm(n_e, axis=-1) > 0)
+    ang = _angle_deg(n[vis], n_e[vis])
+    cdiff = np.abs(conf - c_e)
+    print("PARITY estimate 1080p benchmark frame: on %d non-occluded px depth L1-rel %.3g, differing depth %.3g, "
+          "normal angle p99.9 %.3g deg max %.3g deg, confidence mean abs %.3g"
+          % (vis.sum(), np.mean(rel[vis]), np.mean(rel[vis] > 1e-5), np.percentile(ang, 99.9), ang.max(),
+             np.mean(cdiff[vis])))
+    assert vis.mean() > 0.5
+    assert np.mean(rel[vis]) <= 1e-3, np.mean(rel[vis])
+    assert np.percentile(ang, 99.9) <= 0.5
+    assert np.mean(cdiff[vis]) < 2e-3
+
+
 def test_estimate_equals_the_stage_entry_points_at_full_size(ctx):
     """The benchmark's frame at one level (1920x1080, 5 views, 256 planes,
     path-gradient SGM with the adaptive P2): the estimate, i.e. the batched
