@@ -70,24 +70,26 @@ def test_ncc_cost_volume_flat_regions_and_invalid_views(nctx, orc):
     assert np.all(exp[14:26, 14:26] == 255)
 
 
-def test_ncc_cost_volume_fhd_sampled(nctx, orc):
+def test_ncc_cost_volume_fhd_every_voxel(nctx, orc):
+    """Every voxel of the 1080p benchmark frame's NCC cost volume (1920 x
+    1080 x 256 planes, 5 views) against the FP64 oracle, band by band: the
+    FP32 correlation can round a cost next to a .5 boundary the other way, so
+    at most 1e-4 of the voxels may differ."""
     from paper_2112_00821_b300 import synth
     sc, _ = synth.workload("fhd_1920x1080_g256_l4", 0, want_gt=False)
     got = nctx.cost_volume(dev(sc.ref), [dev(x) for x in sc.nbrs], sc.side, sc.K, sc.R, sc.t, sc.plane_n,
                            sc.rho_far, sc.drho, 256)
-    n = 100_000
-    g = np.random.default_rng(2)
-    xs, ys, gs = g.integers(0, 1920, n), g.integers(0, 1080, n), g.integers(0, 256, n)
-    xs[:400] = np.r_[np.zeros(200, int), np.full(200, 1919)]
-    ys[400:800] = np.r_[np.zeros(200, int), np.full(200, 1079)]
-    gs[800:1200] = np.r_[np.zeros(200, int), np.full(200, 255)]
-    exp = orc.cost_at(sc.ref, sc.nbrs, sc.side, sc.K, sc.R, sc.t, sc.plane_n, sc.rho_far, sc.drho, xs, ys, gs,
-                      cost=1)
-    gv = _host16(got[torch.from_numpy(ys).cuda(), torch.from_numpy(xs).cuda(), torch.from_numpy(gs).cuda()])
-    frac = float(np.mean(gv != exp))
-    print("PARITY ncc fhd sampled %d voxels: differing %.3g (max |diff| %d)"
-          % (n, frac, int(np.abs(gv.astype(int) - exp).max())))
-    assert frac <= 1e-3
+    vol = _host16(got)[..., :256]
+    diff, maxd = 0, 0
+    for y0 in range(0, 1080, 120):
+        exp = orc.cost_band(sc.ref, sc.nbrs, sc.side, sc.K, sc.R, sc.t, sc.plane_n, sc.rho_far, sc.drho, 256,
+                            y0, y0 + 120, cost=1)
+        band = vol[y0:y0 + 120]
+        diff += int(np.sum(band != exp))
+        maxd = max(maxd, int(np.abs(band.astype(int) - exp).max()))
+    frac = diff / vol.size
+    print("PARITY ncc fhd 1920x1080x256, every voxel: %d differ (%.3g, max |diff| %d)" % (diff, frac, maxd))
+    assert frac <= 1e-4, frac
 
 
 @pytest.mark.parametrize("variant", [0, 2])
