@@ -546,7 +546,7 @@ __device__ __forceinline__ int cen_fix(const CostArgs& a, const float (*vt)[SW],
 // rows, pixel rows pr0 + r at column pc), decided exactly by cen_fix, one
 // pixel at a time for the whole warp; corr[r] gets the change of chunk row r's
 // Hamming distance (zero for the others).  Called by the whole warp, and out
-// of line: about one warp-pair in thirty has a pixel left here.
+// of line: about one warp-pair in eighty has a pixel left here.
 __device__ __noinline__ void fix_ties(const CostArgs& a, const SmemCost& sm, int buf, int k, int tx0, int ty0,
                                       int pr0, int pc, int jlast, uint32_t fmask, int lane, int* corr)
 {
